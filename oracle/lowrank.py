@@ -1,0 +1,140 @@
+"""Randomized SVD (Algorithm 1) and randomized Nystrom (Algorithm 2) on the
+block SRHT sketch, plain FP64 numpy/LAPACK. TEST INFRASTRUCTURE ONLY.
+
+Orientation. The paper states both algorithms for an m x n matrix with m <= n
+and the sketch Y = A Omega^T. This library takes the tall n x m matrix (the
+paper's A transposed) and forms B = Omega A, so the paper's Y is B^T here and
+the roles of the two factors swap (Sec. 3.1, Algorithm 1, last step):
+U = P V~_k, S = Sigma~_k, V = Q U~_k.
+
+Readings of the paper used here (each also listed with the design notes):
+
+* Algorithm 1 uses Householder QR (LAPACK geqrf/orgqr via numpy) and the SVD
+  of the small R^T factor (LAPACK gesdd).
+* Algorithm 2, step 6 writes (Y V~_k) Sigma~_k^-1; with Z = Q~ R and
+  R = U~ Sigma~ V~^T the quantity that equals Q~ U~_k (the stabler variant
+  the text mentions) is (Z V~_k) Sigma~_k^-1, so Z is used.
+* Remark 3.1 only says "shift as in Li et al."; the shift used is
+  nu = sqrt(n) * 2^-52 * ||Y||_F, Y_nu = Y + nu Omega^T,
+  core = sym(Omega Y_nu), Lambda = max(Sigma~_k^2 - nu, 0); if the Cholesky
+  factorisation still fails, nu is doubled (at most 10 times).
+* Cholesky convention: C upper triangular with C^T C = core, Z = Y C^-1.
+* Singular vectors are only defined up to sign: each column of U is flipped
+  so its largest-magnitude entry (lowest index on ties) is positive, and the
+  matching column of V gets the same flip.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+
+from .bsrht import dense_omega, sketch_dense
+
+EPS64 = 2.0 ** -52
+
+
+def sign_normalize(u: np.ndarray, v: np.ndarray | None = None):
+    """Flip columns so that each column's largest-|.| entry is positive."""
+    u = np.array(u, copy=True)
+    idx = np.argmax(np.abs(u), axis=0)
+    sg = np.sign(u[idx, np.arange(u.shape[1])])
+    sg[sg == 0] = 1.0
+    u *= sg
+    if v is None:
+        return u
+    v = np.array(v, copy=True) * sg
+    return u, v
+
+
+def best_rank_k_errors(sigma: np.ndarray, k: int) -> dict:
+    """Eckart-Young optimal errors of a rank-k approximation (Sec. 3):
+    spectral sigma_{k+1}, trace sum_{i>k} sigma_i, Frobenius (sum sigma_i^2)^1/2."""
+    tail = np.asarray(sigma, dtype=np.float64)[k:]
+    return {
+        "spectral": float(tail[0]) if tail.size else 0.0,
+        "trace": float(np.sum(tail)),
+        "fro": float(math.sqrt(np.sum(tail * tail))),
+    }
+
+
+def truncated_svd(a: np.ndarray, k: int):
+    """Best rank-k approximation [[A]]_k by LAPACK SVD: (U_k, s_k, V_k)."""
+    u, s, vt = np.linalg.svd(np.asarray(a, dtype=np.float64), full_matrices=False)
+    uk, vk = sign_normalize(u[:, :k], vt[:k].T)
+    return uk, s[:k], vk
+
+
+def rsvd(a: np.ndarray, k: int, l: int, p: int, seed: int):
+    """Algorithm 1 for the tall n x m matrix ``a``; returns (U n x k, S k, V m x k)."""
+    a = np.asarray(a, dtype=np.float64)
+    # Step 1: Y = A_paper Omega^T = (Omega A)^T, m x l.
+    y = sketch_dense(a, p, l, seed).T
+    # Step 2: orthonormal basis Q of range(Y).
+    q, _ = np.linalg.qr(y)
+    # Step 3: Z = Q^T A_paper = (A Q)^T; step 4 needs Z^T = A Q = P R.
+    zt = a @ q
+    pmat, rmat = np.linalg.qr(zt)
+    # Step 5: SVD of R^T (l x l), truncated to rank k.
+    ut, st, vtt = np.linalg.svd(rmat.T)
+    # Step 6: A_paper ~ (Q U~_k) S~_k (P V~_k)^T, so A ~ (P V~_k) S~_k (Q U~_k)^T.
+    u = pmat @ vtt[:k].T
+    v = q @ ut[:, :k]
+    u, v = sign_normalize(u, v)
+    return u, st[:k].copy(), v
+
+
+def nystrom_shift(y: np.ndarray) -> float:
+    """nu = sqrt(n) * eps * ||Y||_F (reading of Remark 3.1)."""
+    return math.sqrt(y.shape[0]) * EPS64 * float(np.linalg.norm(y))
+
+
+def nystrom(a: np.ndarray, k: int, l: int, p: int, seed: int,
+            shift: bool = True, max_doublings: int = 10):
+    """Algorithm 2 (with the Z fix in step 6 and the shift of Remark 3.1).
+
+    ``a`` is n x n symmetric PSD. Returns (U n x k, Lambda k, nu) with
+    A ~ U diag(Lambda) U^T.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    n = a.shape[0]
+    om = dense_omega(n, p, l, seed)
+    # Step 1: Y = A Omega^T (n x l).
+    y = a @ om.T
+    nu = nystrom_shift(y) if shift else 0.0
+    for _ in range(max_doublings + 1):
+        y_nu = y + nu * om.T
+        core = om @ y_nu
+        core = 0.5 * (core + core.T)
+        try:
+            # Step 2: Cholesky factor C (upper, C^T C = core).
+            c = sla.cholesky(core, lower=False)
+            break
+        except np.linalg.LinAlgError:
+            nu = 2.0 * nu if nu > 0 else EPS64 * float(np.linalg.norm(y))
+    else:
+        raise np.linalg.LinAlgError("core not positive definite after shifting")
+    # Step 3: Z = Y C^-1 (triangular solve from the right).
+    z = sla.solve_triangular(c, y_nu.T, trans="T", lower=False).T
+    # Step 4: R factor of Z.
+    rmat = np.linalg.qr(z, mode="r")
+    # Step 5: SVD of R.
+    _, sr, vrt = np.linalg.svd(rmat)
+    # Step 6: U^ = (Z V~_k) Sigma~_k^-1.
+    u = (z @ vrt[:k].T) / sr[:k]
+    # Step 7: A ~ U^ Sigma~_k^2 U^^T, minus the shift.
+    lam = np.maximum(sr[:k] ** 2 - nu, 0.0)
+    u = sign_normalize(u)
+    return u, lam, nu
+
+
+def nystrom_full(a: np.ndarray, l: int, p: int, seed: int) -> np.ndarray:
+    """The untruncated Nystrom matrix (Omega A)^T (Omega A Omega^T)^+ (Omega A)
+    by its definition in Sec. 3.2 (pseudo-inverse, no shift)."""
+    a = np.asarray(a, dtype=np.float64)
+    om = dense_omega(a.shape[0], p, l, seed)
+    b = om @ a
+    core = b @ om.T
+    return b.T @ np.linalg.pinv(core, hermitian=True) @ b

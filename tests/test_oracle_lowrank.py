@@ -1,0 +1,126 @@
+"""Pins of the CPU oracle's randomized SVD (Algorithm 1) and Nystrom
+(Algorithm 2) against closed forms, LAPACK special cases and the bounds of
+Sec. 3 (no GPU)."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import bsrht, lowrank
+import synth
+
+
+def test_sign_normalize():
+    u = np.array([[1.0, -3.0], [-2.0, 1.0]])
+    v = np.array([[1.0, 1.0]])
+    un, vn = lowrank.sign_normalize(u, v)
+    assert np.array_equal(un, [[-1.0, 3.0], [2.0, -1.0]])
+    assert np.array_equal(vn, [[-1.0, -1.0]])
+
+
+def test_best_rank_k_errors_closed_form():
+    """Sec. 3: spectral sigma_{k+1}, trace sum of the tail, Frobenius norm of the tail."""
+    s = np.array([5.0, 4.0, 3.0, 2.0, 1.0])
+    e = lowrank.best_rank_k_errors(s, 2)
+    assert e == {"spectral": 3.0, "trace": 6.0, "fro": math.sqrt(14.0)}
+    a, _ = synth.haar_spectrum(200, 40, seed=1)
+    u, sk, v = lowrank.truncated_svd(a, 5)
+    sv = np.linalg.svd(a, compute_uv=False)
+    assert abs(np.linalg.norm(a - (u * sk) @ v.T, 2) - sv[5]) < 1e-12
+
+
+@pytest.mark.parametrize("p", [1, 4, 8])
+def test_rsvd_exact_recovery(p):
+    """range(A Omega^T) captures an exact rank-r matrix when r < l (w.p. 1)."""
+    a = synth.exact_rank(600, 80, 20, seed=3)
+    u, s, v = lowrank.rsvd(a, 20, 32, p, seed=5)
+    assert np.linalg.norm(a - (u * s) @ v.T) <= 1e-12 * np.linalg.norm(a)
+    np.testing.assert_allclose(s, 1.0 / np.arange(1, 21), rtol=1e-12)
+
+
+def test_rsvd_full_sketch_is_truncated_svd():
+    """With l = m the sketch spans all of R^m, so Algorithm 1 returns the
+    truncated SVD that LAPACK computes directly (Eckart-Young optimum)."""
+    a, _ = synth.haar_spectrum(512, 32, seed=2)
+    u, s, v = lowrank.rsvd(a, 8, 32, 4, seed=1)
+    ur, sr, vr = lowrank.truncated_svd(a, 8)
+    np.testing.assert_allclose(s, sr, rtol=1e-12)
+    np.testing.assert_allclose(u, ur, atol=1e-10)
+    np.testing.assert_allclose(v, vr, atol=1e-10)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_rsvd_eckart_young_and_quasi_optimality(seed):
+    """Errors are >= the Eckart-Young optimum and <= opt + 2.5 ||A - [[A]]_d||_F
+    (the RSVD bound of Sec. 3.1 with d = l/4)."""
+    a, sig = synth.haar_spectrum(2048, 128, seed=11)
+    k, l = 10, 64
+    u, s, v = lowrank.rsvd(a, k, l, 4, seed)
+    res = a - (u * s) @ v.T
+    opt = lowrank.best_rank_k_errors(sig, k)
+    tail_d = lowrank.best_rank_k_errors(sig, l // 4)["fro"]
+    fro = np.linalg.norm(res)
+    spec = np.linalg.norm(res, 2)
+    assert fro >= opt["fro"] * (1 - 1e-12)
+    assert spec >= opt["spectral"] * (1 - 1e-12)
+    assert fro <= opt["fro"] + 2.5 * tail_d
+    assert spec <= opt["spectral"] + 2.5 * tail_d
+    # Orthonormal factors
+    assert np.linalg.norm(u.T @ u - np.eye(k)) < 1e-12
+    assert np.linalg.norm(v.T @ v - np.eye(k)) < 1e-12
+
+
+def test_nystrom_exact_recovery():
+    """A PSD matrix of exact rank r < l is reproduced (up to the shift)."""
+    a = synth.psd_lowrank(400, 15, seed=2)
+    u, lam, nu = lowrank.nystrom(a, 15, 30, 4, seed=3)
+    assert nu > 0
+    assert np.linalg.norm(a - (u * lam) @ u.T) <= 1e-9 * np.linalg.norm(a)
+    np.testing.assert_allclose(lam, 1.0 / np.arange(1, 16), rtol=1e-8)
+
+
+def test_nystrom_algorithm_matches_definition():
+    """Algorithm 2 with k = l equals the Nystrom matrix of Sec. 3.2,
+    (Omega A)^T (Omega A Omega^T)^+ (Omega A), up to the O(nu) shift."""
+    x = synth.rbf_points(300, 6, seed=4).astype(np.float64)
+    h = synth.rbf_bandwidth(x)
+    a = synth.rbf_kernel(x, h)
+    l = 40
+    u, lam, nu = lowrank.nystrom(a, l, l, 4, seed=8)
+    ref = lowrank.nystrom_full(a, l, 4, seed=8)
+    assert np.linalg.norm((u * lam) @ u.T - ref) <= 1e-7 * np.linalg.norm(a)
+
+
+def test_nystrom_residual_is_psd_and_trace_identity():
+    """Sec. 3.2: A - [[A]]^(Nyst) is PSD, so its trace norm is tr(A) - tr(A^)."""
+    x = synth.rbf_points(256, 5, seed=5).astype(np.float64)
+    a = synth.rbf_kernel(x, synth.rbf_bandwidth(x))
+    ah = lowrank.nystrom_full(a, 32, 4, seed=1)
+    res = a - ah
+    ev = np.linalg.eigvalsh(0.5 * (res + res.T))
+    assert ev.min() >= -1e-9 * np.trace(a)
+    assert abs(np.sum(np.abs(ev)) - (np.trace(a) - np.trace(ah))) <= 1e-8 * np.trace(a)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_nystrom_trace_bounds(seed):
+    """Eckart-Young lower bound and the Nystrom bound of Sec. 3.2,
+    ||A - [[A]]_k^(Nyst)||_* <= ||A - [[A]]_k||_* + 3 ||A - [[A]]_d||_*."""
+    x = synth.rbf_points(512, 8, seed=6).astype(np.float64)
+    a = synth.rbf_kernel(x, 0.5 * synth.rbf_bandwidth(x))
+    lam_all = np.linalg.eigvalsh(a)[::-1]
+    k, l = 20, 80
+    u, lam, _ = lowrank.nystrom(a, k, l, 4, seed)
+    res = a - (u * lam) @ u.T
+    trace_err = np.sum(np.abs(np.linalg.eigvalsh(0.5 * (res + res.T))))
+    opt = np.sum(lam_all[k:])
+    tail_d = np.sum(lam_all[l // 4:])
+    assert trace_err >= opt * (1 - 1e-10)
+    assert trace_err <= opt + 3 * tail_d
+
+
+def test_nystrom_shift_rule():
+    """Remark 3.1 reading: nu = sqrt(n) eps ||Y||_F."""
+    y = np.ones((16, 3))
+    assert lowrank.nystrom_shift(y) == 4.0 * 2.0 ** -52 * math.sqrt(48.0)
