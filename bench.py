@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the block-SRHT hot path on GB300.
+
+One step = the whole hot path over one batch of synthetic input: the block
+SRHT sketch B = Omega A (Sec. 2) followed by the rank-k randomized SVD of
+Algorithm 1 (Sec. 3.1) on the tall-skinny workload n = 2^20, m = 4096,
+A = G1 diag(i^-2) G2^T + 1e-4 N in FP32, p = 4 blocks, l = 512, k = 100.
+
+Prints ONE JSON line (rank 0). ``value`` is the whole-step throughput in
+GB/s of A: (n * m * sizeof(A)) / step time; the sketch kernel's own HBM
+throughput and the per-stage times are reported beside it. A (16 GiB) is far
+larger than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs its own replica on its own GPU (weak
+scaling, no collective on the data path); the step time is the max over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "tall-skinny lowrank+noise n=2^20 m=4096 fp32 p=4 l=512 rank-100 rSVD"
+METRIC = "ΩA sketch HBM GB/s (% peak); rSVD/Nyström time at stated error; p50/p99 latency"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--m", type=int, default=4096)
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--l", type=int, default=512)
+    ap.add_argument("--k", type=int, default=100)
+    ap.add_argument("--dtype", choices=["f32", "f64", "bf16", "f16"], default="f32")
+    ap.add_argument("--mode", choices=["full", "sketch"], default="full",
+                    help="full = sketch + rSVD (the benchmark step); sketch = sketch only")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-cols", type=int, default=64)
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def torch_dtype(name):
+    import torch
+    return {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16, "f16": torch.float16}[name]
+
+
+def make_input(args, rank):
+    import synth
+    dt = torch_dtype(args.dtype)
+    import torch
+    if dt in (torch.bfloat16, torch.float16):
+        a = synth.lowrank_noise_device(args.n, args.m, seed=1236 + rank, dtype=torch.float32)
+        return a.to(dt)
+    return synth.lowrank_noise_device(args.n, args.m, seed=1236 + rank, dtype=dt)
+
+
+# --------------------------------------------------------------- CPU oracle
+def cpu_baseline(args, seconds_target=15.0):
+    """The CPU oracle's dense sketch on a column sample of the same workload
+    (the sketch is column-separable), scaled to GB/s of A."""
+    import numpy as np
+    from oracle import bsrht as orc
+    import synth
+
+    cols = args.cpu_sample_cols
+    n = args.n
+    a = synth.lowrank_noise(n, cols, rank=min(1000, cols), seed=77).astype(np.float32)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        orc.sketch_dense(a, args.p, args.l, seed=reps)
+        reps += 1
+        if time.perf_counter() - t0 > seconds_target or reps >= 3:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    elem = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}[args.dtype]
+    gbs = n * cols * elem / dt / 1e9
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"dense-Omega oracle sketch of an n={n} x {cols}-column slice "
+                      f"(p={args.p}, l={args.l}), {reps} rep(s), {dt:.2f} s each; GB/s of A columns"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    import numpy as np
+    from oracle import bsrht as orc
+    import synth
+
+    cols = args.cpu_sample_cols
+    a = synth.lowrank_noise(args.n, cols, rank=min(1000, cols), seed=77).astype(np.float32)
+    for w in range(args.warmup):
+        orc.sketch_dense(a, args.p, args.l, seed=w)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        orc.sketch_dense(a, args.p, args.l, seed=s)
+        times.append(time.perf_counter() - t0)
+    dt = statistics.mean(times)
+    elem = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}[args.dtype]
+    gbs = args.n * cols * elem / dt / 1e9
+    sample = (f"each step: dense-Omega oracle sketch of an n={args.n} x {cols}-column slice of the "
+              f"workload (column-separable), GB/s of A")
+    line = {"metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample}, "impl": "reference",
+            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup(args)
+    import paper_2210_11295_gb300 as lib
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    a = make_input(args, rank)
+    torch.cuda.synchronize()
+    n, m, p, l, k = args.n, args.m, args.p, args.l, args.k
+    elem = a.element_size()
+    stream = torch.cuda.current_stream()
+    mode = args.mode
+    if mode == "full":
+        try:
+            lib.bsrht_rsvd(a[:4096, :256].contiguous(), 4, 16, 1, 0)
+        except lib.BsrhtError as e:
+            if e.status != -95:
+                raise
+            mode = "sketch"
+    out = torch.empty(l, m, device=dev, dtype=lib.sketch_out_dtype(a.dtype))
+    ws = torch.empty(max(lib.bsrht_sketch_workspace(n, m, p, l, a.dtype), 1), dtype=torch.uint8, device=dev)
+    if mode == "full":
+        rws = torch.empty(max(lib.bsrht_rsvd_workspace(n, m, k, l, p, a.dtype), 1), dtype=torch.uint8, device=dev)
+        u = torch.empty(n, k, device=dev, dtype=torch.float64)
+        s = torch.empty(k, device=dev, dtype=torch.float64)
+        v = torch.empty(m, k, device=dev, dtype=torch.float64)
+
+    def step(seed):
+        if mode == "full":
+            lib.bsrht_rsvd(a, k, l, p, seed, workspace=rws, outs=(u, s, v))
+        else:
+            lib.bsrht_sketch(a, p, l, seed, out=out, workspace=ws)
+
+    for w in range(args.warmup):
+        step(w)
+    torch.cuda.synchronize()
+
+    # Sketch kernel alone, CUDA events on the launching stream (the roofline leg).
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        lib.bsrht_sketch(a, p, l, 1000 + i, out=out, workspace=ws)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    sketch_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+
+    # The timed steps.
+    launches0 = lib.bsrht_kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = lib.bsrht_kernel_launches() - launches0
+    step_ms = t_start.elapsed_time(t_end) / args.steps
+    step_ms = max_over_ranks(world, step_ms)
+
+    # End to end through the C ABI from pinned host buffers.
+    a_host = a.cpu().pin_memory()
+    e2e_ms = None
+    h2d = n * m * elem
+    d2h = (n * k + k + m * k) * 8 if mode == "full" else l * m * out.element_size()
+    if args.e2e_steps > 0:
+        a_dev2 = torch.empty_like(a)
+        if mode == "full":
+            hu = torch.empty(n, k, dtype=torch.float64).pin_memory()
+            hs = torch.empty(k, dtype=torch.float64).pin_memory()
+            hv = torch.empty(m, k, dtype=torch.float64).pin_memory()
+        else:
+            hb = torch.empty(l, m, dtype=out.dtype).pin_memory()
+        del a
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            a_dev2.copy_(a_host, non_blocking=True)
+            if mode == "full":
+                lib.bsrht_rsvd(a_dev2, k, l, p, i, workspace=rws, outs=(u, s, v))
+                hu.copy_(u, non_blocking=True)
+                hs.copy_(s, non_blocking=True)
+                hv.copy_(v, non_blocking=True)
+            else:
+                lib.bsrht_sketch(a_dev2, p, l, i, out=out, workspace=ws)
+                hb.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
+        e2e_ms = max_over_ranks(world, e2e_ms)
+
+    total_bytes_all = sum_over_ranks(world, float(n * m * elem))
+    value = total_bytes_all / (step_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    sketch_bytes = n * m * elem + l * m * out.element_size()
+    achieved = sketch_bytes / (sketch_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(step_ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"f32": "f32", "f64": "f64", "bf16": "f32", "f16": "f32"}[args.dtype],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if (mode == "full" and args.dtype == "f32" and n == 1 << 20 and m == 4096)
+                   else f"n={n} m={m} {args.dtype} p={p} l={l} k={k} mode={mode}",
+                   "n": n, "m": m, "p": p, "l": l, "k": k, "storage": args.dtype, "step": mode,
+                   "l2": "A is 16 GiB >> 129 MB L2: inputs larger than L2, no flush"},
+        "sketch": {"ms": round(sketch_ms, 4), "gbs": round(achieved, 2),
+                   "frac_of_measured_peak": round(achieved / peak, 4)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "k_sketch_chunked + k_sketch_reduce (one bsrht_sketch call)",
+                     "peak_kind": peak_kind},
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+        "e2e": {"value": round(total_bytes_all / (e2e_ms * 1e-3) / 1e9, 3) if e2e_ms else None, "unit": "GB/s",
+                "ms_per_step": round(e2e_ms, 3) if e2e_ms else None,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

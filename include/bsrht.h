@@ -1,0 +1,167 @@
+/*
+ * bsrht.h - C ABI of the block SRHT sketching library (sm_103a, one GPU).
+ *
+ * Method: Balabanov, Beaupere, Grigori, Lederer, "Block subsampled randomized
+ * Hadamard transform for low-rank approximation on distributed
+ * architectures".  Orientation used by every call: A is n x m and tall, the
+ * sketching matrix Omega is l x n, and the sketch is B = Omega A (l x m).
+ * The paper writes the same quantities for the transposed m x n matrix, so
+ * its Y = A Omega^T is B^T here.
+ *
+ * Omega (Sec. 2, eq. 2.3) = [Omega^(1) ... Omega^(p)],
+ *   Omega^(i) = sqrt(r/l) Dt^(i) R H D^(i),
+ * with one sampling matrix R (uniform, with replacement) shared by all p
+ * blocks, independent Rademacher diagonals D^(i) (r x r) and Dt^(i) (l x l),
+ * and H the r x r Walsh-Hadamard matrix (Sylvester/natural order) scaled by
+ * 1/sqrt(r); every entry of Omega is +-1/sqrt(l).  Block i holds rows
+ * [i*rb, min(n,(i+1)*rb)) of A with rb = ceil(n/p); r is the next power of
+ * two >= rb and the missing rows count as zero (the partial SRHT / zero
+ * padding of Sec. 2).
+ *
+ * Randomness: Philox4x64-10 (Salmon et al., SC'11) with key (seed, 0).
+ *   D^(i)_kk  : counter (k>>8, i, 0, 0), output word (k>>6)&3, bit k&63
+ *   Dt^(i)_jj : counter (j>>8, i, 1, 0), output word (j>>6)&3, bit j&63
+ *               (a set bit means -1)
+ *   R row j   : counter (j>>2, 0, 2, 0), output word j&3, s_j = word mod r
+ * so a given (seed, n, p, l) defines the same Omega on every device.
+ *
+ * Memory: every matrix is row-major.  Unless noted, pointers are DEVICE
+ * pointers owned by the caller; the library never frees them and never
+ * writes to A.  Calls are asynchronous and stream-ordered on opts->stream
+ * (NULL = the legacy default stream); a non-zero return means nothing was
+ * enqueued, except BSRHT_ECUDA (a launch failed) and the numerical statuses
+ * of bsrht_rsvd / bsrht_nystrom, which are read back on the stream and so
+ * make those two calls synchronous with it.
+ *
+ * Scratch: if opts->workspace is NULL the library allocates scratch from its
+ * own per-device pool (cudaMalloc, kept for reuse, released by
+ * bsrht_release_pool); otherwise it uses the caller's buffer, which must hold
+ * at least the bytes that the matching *_workspace query reports.
+ */
+#ifndef BSRHT_H_
+#define BSRHT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes (0 = success, negative = failure) ------------------- */
+#define BSRHT_OK 0
+#define BSRHT_EINVAL (-22)     /* bad size, pointer, dtype, stride or option   */
+#define BSRHT_ENOMEM (-12)     /* scratch allocation failed / workspace short  */
+#define BSRHT_EUNSUP (-95)     /* valid but unsupported combination            */
+#define BSRHT_ETIMEDOUT (-110) /* a bounded wait gave up                       */
+#define BSRHT_ENOTPD (-1001)   /* Nystrom core not positive definite after all
+                                  shift doublings (Remark 3.1)                  */
+#define BSRHT_ENOCONV (-1002)  /* Jacobi SVD hit its sweep limit               */
+#define BSRHT_ECUDA (-1003)    /* a CUDA runtime call or launch failed          */
+
+/* ---- element types of A ----------------------------------------------- */
+typedef enum bsrht_dtype {
+  BSRHT_F64 = 0,  /* double: sketch computed and returned in FP64           */
+  BSRHT_F32 = 1,  /* float : FP32 arithmetic, FP32 sketch                   */
+  BSRHT_BF16 = 2, /* bfloat16 storage, FP32 arithmetic, FP32 sketch         */
+  BSRHT_F16 = 3   /* IEEE half storage, FP32 arithmetic, FP32 sketch        */
+} bsrht_dtype;
+
+/* ---- kernel variant of the sketch ------------------------------------- */
+typedef enum bsrht_variant {
+  BSRHT_VARIANT_AUTO = 0,     /* library choice                             */
+  BSRHT_VARIANT_CUDACORE = 1, /* radix-2 butterflies on CUDA cores (K1)     */
+  BSRHT_VARIANT_TENSOR = 2    /* Kronecker H16 factors on tensor cores (K2)  */
+} bsrht_variant;
+
+typedef struct bsrht_opts {
+  int32_t dtype;          /* bsrht_dtype of A                                */
+  int32_t variant;        /* bsrht_variant                                   */
+  int64_t lda;            /* elements between consecutive rows of A; 0 means
+                             the row length (m, or n for bsrht_nystrom)      */
+  void* stream;           /* cudaStream_t, NULL = legacy default stream      */
+  void* workspace;        /* device scratch or NULL (library pool)           */
+  size_t workspace_bytes; /* size of opts->workspace in bytes                */
+} bsrht_opts;
+
+/* Fills *opts with dtype F64, variant AUTO, lda 0, NULL stream/workspace. */
+void bsrht_opts_init(bsrht_opts* opts);
+
+/* Short English description of a status code (static storage). */
+const char* bsrht_strerror(int status);
+
+/*
+ * bsrht_sketch - B = Omega A (eq. 2.3 applied as the block sum of eq. 2.4).
+ *   A    : n x m, row stride opts->lda (>= m), element type opts->dtype.
+ *   n, m : n >= 1, m >= 0.  p: number of blocks, 1 <= p <= n.
+ *   l    : sketch rows, 1 <= l <= n (Thm 2.1 assumes n >= l); l > r is
+ *          allowed because R samples with replacement.
+ *   out  : l x m, row stride m; double for BSRHT_F64 input, float otherwise.
+ * One pass over A: Philox signs, the Walsh-Hadamard butterflies, the row
+ * sample and the sum over the p blocks all run inside the kernels; the block
+ * sum is reduced in a fixed order, so repeated calls give identical bits.
+ * Returns BSRHT_EINVAL on bad arguments (nothing enqueued).
+ */
+int bsrht_sketch(const void* A, int64_t n, int64_t m, int32_t p, int64_t l,
+                 uint64_t seed, void* out, const bsrht_opts* opts);
+
+/* Scratch bytes bsrht_sketch needs for these sizes (host only, no GPU work). */
+int bsrht_sketch_workspace(int64_t n, int64_t m, int32_t p, int64_t l,
+                           const bsrht_opts* opts, size_t* bytes);
+
+/*
+ * bsrht_rsvd - rank-k randomized SVD, Algorithm 1 of Sec. 3.1, on the sketch.
+ *   A (n x m) ~ U diag(S) V^T with U n x k, S k (descending), V m x k, all
+ *   double, U and V with orthonormal columns.  Requires 1 <= k <= l <= m and
+ *   l <= n.  Steps: B = Omega A; Q = orth(B^T) (FP64 CholeskyQR2);
+ *   W = A Q (second pass over A, in the arithmetic of A: FP64 for F64, FP32
+ *   otherwise); W = P R (CholeskyQR2); SVD of R^T (FP64 one-sided Jacobi);
+ *   U = P V~_k, S = Sigma~_k, V = Q U~_k.  Each column of U is flipped so its
+ *   largest-magnitude entry is positive (V gets the same flip).
+ *   Synchronises opts->stream to read the status of the small factorizations;
+ *   returns BSRHT_ENOTPD if a Gram matrix is numerically singular,
+ *   BSRHT_ENOCONV if the Jacobi SVD does not converge.
+ */
+int bsrht_rsvd(const void* A, int64_t n, int64_t m, int32_t k, int64_t l,
+               int32_t p, uint64_t seed, double* U, double* S, double* V,
+               const bsrht_opts* opts);
+
+int bsrht_rsvd_workspace(int64_t n, int64_t m, int32_t k, int64_t l, int32_t p,
+                         const bsrht_opts* opts, size_t* bytes);
+
+/*
+ * bsrht_nystrom - rank-k randomized Nystrom approximation, Algorithm 2 of
+ * Sec. 3.2, of a symmetric positive semi-definite n x n matrix A (row stride
+ * opts->lda >= n; symmetry is assumed, not checked).
+ *   A ~ U diag(Lambda) U^T with U n x k (orthonormal columns), Lambda k
+ *   (descending, >= 0), both double.  Requires 1 <= k <= l <= n.
+ *   Steps: Y = (Omega A)^T; shift nu = sqrt(n) 2^-52 ||Y||_F,
+ *   Y_nu = Y + nu Omega^T; core = sym(Omega Y_nu); FP64 Cholesky C^T C =
+ *   core (nu doubled up to 10 times on failure, Remark 3.1);
+ *   Z = Y_nu C^-1; R factor of Z (CholeskyQR2); SVD R = U~ Sigma~ V~^T;
+ *   U = Z V~_k Sigma~_k^-1; Lambda = max(Sigma~_k^2 - nu, 0).
+ *   Synchronises opts->stream; BSRHT_ENOTPD if the core stays indefinite.
+ */
+int bsrht_nystrom(const void* A, int64_t n, int32_t k, int64_t l, int32_t p,
+                  uint64_t seed, double* U, double* Lambda,
+                  const bsrht_opts* opts);
+
+int bsrht_nystrom_workspace(int64_t n, int32_t k, int64_t l, int32_t p,
+                            const bsrht_opts* opts, size_t* bytes);
+
+/* Frees the library's scratch pool on the current device (no-op if empty).
+ * The caller must make sure no call that uses the pool is still running. */
+int bsrht_release_pool(void);
+
+/* Number of CUDA kernels the library has launched in this process (all
+ * devices, all threads).  Diagnostic counter for benchmarks and tests. */
+uint64_t bsrht_kernel_launches(void);
+
+/* Library version, e.g. "0.1.0" (static storage). */
+const char* bsrht_version(void);
+
+#ifdef __cplusplus
+} /* extern "C" */
+#endif
+
+#endif /* BSRHT_H_ */

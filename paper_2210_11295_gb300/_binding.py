@@ -1,0 +1,213 @@
+"""ctypes binding of libbsrht (include/bsrht.h): argument marshalling only.
+
+Every function here forwards torch tensors' device pointers, strides and the
+current CUDA stream to the C entry point of the same name; all arithmetic runs
+in the library's CUDA kernels. If the library has not been built the import
+of this module raises, so there is no silent fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libbsrht.so")
+
+BSRHT_OK = 0
+BSRHT_EINVAL = -22
+BSRHT_ENOMEM = -12
+BSRHT_EUNSUP = -95
+BSRHT_ETIMEDOUT = -110
+BSRHT_ENOTPD = -1001
+BSRHT_ENOCONV = -1002
+BSRHT_ECUDA = -1003
+
+F64, F32, BF16, F16 = 0, 1, 2, 3
+VARIANT_AUTO, VARIANT_CUDACORE, VARIANT_TENSOR = 0, 1, 2
+
+_DTYPES = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
+
+
+class BsrhtError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("dtype", ctypes.c_int32),
+        ("variant", ctypes.c_int32),
+        ("lda", ctypes.c_int64),
+        ("stream", ctypes.c_void_p),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libbsrht.so is not built ({LIB_PATH}); run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(LIB_PATH)
+    i64, i32, u64, vp, sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t
+    pd = ctypes.POINTER(ctypes.c_double)
+    po = ctypes.POINTER(Opts)
+    sigs = {
+        "bsrht_opts_init": (None, [po]),
+        "bsrht_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "bsrht_version": (ctypes.c_char_p, []),
+        "bsrht_sketch": (ctypes.c_int, [vp, i64, i64, i32, i64, u64, vp, po]),
+        "bsrht_sketch_workspace": (ctypes.c_int, [i64, i64, i32, i64, po, ctypes.POINTER(sz)]),
+        "bsrht_rsvd": (ctypes.c_int, [vp, i64, i64, i32, i64, i32, u64, pd, pd, pd, po]),
+        "bsrht_rsvd_workspace": (ctypes.c_int, [i64, i64, i32, i64, i32, po, ctypes.POINTER(sz)]),
+        "bsrht_nystrom": (ctypes.c_int, [vp, i64, i32, i64, i32, u64, pd, pd, po]),
+        "bsrht_nystrom_workspace": (ctypes.c_int, [i64, i32, i64, i32, po, ctypes.POINTER(sz)]),
+        "bsrht_release_pool": (ctypes.c_int, []),
+        "bsrht_kernel_launches": (ctypes.c_uint64, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def strerror(status: int) -> str:
+    return lib.bsrht_strerror(int(status)).decode()
+
+
+def version() -> str:
+    return lib.bsrht_version().decode()
+
+
+def _check(status: int, where: str) -> None:
+    if status != BSRHT_OK:
+        raise BsrhtError(status, where)
+
+
+def _dptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dbl(t: torch.Tensor):
+    return ctypes.cast(ctypes.c_void_p(t.data_ptr()), ctypes.POINTER(ctypes.c_double))
+
+
+def make_opts(a: torch.Tensor, variant: int = VARIANT_AUTO, workspace: torch.Tensor | None = None,
+              stream: torch.cuda.Stream | None = None) -> Opts:
+    if a.dim() != 2 or a.stride(1) != 1:
+        raise ValueError("A must be a 2-D tensor with unit column stride (row-major)")
+    if a.dtype not in _DTYPES:
+        raise ValueError(f"unsupported dtype {a.dtype}")
+    o = Opts()
+    lib.bsrht_opts_init(ctypes.byref(o))
+    o.dtype = _DTYPES[a.dtype]
+    o.variant = int(variant)
+    o.lda = int(a.stride(0)) if a.shape[0] > 1 else int(a.shape[1])
+    s = stream if stream is not None else torch.cuda.current_stream(a.device)
+    o.stream = ctypes.c_void_p(s.cuda_stream)
+    if workspace is not None:
+        o.workspace = ctypes.c_void_p(workspace.data_ptr())
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def sketch_out_dtype(dtype: torch.dtype) -> torch.dtype:
+    return torch.float64 if dtype == torch.float64 else torch.float32
+
+
+def bsrht_sketch_workspace(n: int, m: int, p: int, l: int, dtype=torch.float32,
+                           variant: int = VARIANT_AUTO) -> int:
+    o = Opts()
+    lib.bsrht_opts_init(ctypes.byref(o))
+    o.dtype = _DTYPES[dtype]
+    o.variant = int(variant)
+    out = ctypes.c_size_t(0)
+    _check(lib.bsrht_sketch_workspace(n, m, p, l, ctypes.byref(o), ctypes.byref(out)), "bsrht_sketch_workspace")
+    return int(out.value)
+
+
+def bsrht_sketch(a: torch.Tensor, p: int, l: int, seed: int, out: torch.Tensor | None = None,
+                 variant: int = VARIANT_AUTO, workspace: torch.Tensor | None = None,
+                 stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """B = Omega A (l x m) for the n x m device matrix ``a``."""
+    n, m = a.shape
+    if out is None:
+        out = torch.empty(l, m, device=a.device, dtype=sketch_out_dtype(a.dtype))
+    if out.shape != (l, m) or not out.is_contiguous() or out.dtype != sketch_out_dtype(a.dtype):
+        raise ValueError("out must be a contiguous l x m tensor of the sketch dtype")
+    o = make_opts(a, variant, workspace, stream)
+    _check(lib.bsrht_sketch(_dptr(a), n, m, p, l, seed & (2**64 - 1), _dptr(out), ctypes.byref(o)),
+           "bsrht_sketch")
+    return out
+
+
+def bsrht_rsvd_workspace(n: int, m: int, k: int, l: int, p: int, dtype=torch.float32) -> int:
+    o = Opts()
+    lib.bsrht_opts_init(ctypes.byref(o))
+    o.dtype = _DTYPES[dtype]
+    out = ctypes.c_size_t(0)
+    _check(lib.bsrht_rsvd_workspace(n, m, k, l, p, ctypes.byref(o), ctypes.byref(out)), "bsrht_rsvd_workspace")
+    return int(out.value)
+
+
+def bsrht_rsvd(a: torch.Tensor, k: int, l: int, p: int, seed: int, variant: int = VARIANT_AUTO,
+               workspace: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None,
+               outs=None):
+    """Rank-k randomized SVD (Algorithm 1): returns (U n x k, S k, V m x k) in float64."""
+    n, m = a.shape
+    if outs is None:
+        u = torch.empty(n, k, device=a.device, dtype=torch.float64)
+        s = torch.empty(k, device=a.device, dtype=torch.float64)
+        v = torch.empty(m, k, device=a.device, dtype=torch.float64)
+    else:
+        u, s, v = outs
+    o = make_opts(a, variant, workspace, stream)
+    _check(lib.bsrht_rsvd(_dptr(a), n, m, k, l, p, seed & (2**64 - 1), _dbl(u), _dbl(s), _dbl(v),
+                          ctypes.byref(o)), "bsrht_rsvd")
+    return u, s, v
+
+
+def bsrht_nystrom_workspace(n: int, k: int, l: int, p: int, dtype=torch.float32) -> int:
+    o = Opts()
+    lib.bsrht_opts_init(ctypes.byref(o))
+    o.dtype = _DTYPES[dtype]
+    out = ctypes.c_size_t(0)
+    _check(lib.bsrht_nystrom_workspace(n, k, l, p, ctypes.byref(o), ctypes.byref(out)),
+           "bsrht_nystrom_workspace")
+    return int(out.value)
+
+
+def bsrht_nystrom(a: torch.Tensor, k: int, l: int, p: int, seed: int, variant: int = VARIANT_AUTO,
+                  workspace: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None,
+                  outs=None):
+    """Rank-k randomized Nystrom (Algorithm 2): returns (U n x k, Lambda k) in float64."""
+    n = a.shape[0]
+    if a.shape[1] != n:
+        raise ValueError("A must be square")
+    if outs is None:
+        u = torch.empty(n, k, device=a.device, dtype=torch.float64)
+        lam = torch.empty(k, device=a.device, dtype=torch.float64)
+    else:
+        u, lam = outs
+    o = make_opts(a, variant, workspace, stream)
+    _check(lib.bsrht_nystrom(_dptr(a), n, k, l, p, seed & (2**64 - 1), _dbl(u), _dbl(lam), ctypes.byref(o)),
+           "bsrht_nystrom")
+    return u, lam
+
+
+def bsrht_kernel_launches() -> int:
+    """Cumulative count of CUDA kernels the library has launched."""
+    return int(lib.bsrht_kernel_launches())
+
+
+def bsrht_release_pool() -> None:
+    _check(lib.bsrht_release_pool(), "bsrht_release_pool")

@@ -1,0 +1,67 @@
+// Internal interface of the sketch kernels (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace bsrht {
+
+struct SketchPlan {
+  int dtype = 0;      // bsrht_dtype of A
+  int variant = 1;    // 1 = CUDA-core butterflies (K1), 2 = tensor cores (K2)
+  int path = 0;       // 0 = chunked FWHT kernel, 1 = small-r direct kernel
+  int inst = 0;       // kernel instance id within the dtype family
+  int W = 0, NT = 0, R2 = 0, JM = 0, NRL = 0;
+  int64_t n = 0, m = 0, lda = 0, l = 0;
+  int p = 0;
+  int64_t rb = 0, r = 0;
+  int64_t nch = 0;    // chunks per block
+  int64_t C = 0;      // chunks per column panel (p * nch)
+  int64_t P = 0;      // column panels
+  int64_t T = 0;      // tiles = P * C
+  int G = 0;          // CTAs of the chunked kernel (persistent, one wave)
+  int64_t jgroup = 0; // sketch rows handled per launch
+  size_t smem = 0;    // dynamic shared memory per CTA
+  size_t part_bytes = 0;  // partial-sum scratch
+  size_t work_bytes = 0;  // total scratch
+};
+
+// Fills plan for the given sizes; returns a bsrht status. When
+// query_device is false, no CUDA call is made and G is an upper bound.
+int sketch_make_plan(SketchPlan& plan, int dtype, int variant, int64_t n, int64_t m,
+                     int64_t lda, int p, int64_t l, bool query_device);
+
+// Enqueues the sketch on stream; work must hold plan.work_bytes.
+int sketch_run(const SketchPlan& plan, const void* A, uint64_t seed, void* out, int64_t ldo,
+               void* work, cudaStream_t stream);
+
+int num_sms();
+
+}  // namespace bsrht
+
+namespace bsrht {
+
+// Kernel instances of the chunked CUDA-core sketch (K1).
+struct K1Inst {
+  int NT, R2, JM;
+};
+// FP32 arithmetic (A in f32 / bf16 / f16), panels of 32 columns.
+constexpr int kW32 = 32;
+constexpr K1Inst kInstF32[] = {{512, 1024, 32}, {512, 512, 64}, {512, 256, 64}, {128, 128, 64},
+                               {128, 64, 64},   {128, 32, 64},  {128, 16, 64}};
+// FP64 arithmetic, panels of 16 columns (128-byte rows).
+constexpr int kW64 = 16;
+constexpr K1Inst kInstF64[] = {{512, 1024, 16}, {256, 512, 16}, {256, 256, 32}, {128, 128, 32},
+                               {128, 64, 32}};
+
+struct SketchArgs;
+// Per-family launchers (sketch_f32.cu / sketch_f64.cu).
+int sketch_launch_f32(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo,
+                      cudaStream_t stream);
+int sketch_launch_f64(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo,
+                      cudaStream_t stream);
+int sketch_occupancy_f32(const SketchPlan& plan);
+int sketch_occupancy_f64(const SketchPlan& plan);
+
+}  // namespace bsrht

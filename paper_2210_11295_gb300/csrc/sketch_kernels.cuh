@@ -1,0 +1,244 @@
+// Block SRHT sketch kernels, CUDA-core variant (K1).
+//
+// B = Omega A with Omega = [Omega^(1) ... Omega^(p)] (eq. 2.3) is formed as the
+// block sum of eq. 2.4 in one pass over A.  H_r of each block is split with
+// its tensor form (Sec. 2): for r = r1 * R2,
+//     H_r[s, a*R2 + b] = H_{r1}[s >> log2 R2, a] * H_{R2}[s & (R2-1), b],
+// so a chunk a of R2 rows only needs its own R2-point transform T_a; the
+// r1-point outer factor collapses to a sign per sampled row,
+//     (R H_r D x)_j = sum_a (-1)^popc((s_j >> log2 R2) & a) * T_a[s_j & (R2-1)].
+// A CTA streams chunks of one column panel (W columns): D^(i) signs and the
+// high log2(E) butterfly stages run in registers on a column held by one
+// thread, one shared-memory exchange gives the low log2(NRL) stages, and the
+// sampled rows are gathered from shared memory into per-thread accumulators
+// with the outer-factor and Dt^(i) signs.  Partial sums are written per
+// (CTA, panel) and summed in a fixed order by the reduce kernel, which also
+// applies the 1/sqrt(l) scale (every entry of Omega is +-1/sqrt(l)).
+#pragma once
+
+#include "common.cuh"
+
+namespace bsrht {
+
+struct SketchArgs {
+  const void* A;
+  int64_t lda, n, m;
+  int64_t rb, r;
+  int p;
+  int64_t j0, jn;  // sketch rows [j0, j0 + jn) handled by this launch
+  uint64_t seed;
+  int64_t nch, C, T;
+  int G;
+  void* part;      // Tc [(G + P) * jn * W]; slot of (CTA g, panel pc) = g + pc
+};
+
+// Walsh-Hadamard butterflies over the index of a register array:
+// stage h pairs v[e] with v[e + h] for every e with (e & h) == 0.
+template <typename Tc, int N>
+__device__ __forceinline__ void fwht_regs(Tc (&v)[N]) {
+#pragma unroll
+  for (int h = 1; h < N; h <<= 1) {
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      if ((e & h) == 0) {
+        const Tc x = v[e], y = v[e + h];
+        v[e] = x + y;
+        v[e + h] = x - y;
+      }
+    }
+  }
+}
+
+template <typename Tin, typename Tc, int W, int NT, int R2, int JM>
+struct K1Shape {
+  static constexpr int NRL = NT / W;          // rows handled in parallel (row lanes)
+  static constexpr int E = R2 / NRL;          // rows per thread in the register phase
+  static constexpr int Q = E / NRL;           // high parts per thread in the exchange phase
+  static constexpr int LOG_R2 = ilog2c(R2);
+  static constexpr int JG = JM * NRL;         // sketch rows per launch
+  static constexpr int DW = R2 >= 64 ? R2 / 64 : 1;  // D-sign words per chunk
+  static_assert(NT % W == 0, "NT multiple of W");
+  static_assert((R2 & (R2 - 1)) == 0 && R2 % NRL == 0, "R2 power of two");
+  static_assert(E >= NRL && E % NRL == 0, "exchange phase needs E >= NRL");
+  static_assert(JG % 64 == 0, "sketch-row groups start on 64-bit sign words");
+  static constexpr size_t smem_bytes() {
+    return sizeof(Tc) * R2 * W + 2 * sizeof(uint32_t) * JG + sizeof(uint64_t) * (JG / 64 + DW);
+  }
+};
+
+template <typename Tin, typename Tc, int W, int NT, int R2, int JM>
+__global__ void __launch_bounds__(NT, 1) k_sketch_chunked(SketchArgs g) {
+  using S = K1Shape<Tin, Tc, W, NT, R2, JM>;
+  constexpr int NRL = S::NRL, E = S::E, Q = S::Q, JG = S::JG, DW = S::DW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tc* tile = reinterpret_cast<Tc*>(smem_raw);                        // [R2][W]
+  uint32_t* s_lo = reinterpret_cast<uint32_t*>(tile + R2 * W);        // s_j & (R2-1)
+  uint32_t* s_hi = s_lo + JG;                                         // s_j >> log2 R2
+  uint64_t* s_dt = reinterpret_cast<uint64_t*>(s_hi + JG);            // Dt^(i) bits
+  uint64_t* s_d = s_dt + JG / 64;                                     // D^(i) bits of the chunk
+
+  const int tid = threadIdx.x;
+  const int cg = tid % W;
+  const int rl = tid / W;
+  const int jn = (int)g.jn;
+  const Tin* __restrict__ A = static_cast<const Tin*>(g.A);
+
+  for (int jl = tid; jl < jn; jl += NT) {
+    const uint64_t s = sample_word(g.seed, (uint64_t)(g.j0 + jl)) & (uint64_t)(g.r - 1);
+    s_lo[jl] = (uint32_t)(s & (R2 - 1));
+    s_hi[jl] = (uint32_t)(s >> S::LOG_R2);
+  }
+
+  const int64_t t_begin = (int64_t)blockIdx.x * g.T / g.G;
+  const int64_t t_end = (int64_t)(blockIdx.x + 1) * g.T / g.G;
+  Tc acc[JM];
+#pragma unroll
+  for (int u = 0; u < JM; ++u) acc[u] = Tc(0);
+  int64_t cur_pc = -1, cur_block = -1;
+  Tc* part = static_cast<Tc*>(g.part);
+
+  auto flush = [&](int64_t pc) {
+    Tc* dst = part + ((int64_t)blockIdx.x + pc) * (int64_t)jn * W + cg;
+#pragma unroll
+    for (int u = 0; u < JM; ++u) {
+      const int jl = rl + NRL * u;
+      if (jl < jn) dst[(int64_t)jl * W] = acc[u];
+    }
+  };
+
+  for (int64_t t = t_begin; t < t_end; ++t) {
+    const int64_t pc = t / g.C;
+    const int64_t c = t - pc * g.C;
+    const int64_t i = c / g.nch;
+    const int64_t a = c - i * g.nch;
+    if (pc != cur_pc) {
+      if (cur_pc >= 0) flush(cur_pc);
+#pragma unroll
+      for (int u = 0; u < JM; ++u) acc[u] = Tc(0);
+      cur_pc = pc;
+    }
+    const int64_t rows_i = min(g.rb, g.n - i * g.rb);
+    const int64_t row0 = a * R2;
+    if (row0 >= rows_i) continue;  // all-padding chunk: contributes zero
+
+    __syncthreads();  // previous chunk's gather is done with tile / tables
+    if (i != cur_block) {
+      for (int w = tid; w < (jn + 63) / 64; w += NT)
+        s_dt[w] = sign_word(g.seed, kStreamDt, (uint64_t)i, (uint64_t)(g.j0 >> 6) + w);
+      cur_block = i;
+    }
+    for (int w = tid; w < DW; w += NT)
+      s_d[w] = sign_word(g.seed, kStreamD, (uint64_t)i, (uint64_t)(row0 >> 6) + w);
+    __syncthreads();
+
+    // Register phase: rows rl + NRL*e of column cg; D^(i) signs; stages on
+    // the high log2(E) bits of the in-chunk row index.
+    Tc v[E];
+    const int64_t col = pc * W + cg;
+    const bool col_ok = col < g.m;
+    const int64_t nvalid = min((int64_t)R2, rows_i - row0);
+    const Tin* src = A + (i * g.rb + row0) * g.lda + col;
+    const int dshift = R2 >= 64 ? 0 : (int)(row0 & 63);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int rr = rl + NRL * e;
+      Tc x = Tc(0);
+      if (col_ok && rr < nvalid) x = load_as<Tc>(src + (int64_t)rr * g.lda);
+      const uint32_t neg = (uint32_t)((s_d[rr >> 6] >> ((rr & 63) + dshift)) & 1ull);
+      v[e] = flip(x, neg);
+    }
+    fwht_regs<Tc, E>(v);
+#pragma unroll
+    for (int e = 0; e < E; ++e) tile[(rl + NRL * e) * W + cg] = v[e];
+    __syncthreads();
+
+    // Exchange phase: rows NRL*h + b (b < NRL) of Q high parts h; stages on
+    // the low log2(NRL) bits.
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      Tc w2[NRL];
+      const int h = rl * Q + q;
+#pragma unroll
+      for (int b = 0; b < NRL; ++b) w2[b] = tile[(NRL * h + b) * W + cg];
+      fwht_regs<Tc, NRL>(w2);
+#pragma unroll
+      for (int b = 0; b < NRL; ++b) tile[(NRL * h + b) * W + cg] = w2[b];
+    }
+    __syncthreads();
+
+    // Sampled rows with the outer-factor sign H_{r1}[s_hi, a] and Dt^(i).
+#pragma unroll
+    for (int u = 0; u < JM; ++u) {
+      const int jl = rl + NRL * u;
+      if (jl < jn) {
+        const uint32_t neg =
+            (uint32_t)((__popcll((unsigned long long)s_hi[jl] & (unsigned long long)a) +
+                        (int)((s_dt[jl >> 6] >> (jl & 63)) & 1ull)) & 1);
+        acc[u] += flip(tile[s_lo[jl] * W + cg], neg);
+      }
+    }
+  }
+  if (cur_pc >= 0) flush(cur_pc);
+}
+
+// Fixed-order sum of the per-(CTA, panel) partials and the 1/sqrt(l) scale.
+template <typename Tc, typename Tout, int W>
+__global__ void k_sketch_reduce(SketchArgs g, Tout* __restrict__ out, int64_t ldo, Tc scale) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = g.jn * g.m;
+  if (idx >= total) return;
+  const int64_t jl = idx / g.m;
+  const int64_t col = idx - jl * g.m;
+  const int64_t pc = col / W;
+  const int cw = (int)(col - pc * W);
+  const int64_t lo = pc * g.C, hi = lo + g.C;  // tile range of panel pc
+  int64_t cta = lo * g.G / g.T;
+  if (cta > 0) --cta;
+  while (cta < g.G && (cta + 1) * g.T / g.G <= lo) ++cta;
+  const Tc* part = static_cast<const Tc*>(g.part);
+  Tc s = Tc(0);
+  for (; cta < g.G && cta * g.T / g.G < hi; ++cta)
+    s += part[((cta + pc) * g.jn + jl) * W + cw];
+  out[(g.j0 + jl) * ldo + col] = (Tout)(s * scale);
+}
+
+// Direct kernel for tiny blocks (r below the smallest chunk): each thread
+// forms one output entry as the explicit +-1 combination of its column.
+template <typename Tin, typename Tc, typename Tout>
+__global__ void __launch_bounds__(256) k_sketch_small_r(SketchArgs g, Tout* __restrict__ out,
+                                                        int64_t ldo, Tc scale) {
+  constexpr int JT = 8, CT = 32;
+  __shared__ uint64_t s_dw;
+  __shared__ uint64_t s_dtw[2];
+  const int cw = threadIdx.x % CT;
+  const int jt = threadIdx.x / CT;
+  const int64_t col = (int64_t)blockIdx.x * CT + cw;
+  const int64_t jbase = g.j0 + (int64_t)blockIdx.y * JT;
+  const int64_t j = jbase + jt;
+  const bool ok = col < g.m && j < g.j0 + g.jn;
+  const uint64_t s = ok ? (sample_word(g.seed, (uint64_t)j) & (uint64_t)(g.r - 1)) : 0;
+  const Tin* __restrict__ A = static_cast<const Tin*>(g.A);
+  Tc acc = Tc(0);
+  for (int64_t i = 0; i < g.p; ++i) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_dw = sign_word(g.seed, kStreamD, (uint64_t)i, 0);
+    if (threadIdx.x == 32) s_dtw[0] = sign_word(g.seed, kStreamDt, (uint64_t)i, (uint64_t)(jbase >> 6));
+    if (threadIdx.x == 64)
+      s_dtw[1] = sign_word(g.seed, kStreamDt, (uint64_t)i, (uint64_t)((jbase + JT - 1) >> 6));
+    __syncthreads();
+    const int64_t rows_i = min(g.rb, g.n - i * g.rb);
+    if (!ok || rows_i <= 0) continue;
+    Tc part = Tc(0);
+    for (int64_t k = 0; k < rows_i; ++k) {
+      const Tc x = load_as<Tc>(A + (i * g.rb + k) * g.lda + col);
+      const uint32_t neg = (uint32_t)((__popcll((unsigned long long)(s & (uint64_t)k)) +
+                                       (int)((s_dw >> k) & 1ull)) & 1);
+      part += flip(x, neg);
+    }
+    const uint64_t dtw = ((j >> 6) == (jbase >> 6)) ? s_dtw[0] : s_dtw[1];
+    acc += flip(part, (uint32_t)((dtw >> (j & 63)) & 1ull));
+  }
+  if (ok) out[j * ldo + col] = (Tout)(acc * scale);
+}
+
+}  // namespace bsrht

@@ -1,0 +1,77 @@
+"""The C-ABI library loads and exports every symbol include/bsrht.h declares;
+host-side validation and workspace queries (no GPU work)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bsrht.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bsrht_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("bsrht_sketch", "bsrht_rsvd", "bsrht_nystrom", "bsrht_strerror"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2210_11295_gb300 as b
+    lib = ctypes.CDLL(b.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_version():
+    import paper_2210_11295_gb300 as b
+    assert b.strerror(0) == "success"
+    assert "invalid" in b.strerror(-22)
+    assert b.version().count(".") == 2
+
+
+@pytest.mark.parametrize("n,m,p,l", [(0, 4, 1, 1), (8, 4, 0, 2), (8, 4, 9, 2), (8, 4, 2, 9), (8, 4, 2, 0)])
+def test_sketch_rejects_bad_sizes(n, m, p, l):
+    import paper_2210_11295_gb300 as b
+    from paper_2210_11295_gb300 import _binding as bb
+    o = bb.Opts()
+    b.lib.bsrht_opts_init(ctypes.byref(o))
+    o.dtype = bb.F32
+    out = ctypes.c_size_t(0)
+    st = b.lib.bsrht_sketch_workspace(n, m, p, l, ctypes.byref(o), ctypes.byref(out))
+    assert st == bb.BSRHT_EINVAL
+    # The launch path validates before touching the device.
+    st = b.lib.bsrht_sketch(ctypes.c_void_p(16), n, m, p, l, 0, ctypes.c_void_p(16), ctypes.byref(o))
+    assert st == bb.BSRHT_EINVAL
+
+
+def test_sketch_rejects_null_and_bad_stride():
+    import paper_2210_11295_gb300 as b
+    from paper_2210_11295_gb300 import _binding as bb
+    o = bb.Opts()
+    b.lib.bsrht_opts_init(ctypes.byref(o))
+    o.dtype = bb.F64
+    assert b.lib.bsrht_sketch(None, 64, 4, 2, 8, 0, ctypes.c_void_p(16), ctypes.byref(o)) == bb.BSRHT_EINVAL
+    o.lda = 3  # lda < m
+    assert b.lib.bsrht_sketch(ctypes.c_void_p(16), 64, 4, 2, 8, 0, ctypes.c_void_p(16),
+                              ctypes.byref(o)) == bb.BSRHT_EINVAL
+    o.lda = 0
+    o.dtype = 7
+    assert b.lib.bsrht_sketch(ctypes.c_void_p(16), 64, 4, 2, 8, 0, ctypes.c_void_p(16),
+                              ctypes.byref(o)) == bb.BSRHT_EINVAL
+
+
+def test_workspace_query_scales():
+    import torch
+    import paper_2210_11295_gb300 as b
+    w1 = b.bsrht_sketch_workspace(1 << 20, 4096, 4, 512, torch.float32)
+    w2 = b.bsrht_sketch_workspace(1 << 20, 4096, 4, 512, torch.float64)
+    assert 0 < w1 < 64 << 20 and 0 < w2 < 128 << 20
+    # Tiny blocks take the direct path, which needs no scratch.
+    assert b.bsrht_sketch_workspace(64, 8, 64, 16, torch.float32) == 0
