@@ -1,0 +1,602 @@
+// Dense linear algebra for the low-rank drivers (device kernels + launchers).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "dla.cuh"
+#include "gemm.cuh"
+#include "sketch.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace bsrht {
+
+#define DLA_LAUNCH_CHECK()                       \
+  do {                                           \
+    if (cudaGetLastError() != cudaSuccess) return BSRHT_ECUDA; \
+  } while (0)
+
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------ GEMM
+namespace {
+
+template <typename TA, typename TB, typename TC, typename Tacc, int TM>
+int gemm_launch(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                bool a_trans, const void* B, int64_t ldb, void* C, int64_t ldc, double alpha, double beta,
+                bool tri_b, bool gram) {
+  constexpr int BM = 16 * TM, BN = 16 * TM, BK = 8;
+  GemmArgs g;
+  g.A = A;
+  g.B = B;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.lda = lda;
+  g.ldb = ldb;
+  g.ldc = ldc;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.a_trans = a_trans ? 1 : 0;
+  g.tri_b = tri_b ? 1 : 0;
+  g.upper_c = gram ? 1 : 0;
+  const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  const int64_t tiles = gram ? tm * (tm + 1) / 2 : tm * tn;
+  int splits = 1;
+  const int64_t target = 2 * (int64_t)num_sms();
+  if (tiles < target && K > 64 * BK) {
+    splits = (int)std::min<int64_t>((target + tiles - 1) / tiles, K / (32 * BK));
+    splits = std::max(1, std::min(splits, 64));
+  }
+  dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)splits);
+  if (splits > 1 || gram) {
+    Tacc* P = static_cast<Tacc*>(ar.take(sizeof(Tacc) * (size_t)splits * M * N));
+    if (!ar.ok()) return BSRHT_ENOMEM;
+    if (ar.measure) return BSRHT_OK;
+    g.C = P;
+    g.splits = splits;
+    k_gemm<TA, TB, Tacc, Tacc, TM, TM, BK><<<grid, 256, 0, d.s>>>(g);
+    DLA_LAUNCH_CHECK();
+    k_gemm_splitk_reduce<Tacc, TC><<<blocks_for(M * N, 256), 256, 0, d.s>>>(
+        P, static_cast<TC*>(C), M, N, ldc, splits, alpha, gram ? 1 : 0, BM, BN);
+    DLA_LAUNCH_CHECK();
+    note_launches(2);
+    return BSRHT_OK;
+  }
+  if (ar.measure) return BSRHT_OK;
+  g.C = C;
+  g.splits = 1;
+  k_gemm<TA, TB, TC, Tacc, TM, TM, BK><<<grid, 256, 0, d.s>>>(g);
+  DLA_LAUNCH_CHECK();
+  note_launches(1);
+  return BSRHT_OK;
+}
+
+}  // namespace
+
+int gemm(const Dla& d, Arena& ar, DT ta, DT tb, DT tc, bool acc64, int64_t M, int64_t N, int64_t K,
+         const void* A, int64_t lda, bool a_trans, const void* B, int64_t ldb, void* C, int64_t ldc,
+         double alpha, double beta, bool tri_b, bool gram) {
+  if (M <= 0 || N <= 0) return BSRHT_OK;
+  if ((gram) && beta != 0.0) return BSRHT_EINVAL;
+  if (acc64) {
+    if (ta == DT::F64 && tb == DT::F64 && tc == DT::F64)
+      return gemm_launch<double, double, double, double, 4>(d, ar, M, N, K, A, lda, a_trans, B, ldb, C, ldc,
+                                                            alpha, beta, tri_b, gram);
+    return BSRHT_EUNSUP;
+  }
+  if (tb != DT::F32) return BSRHT_EUNSUP;
+#define GEMM32(TAT, TCT)                                                                                   \
+  return gemm_launch<TAT, float, TCT, float, 8>(d, ar, M, N, K, A, lda, a_trans, B, ldb, C, ldc, alpha, beta, \
+                                                tri_b, gram)
+  if (tc == DT::F32) {
+    if (ta == DT::F32) GEMM32(float, float);
+    if (ta == DT::BF16) GEMM32(__nv_bfloat16, float);
+    if (ta == DT::F16) GEMM32(__half, float);
+  } else if (tc == DT::F64) {
+    if (ta == DT::F32) GEMM32(float, double);
+  }
+#undef GEMM32
+  return BSRHT_EUNSUP;
+}
+
+// ------------------------------------------------------------ Cholesky
+constexpr int kNB = 32;
+
+__global__ void k_chol_diag(double* g, int64_t l, int64_t k0, int nb, int* status) {
+  __shared__ double a[kNB][kNB + 1];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    a[i][j] = (j <= i) ? g[(k0 + i) * l + k0 + j] : 0.0;
+  }
+  for (int j = 0; j < nb; ++j) {
+    __syncthreads();
+    if (tid == 0) {
+      double dj = a[j][j];
+      if (!(dj > 0.0)) {
+        atomicOr(status, kStatusNotPD);
+        dj = 1.0;
+      }
+      a[j][j] = sqrt(dj);
+    }
+    __syncthreads();
+    const double piv = a[j][j];
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) a[i][j] /= piv;
+    __syncthreads();
+    const int rem = nb - j - 1;
+    for (int e = tid; e < rem * rem; e += blockDim.x) {
+      const int i = j + 1 + e / rem, c = j + 1 + e % rem;
+      if (c <= i) a[i][c] -= a[i][j] * a[c][j];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    g[(k0 + i) * l + k0 + j] = (j <= i) ? a[i][j] : 0.0;
+  }
+}
+
+// Rows below the diagonal block: L[i, k0:k0+nb] = A[i, k0:k0+nb] L_kk^-T.
+__global__ void k_chol_panel(double* g, int64_t l, int64_t k0, int nb) {
+  __shared__ double lkk[kNB][kNB + 1];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    lkk[i][j] = g[(k0 + i) * l + k0 + j];
+  }
+  __syncthreads();
+  const int64_t i = k0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= l) return;
+  double x[kNB];
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) x[c] = c < nb ? g[i * l + k0 + c] : 0.0;
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) {
+    if (c < nb) {
+      double v = x[c];
+#pragma unroll
+      for (int e = 0; e < kNB; ++e)
+        if (e < c) v -= x[e] * lkk[c][e];
+      x[c] = v / lkk[c][c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kNB; ++c)
+    if (c < nb) g[i * l + k0 + c] = x[c];
+}
+
+// Trailing update of the lower triangle: A[i][j] -= sum_c L[i][k0+c] L[j][k0+c].
+__global__ void k_chol_update(double* g, int64_t l, int64_t k0, int nb) {
+  __shared__ double li[32][kNB + 1];
+  __shared__ double lj[32][kNB + 1];
+  const int64_t t0 = k0 + nb;
+  const int64_t bi = t0 + (int64_t)blockIdx.y * 32, bj = t0 + (int64_t)blockIdx.x * 32;
+  if (bj > bi) return;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8 threads
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t ri = bi + r, rj = bj + r;
+    li[r][tx] = (ri < l && tx < nb) ? g[ri * l + k0 + tx] : 0.0;
+    lj[r][tx] = (rj < l && tx < nb) ? g[rj * l + k0 + tx] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = bi + r, j = bj + tx;
+    if (i >= l || j >= l || j > i) continue;
+    double s = 0.0;
+#pragma unroll 8
+    for (int c = 0; c < nb; ++c) s += li[r][c] * lj[tx][c];
+    g[i * l + j] -= s;
+  }
+}
+
+__global__ void k_zero_upper(double* g, int64_t l) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= l * l) return;
+  const int64_t i = idx / l, j = idx % l;
+  if (j > i) g[idx] = 0.0;
+}
+
+int cholesky(const Dla& d, double* g, int64_t l) {
+  int launches = 0;
+  for (int64_t k0 = 0; k0 < l; k0 += kNB) {
+    const int nb = (int)std::min<int64_t>(kNB, l - k0);
+    k_chol_diag<<<1, 256, 0, d.s>>>(g, l, k0, nb, d.status);
+    DLA_LAUNCH_CHECK();
+    const int64_t below = l - k0 - nb;
+    launches += 1;
+    if (below > 0) {
+      k_chol_panel<<<blocks_for(below, 128), 128, 0, d.s>>>(g, l, k0, nb);
+      DLA_LAUNCH_CHECK();
+      const unsigned tb = (unsigned)((below + 31) / 32);
+      k_chol_update<<<dim3(tb, tb), 256, 0, d.s>>>(g, l, k0, nb);
+      DLA_LAUNCH_CHECK();
+      launches += 2;
+    }
+  }
+  k_zero_upper<<<blocks_for(l * l, 256), 256, 0, d.s>>>(g, l);
+  DLA_LAUNCH_CHECK();
+  note_launches(launches + 1);
+  return BSRHT_OK;
+}
+
+// ------------------------------------------------------ triangular inverse
+__global__ void k_transpose_sq(const double* in, double* out, int64_t l) {
+  __shared__ double t[32][33];
+  const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = by + r, j = bx + tx;
+    t[r][tx] = (i < l && j < l) ? in[i * l + j] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = bx + r, j = by + tx;
+    if (i < l && j < l) out[i * l + j] = t[tx][r];
+  }
+}
+
+// Column j of L^-1 by forward substitution; written as row j of R^-1 = L^-T.
+// LT = L^T (row k of LT is column k of L).
+__global__ void k_trinv(const double* __restrict__ LT, double* __restrict__ Rinv, int64_t l) {
+  extern __shared__ double x[];
+  const int64_t j = blockIdx.x;
+  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) x[i] = (i == j) ? 1.0 : 0.0;
+  for (int64_t k = j; k < l; ++k) {
+    __syncthreads();
+    if (threadIdx.x == 0) x[k] /= LT[k * l + k];
+    __syncthreads();
+    const double xk = x[k];
+    for (int64_t i = k + 1 + threadIdx.x; i < l; i += blockDim.x) x[i] -= LT[k * l + i] * xk;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) Rinv[j * l + i] = x[i];
+}
+
+int tri_inverse(const Dla& d, const double* L, double* LT, double* Rinv, int64_t l) {
+  const unsigned t = (unsigned)((l + 31) / 32);
+  k_transpose_sq<<<dim3(t, t), 256, 0, d.s>>>(L, LT, l);
+  DLA_LAUNCH_CHECK();
+  k_trinv<<<(unsigned)l, 256, sizeof(double) * l, d.s>>>(LT, Rinv, l);
+  DLA_LAUNCH_CHECK();
+  note_launches(2);
+  return BSRHT_OK;
+}
+
+// ------------------------------------------------------- Jacobi SVD
+__device__ __forceinline__ int rr_player(int pos, int round, int lp) {
+  if (pos == 0) return 0;
+  return 1 + (pos - 1 + round) % (lp - 1);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One-sided (Hestenes) Jacobi on the columns of M with round-robin pairs;
+// one warp per column pair, a grid-wide barrier between rounds.
+__global__ void k_jacobi(double* __restrict__ M, double* __restrict__ V, int l, int lp, double tol,
+                         int max_sweeps, int* __restrict__ rot_counts, int* __restrict__ status) {
+  cg::grid_group grid = cg::this_grid();
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int round = 0; round < lp - 1; ++round) {
+      for (int k = warp; k < lp / 2; k += nwarps) {
+        int p = rr_player(k, round, lp), q = rr_player(lp - 1 - k, round, lp);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        if (q >= l) continue;  // padding column
+        double* a = M + (int64_t)p * l;
+        double* b = M + (int64_t)q * l;
+        double al0 = 0, al1 = 0, be0 = 0, be1 = 0, ga0 = 0, ga1 = 0;
+        int i = lane;
+        for (; i + 32 < l; i += 64) {
+          const double x0 = a[i], y0 = b[i], x1 = a[i + 32], y1 = b[i + 32];
+          al0 = fma(x0, x0, al0);
+          be0 = fma(y0, y0, be0);
+          ga0 = fma(x0, y0, ga0);
+          al1 = fma(x1, x1, al1);
+          be1 = fma(y1, y1, be1);
+          ga1 = fma(x1, y1, ga1);
+        }
+        if (i < l) {
+          const double x0 = a[i], y0 = b[i];
+          al0 = fma(x0, x0, al0);
+          be0 = fma(y0, y0, be0);
+          ga0 = fma(x0, y0, ga0);
+        }
+        const double alpha = warp_sum(al0 + al1), beta = warp_sum(be0 + be1), gamma = warp_sum(ga0 + ga1);
+        if (gamma == 0.0 || !(fabs(gamma) > tol * sqrt(alpha * beta))) continue;
+        const double zeta = (beta - alpha) / (2.0 * gamma);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        for (int r = lane; r < l; r += 32) {
+          const double x = a[r], y = b[r];
+          a[r] = c * x - s * y;
+          b[r] = s * x + c * y;
+        }
+        double* va = V + (int64_t)p * l;
+        double* vb = V + (int64_t)q * l;
+        for (int r = lane; r < l; r += 32) {
+          const double x = va[r], y = vb[r];
+          va[r] = c * x - s * y;
+          vb[r] = s * x + c * y;
+        }
+        if (lane == 0) atomicAdd(&rot_counts[sweep], 1);
+      }
+      grid.sync();
+    }
+    if (*((volatile int*)&rot_counts[sweep]) == 0) break;
+  }
+  if (sweep >= max_sweeps && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusNoConv);
+}
+
+__global__ void k_init_identity_cols(double* V, int64_t l) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < l * l) V[idx] = (idx / l == idx % l) ? 1.0 : 0.0;
+}
+
+__global__ void k_col_norms(const double* __restrict__ M, double* __restrict__ sigma, int64_t l) {
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (c >= l) return;
+  double s = 0.0;
+  for (int64_t i = lane; i < l; i += 32) s = fma(M[c * l + i], M[c * l + i], s);
+  s = warp_sum(s);
+  if (lane == 0) sigma[c] = sqrt(s);
+}
+
+// perm[rank] = c with ranks by descending sigma (ties: lower index first).
+__global__ void k_rank_desc(const double* __restrict__ sigma, int* __restrict__ perm, int64_t l) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= l) return;
+  const double v = sigma[c];
+  int64_t rank = 0;
+  for (int64_t e = 0; e < l; ++e) {
+    const double w = sigma[e];
+    rank += (w > v) || (w == v && e < c);
+  }
+  perm[rank] = (int)c;
+}
+
+// U[i][r] = M[perm[r]][i] / sigma, Vout[i][r] = Vcols[perm[r]][i], sig_out[r].
+__global__ void k_svd_finish(const double* __restrict__ M, const double* __restrict__ Vc,
+                             const double* __restrict__ sigma, const int* __restrict__ perm,
+                             double* __restrict__ U, double* __restrict__ Vout, double* __restrict__ sig_out,
+                             int64_t l) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= l * l) return;
+  const int64_t i = idx / l, r = idx % l;
+  const int c = perm[r];
+  const double s = sigma[c];
+  U[i * l + r] = s > 0.0 ? M[(int64_t)c * l + i] / s : 0.0;
+  Vout[i * l + r] = Vc[(int64_t)c * l + i];
+  if (i == 0) sig_out[r] = s;
+}
+
+int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout) {
+  const int max_sweeps = 40;
+  double* Vc = static_cast<double*>(ar.take(sizeof(double) * l * l));
+  double* sig = static_cast<double*>(ar.take(sizeof(double) * l));
+  int* perm = static_cast<int*>(ar.take(sizeof(int) * l));
+  int* rot = static_cast<int*>(ar.take(sizeof(int) * max_sweeps));
+  if (!ar.ok()) return BSRHT_ENOMEM;
+  if (ar.measure) return BSRHT_OK;
+  BSRHT_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(int) * max_sweeps, d.s));
+  k_init_identity_cols<<<blocks_for(l * l, 256), 256, 0, d.s>>>(Vc, l);
+  DLA_LAUNCH_CHECK();
+  int li = (int)l, lp = (int)(l + (l & 1));
+  double tol = 1e-15;
+  int dev = 0, occ = 0;
+  BSRHT_CUDA_TRY(cudaGetDevice(&dev));
+  const int threads = 256;
+  BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi, threads, 0));
+  const int pairs = lp / 2;
+  int blocks = std::max(1, std::min((pairs + threads / 32 - 1) / (threads / 32), num_sms() * std::max(occ, 1)));
+  int msw = max_sweeps;
+  void* args[] = {&colsM, &Vc, &li, &lp, &tol, &msw, &rot, (void*)&d.status};
+  if (l > 1) {
+    BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(blocks), dim3(threads), args, 0, d.s));
+  }
+  k_col_norms<<<blocks_for(l, 8), 256, 0, d.s>>>(colsM, sig, l);
+  DLA_LAUNCH_CHECK();
+  k_rank_desc<<<blocks_for(l, 256), 256, 0, d.s>>>(sig, perm, l);
+  DLA_LAUNCH_CHECK();
+  k_svd_finish<<<blocks_for(l * l, 256), 256, 0, d.s>>>(colsM, Vc, sig, perm, U, Vout, sigma, l);
+  DLA_LAUNCH_CHECK();
+  note_launches(l > 1 ? 5 : 4);
+  return BSRHT_OK;
+}
+
+// ------------------------------------------------------------ helpers
+template <typename TI, typename TO>
+__global__ void k_transpose_cast(const TI* __restrict__ in, int64_t rows, int64_t cols, int64_t ldin,
+                                 TO* __restrict__ out, int64_t ldout) {
+  __shared__ double t[32][33];
+  const int64_t bc = (int64_t)blockIdx.x * 32, br = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = br + r, j = bc + tx;
+    t[r][tx] = (i < rows && j < cols) ? (double)Elem<TI>::to_f64(in[i * ldin + j]) : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t j = bc + r, i = br + tx;
+    if (i < rows && j < cols) out[j * ldout + i] = (TO)t[tx][r];
+  }
+}
+
+int transpose_cast(const Dla& d, DT tin, const void* in, int64_t rows, int64_t cols, int64_t ldin, DT tout,
+                   void* out, int64_t ldout) {
+  if (rows <= 0 || cols <= 0) return BSRHT_OK;
+  dim3 grid(blocks_for(cols, 32), blocks_for(rows, 32));
+#define TC_CASE(TIT, TOT)                                                                                  \
+  k_transpose_cast<TIT, TOT><<<grid, 256, 0, d.s>>>(static_cast<const TIT*>(in), rows, cols, ldin,         \
+                                                    static_cast<TOT*>(out), ldout)
+  if (tin == DT::F64 && tout == DT::F64) TC_CASE(double, double);
+  else if (tin == DT::F32 && tout == DT::F64) TC_CASE(float, double);
+  else if (tin == DT::F32 && tout == DT::F32) TC_CASE(float, float);
+  else if (tin == DT::F64 && tout == DT::F32) TC_CASE(double, float);
+  else return BSRHT_EUNSUP;
+#undef TC_CASE
+  DLA_LAUNCH_CHECK();
+  note_launches(1);
+  return BSRHT_OK;
+}
+
+template <typename TI, typename TO>
+__global__ void k_cast(const TI* __restrict__ in, TO* __restrict__ out, int64_t count) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < count) out[idx] = (TO)in[idx];
+}
+
+int cast_copy(const Dla& d, DT tin, const void* in, DT tout, void* out, int64_t count) {
+  if (count <= 0) return BSRHT_OK;
+  if (tin == DT::F64 && tout == DT::F32)
+    k_cast<double, float><<<blocks_for(count, 256), 256, 0, d.s>>>(static_cast<const double*>(in),
+                                                                    static_cast<float*>(out), count);
+  else if (tin == DT::F32 && tout == DT::F64)
+    k_cast<float, double><<<blocks_for(count, 256), 256, 0, d.s>>>(static_cast<const float*>(in),
+                                                                    static_cast<double*>(out), count);
+  else if (tin == DT::F64 && tout == DT::F64)
+    k_cast<double, double><<<blocks_for(count, 256), 256, 0, d.s>>>(static_cast<const double*>(in),
+                                                                     static_cast<double*>(out), count);
+  else
+    return BSRHT_EUNSUP;
+  DLA_LAUNCH_CHECK();
+  note_launches(1);
+  return BSRHT_OK;
+}
+
+int transpose_lower_to_upper(const Dla& d, const double* Li, double* R, int64_t l) {
+  const unsigned t = (unsigned)((l + 31) / 32);
+  k_transpose_sq<<<dim3(t, t), 256, 0, d.s>>>(Li, R, l);
+  DLA_LAUNCH_CHECK();
+  note_launches(1);
+  return BSRHT_OK;
+}
+
+__global__ void k_scale_cols(double* X, int64_t rows, int64_t cols, int64_t ld, const double* sc, int inv) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols) return;
+  const int64_t i = idx / cols, j = idx % cols;
+  const double s = sc[j];
+  X[i * ld + j] = inv ? (s != 0.0 ? X[i * ld + j] / s : 0.0) : X[i * ld + j] * s;
+}
+
+int scale_columns(const Dla& d, double* X, int64_t rows, int64_t cols, int64_t ld, const double* scale,
+                  bool invert) {
+  if (rows * cols <= 0) return BSRHT_OK;
+  k_scale_cols<<<blocks_for(rows * cols, 256), 256, 0, d.s>>>(X, rows, cols, ld, scale, invert ? 1 : 0);
+  DLA_LAUNCH_CHECK();
+  note_launches(1);
+  return BSRHT_OK;
+}
+
+// Column argmax of |U| per row chunk: partial (value, index) per chunk.
+__global__ void k_colargmax_partial(const double* __restrict__ U, int64_t n, int64_t k, int64_t rows_per,
+                                    double* __restrict__ pv, int64_t* __restrict__ pi) {
+  const int64_t c = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+  double best = -1.0;
+  int64_t bi = r0;
+  for (int64_t i = r0; i < r1; ++i) {
+    const double v = fabs(U[i * k + c]);
+    if (v > best) {
+      best = v;
+      bi = i;
+    }
+  }
+  pv[(int64_t)blockIdx.x * k + c] = best;
+  pi[(int64_t)blockIdx.x * k + c] = bi;
+}
+
+__global__ void k_colargmax_final(const double* __restrict__ U, int64_t k, int nchunks, const double* pv,
+                                  const int64_t* pi, double* __restrict__ sgn) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  double best = -1.0;
+  int64_t bi = 0;
+  for (int b = 0; b < nchunks; ++b) {
+    const double v = pv[(int64_t)b * k + c];
+    if (v > best) {
+      best = v;
+      bi = pi[(int64_t)b * k + c];
+    }
+  }
+  sgn[c] = (U[bi * k + c] < 0.0) ? -1.0 : 1.0;
+}
+
+int sign_normalize(const Dla& d, Arena& ar, double* U, int64_t n, int64_t k, double* V, int64_t m) {
+  const int nchunks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, n / 256));
+  const int64_t rows_per = (n + nchunks - 1) / nchunks;
+  double* pv = static_cast<double*>(ar.take(sizeof(double) * nchunks * k));
+  int64_t* pi = static_cast<int64_t*>(ar.take(sizeof(int64_t) * nchunks * k));
+  double* sg = static_cast<double*>(ar.take(sizeof(double) * k));
+  if (!ar.ok()) return BSRHT_ENOMEM;
+  if (ar.measure) return BSRHT_OK;
+  const int tb = (int)std::min<int64_t>(256, k);
+  k_colargmax_partial<<<dim3(nchunks, blocks_for(k, tb)), tb, 0, d.s>>>(U, n, k, rows_per, pv, pi);
+  DLA_LAUNCH_CHECK();
+  k_colargmax_final<<<blocks_for(k, 128), 128, 0, d.s>>>(U, k, nchunks, pv, pi, sg);
+  DLA_LAUNCH_CHECK();
+  note_launches(2);
+  int st = scale_columns(d, U, n, k, k, sg, false);
+  if (st != BSRHT_OK) return st;
+  if (V) st = scale_columns(d, V, m, k, k, sg, false);
+  return st;
+}
+
+template <typename T>
+__global__ void k_sumsq_partial(const T* __restrict__ X, int64_t count, double* __restrict__ part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)Elem<T>::to_f64(X[i]);
+    s = fma(v, v, s);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_sqrt(const double* part, int count, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < count; ++i) s += part[i];
+    *out = sqrt(s);
+  }
+}
+
+int frob_norm(const Dla& d, Arena& ar, DT t, const void* X, int64_t count, double* out) {
+  const int nb = 1024;
+  double* part = static_cast<double*>(ar.take(sizeof(double) * nb));
+  if (!ar.ok()) return BSRHT_ENOMEM;
+  if (ar.measure) return BSRHT_OK;
+  if (t == DT::F64)
+    k_sumsq_partial<double><<<nb, 256, 0, d.s>>>(static_cast<const double*>(X), count, part);
+  else if (t == DT::F32)
+    k_sumsq_partial<float><<<nb, 256, 0, d.s>>>(static_cast<const float*>(X), count, part);
+  else
+    return BSRHT_EUNSUP;
+  DLA_LAUNCH_CHECK();
+  k_sum_sqrt<<<1, 32, 0, d.s>>>(part, nb, out);
+  DLA_LAUNCH_CHECK();
+  note_launches(2);
+  return BSRHT_OK;
+}
+
+}  // namespace bsrht

@@ -1,0 +1,81 @@
+// Dense linear algebra for the low-rank drivers (host interface).
+//
+// Tall-skinny products run on the tiled CUDA-core GEMM (gemm.cuh); the small
+// l x l factorizations (Cholesky, triangular inverse, one-sided Jacobi SVD)
+// run in FP64 on the device.  Everything is enqueued on one stream; scratch
+// comes from a caller-provided arena.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace bsrht {
+
+enum class DT { F64, F32, BF16, F16 };
+
+inline size_t dt_size(DT t) { return t == DT::F64 ? 8 : (t == DT::F32 ? 4 : 2); }
+
+// Bump allocator over a caller buffer (256-byte aligned slices).
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, used = 0, high = 0;
+  bool measure = false;  // only count bytes (no pointers handed out)
+  void* take(size_t bytes) {
+    used = (used + 255) / 256 * 256;
+    void* p = measure ? nullptr : base + used;
+    used += bytes;
+    if (used > high) high = used;
+    return p;
+  }
+  // Scratch taken after mark() may be handed out again after release():
+  // every user is stream-ordered on the same stream.
+  size_t mark() const { return used; }
+  void release(size_t m) { used = m; }
+  bool ok() const { return measure || used <= cap; }
+};
+
+struct Dla {
+  cudaStream_t s;
+  int* status;  // device int: 0 ok, else first failure code (see kStatus*)
+};
+
+constexpr int kStatusNotPD = 1;
+constexpr int kStatusNoConv = 2;
+
+// C[M x N] = alpha * op(A) B + beta C.  op(A) = A (M x K, lda) or A^T (A is
+// K x M, lda).  B is K x N (ldb).  Accumulation in FP64 when acc64, else
+// FP32.  tri_b: B upper triangular.  gram: C is the symmetric M x M product
+// A^T A (a_trans, B == A), only the upper tiles are formed and mirrored.
+// splitk scratch is taken from the arena when needed.
+int gemm(const Dla& d, Arena& ar, DT ta, DT tb, DT tc, bool acc64, int64_t M, int64_t N, int64_t K,
+         const void* A, int64_t lda, bool a_trans, const void* B, int64_t ldb, void* C, int64_t ldc,
+         double alpha, double beta, bool tri_b, bool gram);
+
+// Lower Cholesky factor L (G = L L^T) of the symmetric l x l FP64 matrix g
+// (lower triangle read; ldg = l); L overwrites g's lower triangle, the strict
+// upper triangle is zeroed.  Sets *status |= kStatusNotPD on a non-positive
+// pivot.
+int cholesky(const Dla& d, double* g, int64_t l);
+
+// Rinv = L^-T (upper triangular, row-major) for the lower-triangular l x l
+// L; LT receives L^T (the upper Cholesky factor R = L^T).
+int tri_inverse(const Dla& d, const double* L, double* LT, double* Rinv, int64_t l);
+
+// One-sided Jacobi SVD of the l x l FP64 matrix given by its COLUMNS:
+// colsM[c*l + i] = M[i][c].  On return colsM holds U Sigma (columns),
+// colsV[c*l + i] = V[i][c]; sigma[c] = ||U Sigma e_c||.  Columns are sorted
+// by descending sigma into U (l x l row-major, U[i][c]) and Vout (row-major).
+int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout);
+
+// Elementwise helpers.
+int transpose_cast(const Dla& d, DT tin, const void* in, int64_t rows, int64_t cols, int64_t ldin, DT tout,
+                   void* out, int64_t ldout);  // out[c][r] = in[r][c]
+int cast_copy(const Dla& d, DT tin, const void* in, DT tout, void* out, int64_t count);
+int transpose_lower_to_upper(const Dla& d, const double* Li, double* R, int64_t l);  // R = Li^T
+int scale_columns(const Dla& d, double* X, int64_t rows, int64_t cols, int64_t ld, const double* scale,
+                  bool invert);
+int sign_normalize(const Dla& d, Arena& ar, double* U, int64_t n, int64_t k, double* V, int64_t m);
+int frob_norm(const Dla& d, Arena& ar, DT t, const void* X, int64_t count, double* out);
+
+}  // namespace bsrht
