@@ -110,6 +110,32 @@ int bsrht_sketch_workspace(int64_t n, int64_t m, int32_t p, int64_t l,
                            const bsrht_opts* opts, size_t* bytes);
 
 /*
+ * bsrht_sketch_noalloc - bsrht_sketch for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this is a deployment aid.
+ * Some callers may not call cudaMalloc at all: a host whose own caching
+ * allocator must account for every device byte, a loop that may not block on
+ * the implicit device synchronisation an allocation can cause, or a plug-in
+ * whose host application owns all device memory.  They still pass A and out
+ * exactly as for bsrht_sketch (same arguments, same result bits), but the
+ * sketch's scratch comes from one fixed 32 MiB array that the library keeps
+ * in device memory on every device that loads it, until the process exits.
+ *   - opts->workspace is ignored; nothing is allocated or freed.
+ *   - Returns BSRHT_ENOMEM, with nothing enqueued, when the sizes need more
+ *     than 32 MiB of scratch (bsrht_sketch_workspace reports the need;
+ *     n = 2^20, m = 4096, l = 512 needs about 19 MB in FP32, 27 MB in FP64).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls on one device share the array: calls whose kernels overlap on
+ *     the GPU (other streams, other host threads) race and corrupt each
+ *     other's results, so serialise them on one stream.  The array keeps the
+ *     last call's contents; the sketch overwrites every slot it reads.
+ */
+int bsrht_sketch_noalloc(const void* A, int64_t n, int64_t m, int32_t p,
+                         int64_t l, uint64_t seed, void* out,
+                         const bsrht_opts* opts);
+
+/*
  * bsrht_rsvd - rank-k randomized SVD, Algorithm 1 of Sec. 3.1, on the sketch.
  *   A (n x m) ~ U diag(S) V^T with U n x k, S k (descending), V m x k, all
  *   double, U and V with orthonormal columns.  Requires 1 <= k <= l <= m and
