@@ -143,7 +143,10 @@ int bsrht_sketch_noalloc(const void* A, int64_t n, int64_t m, int32_t p,
  *   W = A Q (second pass over A, in the arithmetic of A: FP64 for F64, FP32
  *   otherwise); W = P R (CholeskyQR2); SVD of R^T (FP64 one-sided Jacobi);
  *   U = P V~_k, S = Sigma~_k, V = Q U~_k.  Each column of U is flipped so its
- *   largest-magnitude entry is positive (V gets the same flip).
+ *   largest-magnitude entry is positive (V gets the same flip).  When a tall
+ *   factor is numerically rank deficient (repeated rows of Omega, or rank(A)
+ *   < l) CholeskyQR2 is replaced by Householder QR (FP64, m up to 2^17) or by
+ *   an eigen-based basis completed with seeded random directions.
  *   Synchronises opts->stream to read the status of the small factorizations;
  *   returns BSRHT_ENOTPD if a Gram matrix is numerically singular,
  *   BSRHT_ENOCONV if the Jacobi SVD does not converge.
@@ -162,11 +165,13 @@ int bsrht_rsvd_workspace(int64_t n, int64_t m, int32_t k, int64_t l, int32_t p,
  *   A ~ U diag(Lambda) U^T with U n x k (orthonormal columns), Lambda k
  *   (descending, >= 0), both double.  Requires 1 <= k <= l <= n.
  *   Steps: Y = (Omega A)^T; shift nu = sqrt(n) 2^-52 ||Y||_F,
- *   Y_nu = Y + nu Omega^T; core = sym(Omega Y_nu); FP64 Cholesky C^T C =
- *   core (nu doubled up to 10 times on failure, Remark 3.1);
- *   Z = Y_nu C^-1; R factor of Z (CholeskyQR2); SVD R = U~ Sigma~ V~^T;
- *   U = Z V~_k Sigma~_k^-1; Lambda = max(Sigma~_k^2 - nu, 0).
- *   Synchronises opts->stream; BSRHT_ENOTPD if the core stays indefinite.
+ *   Y_nu = Y + nu Omega^T; core = sym(Omega Y_nu) and its Cholesky factor C
+ *   in FP64 (Remark 3.1); if the factorization fails or its squared pivots
+ *   fall below l*eps of the largest (eps of the arithmetic of A), C^-1 is
+ *   replaced by the SVD square root's pseudo-inverse (Remark 3.1);
+ *   Z = Y_nu C^-1; R factor of Z (CholeskyQR2, rank-robust); SVD
+ *   R = U~ Sigma~ V~^T; U = Z V~_k Sigma~_k^-1; Lambda = max(Sigma~_k^2 - nu, 0).
+ *   Synchronises opts->stream.
  */
 int bsrht_nystrom(const void* A, int64_t n, int32_t k, int64_t l, int32_t p,
                   uint64_t seed, double* U, double* Lambda,

@@ -16,8 +16,12 @@ Readings of the paper used here (each also listed with the design notes):
   the text mentions) is (Z V~_k) Sigma~_k^-1, so Z is used.
 * Remark 3.1 only says "shift as in Li et al."; the shift used is
   nu = sqrt(n) * 2^-52 * ||Y||_F, Y_nu = Y + nu Omega^T,
-  core = sym(Omega Y_nu), Lambda = max(Sigma~_k^2 - nu, 0); if the Cholesky
-  factorisation still fails, nu is doubled (at most 10 times).
+  core = sym(Omega Y_nu), Lambda = max(Sigma~_k^2 - nu, 0). The shift does not
+  help when Omega itself has repeated rows (sampling with replacement allows
+  them), so when the Cholesky factorisation fails or its squared pivots fall
+  below tau = l * 2^-52 of the largest, Remark 3.1's other remedy is used:
+  the SVD square root of the core, as a pseudo-inverse (eigenvalues below
+  tau * lambda_max dropped).
 * Cholesky convention: C upper triangular with C^T C = core, Z = Y C^-1.
 * Singular vectors are only defined up to sign: each column of U is flipped
   so its largest-magnitude entry (lowest index on ties) is positive, and the
@@ -91,39 +95,50 @@ def nystrom_shift(y: np.ndarray) -> float:
     return math.sqrt(y.shape[0]) * EPS64 * float(np.linalg.norm(y))
 
 
-def nystrom(a: np.ndarray, k: int, l: int, p: int, seed: int,
-            shift: bool = True, max_doublings: int = 10):
-    """Algorithm 2 (with the Z fix in step 6 and the shift of Remark 3.1).
+def nystrom(a: np.ndarray, k: int, l: int, p: int, seed: int, shift: bool = True,
+            unit_roundoff: float = EPS64):
+    """Algorithm 2 (with the Z fix in step 6 and the remedies of Remark 3.1).
 
     ``a`` is n x n symmetric PSD. Returns (U n x k, Lambda k, nu) with
-    A ~ U diag(Lambda) U^T.
+    A ~ U diag(Lambda) U^T. ``unit_roundoff`` sets the rank threshold
+    tau = l * unit_roundoff of Remark 3.1's SVD square root (the arithmetic
+    of the tall products decides which core directions are resolvable).
     """
     a = np.asarray(a, dtype=np.float64)
     n = a.shape[0]
     om = dense_omega(n, p, l, seed)
-    # Step 1: Y = A Omega^T (n x l).
+    # Step 1: Y = A Omega^T (n x l), shifted: Y_nu = Y + nu Omega^T.
     y = a @ om.T
     nu = nystrom_shift(y) if shift else 0.0
-    for _ in range(max_doublings + 1):
-        y_nu = y + nu * om.T
-        core = om @ y_nu
-        core = 0.5 * (core + core.T)
-        try:
-            # Step 2: Cholesky factor C (upper, C^T C = core).
-            c = sla.cholesky(core, lower=False)
-            break
-        except np.linalg.LinAlgError:
-            nu = 2.0 * nu if nu > 0 else EPS64 * float(np.linalg.norm(y))
-    else:
-        raise np.linalg.LinAlgError("core not positive definite after shifting")
-    # Step 3: Z = Y C^-1 (triangular solve from the right).
-    z = sla.solve_triangular(c, y_nu.T, trans="T", lower=False).T
+    y_nu = y + nu * om.T
+    core = om @ y_nu
+    core = 0.5 * (core + core.T)
+    # Step 2: Cholesky factor C (upper, C^T C = core), Step 3: Z = Y C^-1.
+    # Remark 3.1: when the core is numerically rank deficient (the factorization
+    # fails, or its pivots fall below tau of the largest), C^-1 is replaced by
+    # the SVD square root's pseudo-inverse V_r lambda_r^-1/2 (lambda <= tau
+    # lambda_max dropped).
+    tau = l * unit_roundoff
+    z = None
+    try:
+        c = sla.cholesky(core, lower=False)
+        piv = np.diag(c) ** 2
+        if piv.min() > tau * piv.max():
+            z = sla.solve_triangular(c, y_nu.T, trans="T", lower=False).T
+    except np.linalg.LinAlgError:
+        pass
+    if z is None:
+        lam_c, v_c = np.linalg.eigh(core)
+        keep = lam_c > tau * lam_c.max()
+        z = np.zeros_like(y_nu)
+        z[:, :int(keep.sum())] = y_nu @ (v_c[:, keep] / np.sqrt(lam_c[keep]))
     # Step 4: R factor of Z.
     rmat = np.linalg.qr(z, mode="r")
     # Step 5: SVD of R.
     _, sr, vrt = np.linalg.svd(rmat)
     # Step 6: U^ = (Z V~_k) Sigma~_k^-1.
-    u = (z @ vrt[:k].T) / sr[:k]
+    sk = sr[:k]
+    u = np.divide(z @ vrt[:k].T, sk, out=np.zeros((z.shape[0], k)), where=sk > 0)
     # Step 7: A ~ U^ Sigma~_k^2 U^^T, minus the shift.
     lam = np.maximum(sr[:k] ** 2 - nu, 0.0)
     u = sign_normalize(u)

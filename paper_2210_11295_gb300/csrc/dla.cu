@@ -84,6 +84,9 @@ int gemm(const Dla& d, Arena& ar, DT ta, DT tb, DT tc, bool acc64, int64_t M, in
     if (ta == DT::F64 && tb == DT::F64 && tc == DT::F64)
       return gemm_launch<double, double, double, double, 4>(d, ar, M, N, K, A, lda, a_trans, B, ldb, C, ldc,
                                                             alpha, beta, tri_b, gram);
+    if (ta == DT::F32 && tb == DT::F32 && tc == DT::F64)  // FP64 accumulation of FP32 data
+      return gemm_launch<float, float, double, double, 4>(d, ar, M, N, K, A, lda, a_trans, B, ldb, C, ldc, alpha,
+                                                          beta, tri_b, gram);
     return BSRHT_EUNSUP;
   }
   if (tb != DT::F32) return BSRHT_EUNSUP;
@@ -595,6 +598,134 @@ int frob_norm(const Dla& d, Arena& ar, DT t, const void* X, int64_t count, doubl
   DLA_LAUNCH_CHECK();
   k_sum_sqrt<<<1, 32, 0, d.s>>>(part, nb, out);
   DLA_LAUNCH_CHECK();
+  note_launches(2);
+  return BSRHT_OK;
+}
+
+}  // namespace bsrht
+
+namespace bsrht {
+
+// ------------------------------------------------ Householder QR (FP64)
+// Cooperative kernel: the rows of X are split into contiguous block ranges;
+// every column step needs grid-wide sums, taken as per-block partials that
+// every block then adds in block order (deterministic).
+__global__ void k_house_qr(double* __restrict__ X, int64_t rows, int64_t l, double* __restrict__ tau,
+                           double* __restrict__ part) {
+  cg::grid_group grid = cg::this_grid();
+  const int64_t nb = gridDim.x;
+  const int64_t per = (rows + nb - 1) / nb;
+  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(rows, r0 + per);
+  __shared__ double red[256];
+  __shared__ double s_beta, s_v0, s_tau;
+  for (int64_t j = 0; j < l; ++j) {
+    // (1) sum of squares of X[i][j], i > j, per block
+    double acc = 0.0;
+    for (int64_t i = max(r0, j + 1) + threadIdx.x; i < r1; i += blockDim.x) acc = fma(X[i * l + j], X[i * l + j], acc);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+    grid.sync();
+    // (2) reflector: every block derives the same scalars
+    if (threadIdx.x == 0) {
+      double sigma = 0.0;
+      for (int64_t b = 0; b < nb; ++b) sigma += part[b];
+      const double x0 = (j < rows) ? X[j * l + j] : 0.0;
+      if (sigma == 0.0 || j >= rows) {
+        s_beta = x0;
+        s_v0 = 1.0;
+        s_tau = 0.0;
+      } else {
+        const double alpha = sqrt(x0 * x0 + sigma);
+        const double beta = x0 <= 0.0 ? alpha : -alpha;
+        s_beta = beta;
+        s_v0 = x0 - beta;
+        s_tau = (beta - x0) / beta;
+      }
+    }
+    __syncthreads();
+    const double v0 = s_v0, tj = s_tau;
+    for (int64_t i = max(r0, j + 1) + threadIdx.x; i < r1; i += blockDim.x) X[i * l + j] /= v0;
+    grid.sync();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (j < rows) X[j * l + j] = s_beta;
+      tau[j] = tj;
+    }
+    // (3) w_c = v^T X[j:, c] for c > j, per block (v_j = 1 implicit)
+    for (int64_t c = j + 1 + threadIdx.x; c < l; c += blockDim.x) {
+      double w = 0.0;
+      if (j >= r0 && j < r1) w = X[j * l + c];
+      for (int64_t i = max(r0, j + 1); i < r1; ++i) w = fma(X[i * l + j], X[i * l + c], w);
+      part[(int64_t)blockIdx.x * l + c] = w;
+    }
+    grid.sync();
+    // (4) X[i][c] -= tau v_i w_c
+    if (tj != 0.0) {
+      for (int64_t c = j + 1 + threadIdx.x; c < l; c += blockDim.x) {
+        double w = 0.0;
+        for (int64_t b = 0; b < nb; ++b) w += part[b * l + c];
+        w *= tj;
+        if (j >= r0 && j < r1) X[j * l + c] -= w;
+        for (int64_t i = max(r0, j + 1); i < r1; ++i) X[i * l + c] -= X[i * l + j] * w;
+      }
+    }
+    grid.sync();
+  }
+}
+
+// Q = H_0 ... H_{l-1} [I; 0] by backward accumulation.
+__global__ void k_house_formq(const double* __restrict__ X, int64_t rows, int64_t l, const double* __restrict__ tau,
+                              double* __restrict__ Q, double* __restrict__ part) {
+  cg::grid_group grid = cg::this_grid();
+  const int64_t nb = gridDim.x;
+  const int64_t per = (rows + nb - 1) / nb;
+  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(rows, r0 + per);
+  for (int64_t i = r0; i < r1; ++i)
+    for (int64_t c = threadIdx.x; c < l; c += blockDim.x) Q[i * l + c] = (i == c) ? 1.0 : 0.0;
+  grid.sync();
+  for (int64_t j = min(l, rows) - 1; j >= 0; --j) {
+    const double tj = tau[j];
+    if (tj == 0.0) continue;  // uniform across the grid
+    for (int64_t c = j + threadIdx.x; c < l; c += blockDim.x) {
+      double w = 0.0;
+      if (j >= r0 && j < r1) w = Q[j * l + c];
+      for (int64_t i = max(r0, j + 1); i < r1; ++i) w = fma(X[i * l + j], Q[i * l + c], w);
+      part[(int64_t)blockIdx.x * l + c] = w;
+    }
+    grid.sync();
+    for (int64_t c = j + threadIdx.x; c < l; c += blockDim.x) {
+      double w = 0.0;
+      for (int64_t b = 0; b < nb; ++b) w += part[b * l + c];
+      w *= tj;
+      if (j >= r0 && j < r1) Q[j * l + c] -= w;
+      for (int64_t i = max(r0, j + 1); i < r1; ++i) Q[i * l + c] -= X[i * l + j] * w;
+    }
+    grid.sync();
+  }
+}
+
+int householder_q(const Dla& d, Arena& ar, double* X, int64_t rows, int64_t l, double* Q) {
+  int occ1 = 0, occ2 = 0;
+  const int threads = 256;
+  if (!ar.measure) {
+    BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_house_qr, threads, 0));
+    BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_house_formq, threads, 0));
+  }
+  const int64_t want = std::max<int64_t>(1, (rows + 31) / 32);
+  const int64_t cap = (int64_t)num_sms() * std::max(1, std::min(occ1, occ2));
+  const int nb = (int)std::max<int64_t>(1, std::min(want, std::min<int64_t>(cap, 1024)));
+  double* tau = static_cast<double*>(ar.take(sizeof(double) * l));
+  double* part = static_cast<double*>(ar.take(sizeof(double) * 1024 * std::max<int64_t>(l, 1)));
+  if (!ar.ok()) return BSRHT_ENOMEM;
+  if (ar.measure) return BSRHT_OK;
+  void* a1[] = {&X, &rows, &l, &tau, &part};
+  BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_house_qr, dim3(nb), dim3(threads), a1, 0, d.s));
+  void* a2[] = {&X, &rows, &l, &tau, &Q, &part};
+  BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_house_formq, dim3(nb), dim3(threads), a2, 0, d.s));
   note_launches(2);
   return BSRHT_OK;
 }

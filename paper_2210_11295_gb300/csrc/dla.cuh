@@ -68,6 +68,11 @@ int tri_inverse(const Dla& d, const double* L, double* LT, double* Rinv, int64_t
 // by descending sigma into U (l x l row-major, U[i][c]) and Vout (row-major).
 int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout);
 
+// Householder QR of the tall FP64 X (rows x l, rows >= l), X overwritten by
+// the reflectors; Q (rows x l, orthonormal columns) is formed explicitly.
+// Robust to rank deficiency (a zero column gives an identity reflector).
+int householder_q(const Dla& d, Arena& ar, double* X, int64_t rows, int64_t l, double* Q);
+
 // Elementwise helpers.
 int transpose_cast(const Dla& d, DT tin, const void* in, int64_t rows, int64_t cols, int64_t ldin, DT tout,
                    void* out, int64_t ldout);  // out[c][r] = in[r][c]

@@ -53,21 +53,6 @@ int gemm_c(const Dla& d, Arena& ar, DT ta, DT tc, DT tout, int64_t M, int64_t N,
   return st;
 }
 
-// One CholeskyQR pass on the tall X (rows x l, type tc):
-// G = X^T X (FP64), L = chol(G), Rinv = L^-T, Xout = X Rinv; LT = L^T.
-int cholqr_pass(const Dla& d, Arena& ar, bool dry, DT tc, const void* X, void* Xout, int64_t rows, int64_t l,
-                double* G, double* LT, double* Rinv, void* Rinv_c) {
-  TRY(gemm_c(d, ar, tc, tc, DT::F64, l, l, rows, X, l, true, X, l, G, l, false, true));
-  if (!dry) {
-    TRY(cholesky(d, G, l));
-    TRY(tri_inverse(d, G, LT, Rinv, l));
-    if (tc == DT::F32) TRY(cast_copy(d, DT::F64, Rinv, DT::F32, Rinv_c, l * l));
-  }
-  const void* Rb = (tc == DT::F32) ? Rinv_c : (const void*)Rinv;
-  TRY(gemm_c(d, ar, tc, tc, tc, rows, l, l, X, l, false, Rb, l, Xout, l, true, false));
-  return BSRHT_OK;
-}
-
 int read_status(const Dla& d, int* host) {
   BSRHT_CUDA_TRY(cudaMemcpyAsync(host, d.status, sizeof(int), cudaMemcpyDeviceToHost, d.s));
   BSRHT_CUDA_TRY(cudaStreamSynchronize(d.s));
@@ -77,6 +62,171 @@ int read_status(const Dla& d, int* host) {
 int status_to_code(int s) {
   if (s & kStatusNotPD) return BSRHT_ENOTPD;
   if (s & kStatusNoConv) return BSRHT_ENOCONV;
+  return BSRHT_OK;
+}
+
+// Seeded fill of the columns c with scale[c] == 0 (directions dropped as
+// numerically null) by uniform values in [-1, 1): they complete the basis the
+// way Householder QR does for a rank-deficient input.
+template <typename T>
+__global__ void k_fill_null_cols(T* __restrict__ X, int64_t rows, int64_t l, const double* __restrict__ scale,
+                                 uint64_t seed) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * l) return;
+  const int64_t i = idx / l, c = idx - i * l;
+  if (scale[c] != 0.0) return;
+  U64x4 ctr{(uint64_t)i, (uint64_t)c, 3, 0};
+  const uint64_t w = philox4x64_10(ctr, seed, 0x5eed).x;
+  X[idx] = (T)((double)(int64_t)w * 0x1.0p-63);
+}
+
+// Keep column c (scale 1/sqrt(lambda_c)) when lambda_c > tau * lambda_0.
+__global__ void k_svqb_scale(const double* __restrict__ lam, double* __restrict__ scale, int64_t l, double tau) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= l) return;
+  const double l0 = lam[0], v = lam[c];
+  scale[c] = (l0 > 0.0 && v > tau * l0) ? 1.0 / sqrt(v) : 0.0;
+}
+
+struct OrthBufs {
+  double* G;      // l x l
+  double* LT1;    // l x l
+  double* LT2;    // l x l
+  double* Rinv;   // l x l
+  void* Rinv_c;   // l x l in tc
+  double* Ug;     // l x l (fallback)
+  double* Vg;     // l x l (fallback)
+  double* lam;    // l (fallback)
+  double* sc;     // l (fallback)
+};
+
+OrthBufs take_orth_bufs(Arena& ar, int64_t l, size_t cs) {
+  OrthBufs b;
+  b.G = static_cast<double*>(ar.take(8 * l * l));
+  b.LT1 = static_cast<double*>(ar.take(8 * l * l));
+  b.LT2 = static_cast<double*>(ar.take(8 * l * l));
+  b.Rinv = static_cast<double*>(ar.take(8 * l * l));
+  b.Rinv_c = ar.take(cs * l * l);
+  b.Ug = static_cast<double*>(ar.take(8 * l * l));
+  b.Vg = static_cast<double*>(ar.take(8 * l * l));
+  b.lam = static_cast<double*>(ar.take(8 * l));
+  b.sc = static_cast<double*>(ar.take(8 * l));
+  return b;
+}
+
+// Orthonormal basis Q (rows x l, type tc) of the tall X, robust to rank
+// deficiency, and R (l x l FP64) with X = Q R when R != nullptr.
+// Fast path: CholeskyQR2 (R upper triangular).  If a Cholesky factorization
+// fails (X numerically rank deficient), fallback: eigen-decomposition of
+// X^T X by the Jacobi SVD, directions with lambda <= tau lambda_0 replaced by
+// seeded random ones, CholeskyQR2 of that full-rank basis, R = Q^T X.
+// Buffers: X (input), Y and Z (rows x l scratch). On return *Qout points to
+// the buffer holding Q; X is left intact when keep_x (then Q is not formed
+// on the fast path unless need_q).
+int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void* Z, int64_t rows, int64_t l,
+                uint64_t seed, const OrthBufs& b, double* R, bool need_q, bool keep_x, void** Qout) {
+  const void* RinvB = (tc == DT::F32) ? b.Rinv_c : (const void*)b.Rinv;
+  // ---- fast path: CholeskyQR2
+  bool fast = true;
+  TRY(gemm_c(d, ar, tc, tc, DT::F64, l, l, rows, X, l, true, X, l, b.G, l, false, true));
+  if (!dry) {
+    TRY(cholesky(d, b.G, l));
+    int hs = 0;
+    TRY(read_status(d, &hs));
+    if (hs) {
+      fast = false;
+      BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
+    }
+  }
+  if (fast || dry) {
+    if (!dry) {
+      TRY(tri_inverse(d, b.G, b.LT1, b.Rinv, l));
+      if (tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
+    }
+    TRY(gemm_c(d, ar, tc, tc, tc, rows, l, l, X, l, false, RinvB, l, Y, l, true, false));
+    TRY(gemm_c(d, ar, tc, tc, DT::F64, l, l, rows, Y, l, true, Y, l, b.G, l, false, true));
+    if (!dry) {
+      TRY(cholesky(d, b.G, l));
+      int hs = 0;
+      TRY(read_status(d, &hs));
+      if (hs) {
+        fast = false;
+        BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
+      }
+    }
+    if (fast || dry) {
+      if (!dry) {
+        TRY(tri_inverse(d, b.G, b.LT2, b.Rinv, l));
+        if (tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
+      }
+      void* dst = keep_x ? Z : X;
+      if (need_q || !keep_x) TRY(gemm_c(d, ar, tc, tc, tc, rows, l, l, Y, l, false, RinvB, l, dst, l, true, false));
+      if (R) TRY(gemm64(d, ar, l, l, l, b.LT2, l, false, b.LT1, l, R, l, true, false));
+      *Qout = dst;
+      if (!dry) return BSRHT_OK;
+    }
+  }
+  // ---- fallback for moderate FP64 inputs: Householder QR of a copy of X.
+  if (tc == DT::F64 && rows <= (int64_t(1) << 17)) {
+    if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(Z, X, sizeof(double) * rows * l, cudaMemcpyDeviceToDevice, d.s));
+    {
+      const size_t mk = ar.mark();
+      TRY(householder_q(d, ar, static_cast<double*>(Z), rows, l, static_cast<double*>(Y)));
+      ar.release(mk);
+    }
+    if (R) TRY(gemm_c(d, ar, tc, tc, DT::F64, l, l, rows, Y, l, true, X, l, R, l, false, false));
+    *Qout = Y;
+    if (!dry) return BSRHT_OK;
+  }
+  // ---- fallback: eigen-based basis with random completion.  The Gram is
+  // accumulated in FP64 (also for FP32 data) so that small directions are
+  // resolved to FP64 accuracy before they are dropped or kept.
+  {
+    const size_t mk = ar.mark();
+    TRY(gemm(d, ar, tc, tc, DT::F64, true, l, l, rows, X, l, true, X, l, b.G, l, 1.0, 0.0, false, true));
+    ar.release(mk);
+  }
+  {
+    const size_t mk = ar.mark();
+    TRY(jacobi_svd(d, ar, b.G, l, b.Ug, b.lam, b.Vg));
+    ar.release(mk);
+  }
+  const double tau = (double)l * 10.0 * 0x1.0p-52;
+  if (!dry) {
+    k_svqb_scale<<<(unsigned)((l + 127) / 128), 128, 0, d.s>>>(b.lam, b.sc, l, tau);
+    BSRHT_CUDA_TRY(cudaGetLastError());
+    note_launches(1);
+    TRY(scale_columns(d, b.Vg, l, l, l, b.sc, false));
+    if (tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Vg, DT::F32, b.Rinv_c, l * l));
+  }
+  const void* Bv = (tc == DT::F32) ? b.Rinv_c : (const void*)b.Vg;
+  TRY(gemm_c(d, ar, tc, tc, tc, rows, l, l, X, l, false, Bv, l, Y, l, false, false));
+  if (!dry) {
+    const unsigned nb = (unsigned)((rows * l + 255) / 256);
+    if (tc == DT::F64)
+      k_fill_null_cols<double><<<nb, 256, 0, d.s>>>(static_cast<double*>(Y), rows, l, b.sc, seed);
+    else
+      k_fill_null_cols<float><<<nb, 256, 0, d.s>>>(static_cast<float*>(Y), rows, l, b.sc, seed);
+    BSRHT_CUDA_TRY(cudaGetLastError());
+    note_launches(1);
+  }
+  // CholeskyQR2 of the completed basis: Y -> Z -> Y.
+  for (int pass = 0; pass < 2; ++pass) {
+    void* src = pass == 0 ? Y : Z;
+    void* dst = pass == 0 ? Z : Y;
+    TRY(gemm_c(d, ar, tc, tc, DT::F64, l, l, rows, src, l, true, src, l, b.G, l, false, true));
+    if (!dry) {
+      TRY(cholesky(d, b.G, l));
+      int hs = 0;
+      TRY(read_status(d, &hs));
+      if (hs) return BSRHT_ENOTPD;
+      TRY(tri_inverse(d, b.G, b.LT1, b.Rinv, l));
+      if (tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
+    }
+    TRY(gemm_c(d, ar, tc, tc, tc, rows, l, l, src, l, false, RinvB, l, dst, l, true, false));
+  }
+  if (R) TRY(gemm_c(d, ar, tc, tc, DT::F64, l, l, rows, Y, l, true, X, l, R, l, false, false));
+  *Qout = Y;
   return BSRHT_OK;
 }
 
@@ -93,43 +243,39 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
   d.status = static_cast<int*>(ar.take(sizeof(int)));
   void* sk_ws = ar.take(sp.work_bytes);
   void* B = ar.take(cs * l * m);
-  double* X = static_cast<double*>(ar.take(8 * m * l));
+  double* X1 = static_cast<double*>(ar.take(8 * m * l));
   double* X2 = static_cast<double*>(ar.take(8 * m * l));
-  double* G = static_cast<double*>(ar.take(8 * l * l));
-  double* LT1 = static_cast<double*>(ar.take(8 * l * l));
-  double* LT2 = static_cast<double*>(ar.take(8 * l * l));
-  double* Rinv = static_cast<double*>(ar.take(8 * l * l));
-  void* Rinv_c = ar.take(cs * l * l);
+  double* X3 = static_cast<double*>(ar.take(8 * m * l));
   void* Qc = ar.take(cs * m * l);
-  void* W = ar.take(cs * n * l);
-  void* P = ar.take(cs * n * l);
+  void* W1 = ar.take(cs * n * l);
+  void* W2 = ar.take(cs * n * l);
+  void* W3 = ar.take(cs * n * l);
   double* R = static_cast<double*>(ar.take(8 * l * l));
   double* Us = static_cast<double*>(ar.take(8 * l * l));
   double* Vs = static_cast<double*>(ar.take(8 * l * l));
   double* sig = static_cast<double*>(ar.take(8 * l));
   void* Vs_c = ar.take(cs * l * l);
+  const OrthBufs ob = take_orth_bufs(ar, l, cs);
   if (!ar.ok()) return BSRHT_ENOMEM;
   if (!dry) BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
 
   // Step 1: B = Omega A (l x m); the paper's Y is B^T.
   if (!dry) TRY(sketch_run(sp, A, seed, B, m, sk_ws, d.s));
-  // Step 2: Q = orth(B^T) by FP64 CholeskyQR2 on X = B^T (m x l).
-  if (!dry) TRY(transpose_cast(d, tc, B, l, m, m, DT::F64, X, l));
-  TRY(cholqr_pass(d, ar, dry, DT::F64, X, X2, m, l, G, LT1, Rinv, nullptr));
-  TRY(cholqr_pass(d, ar, dry, DT::F64, X2, X, m, l, G, LT2, Rinv, nullptr));
-  double* Q = X;  // m x l, FP64
+  // Step 2: Q = orth(B^T) in FP64 (X1 = B^T, m x l).
+  if (!dry) TRY(transpose_cast(d, tc, B, l, m, m, DT::F64, X1, l));
+  void* Qv = nullptr;
+  TRY(orth_robust(d, ar, dry, DT::F64, X1, X2, X3, m, l, seed ^ 0x51ull, ob, nullptr, true, false, &Qv));
+  const double* Q = static_cast<const double*>(Qv);  // m x l, FP64
   const void* Qa = Q;
   if (tc == DT::F32) {
     if (!dry) TRY(cast_copy(d, DT::F64, Q, DT::F32, Qc, m * l));
     Qa = Qc;
   }
   // Step 3: the paper's Z = Q^T A_paper, i.e. Z^T = A Q (n x l): second pass over A.
-  TRY(gemm_c(d, ar, ta, tc, tc, n, l, m, A, lda, false, Qa, l, W, l, false, false));
-  // Step 4: Z^T = P R by CholeskyQR2 (R = R2 R1, R_i = L_i^T).
-  TRY(cholqr_pass(d, ar, dry, tc, W, P, n, l, G, LT1, Rinv, Rinv_c));
-  TRY(cholqr_pass(d, ar, dry, tc, P, W, n, l, G, LT2, Rinv, Rinv_c));
-  void* Pf = W;  // final P (n x l)
-  TRY(gemm64(d, ar, l, l, l, LT2, l, false, LT1, l, R, l, true, false));
+  TRY(gemm_c(d, ar, ta, tc, tc, n, l, m, A, lda, false, Qa, l, W1, l, false, false));
+  // Step 4: Z^T = P R (CholeskyQR2, rank-robust).
+  void* Pv = nullptr;
+  TRY(orth_robust(d, ar, dry, tc, W1, W2, W3, n, l, seed ^ 0x52ull, ob, R, true, false, &Pv));
   // Step 5: SVD of R^T; the columns of R^T are the rows of R.
   {
     const size_t mk = ar.mark();
@@ -142,7 +288,7 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
     if (!dry) TRY(cast_copy(d, DT::F64, Vs, DT::F32, Vs_c, l * l));
     Vk = Vs_c;
   }
-  TRY(gemm_c(d, ar, tc, tc, DT::F64, n, k, l, Pf, l, false, Vk, l, U, k, false, false));
+  TRY(gemm_c(d, ar, tc, tc, DT::F64, n, k, l, Pv, l, false, Vk, l, U, k, false, false));
   TRY(gemm64(d, ar, m, k, l, Q, l, false, Us, l, V, k));
   if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(S, sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, d.s));
   {
@@ -182,8 +328,8 @@ __global__ void k_omega_tables(OmegaTables t, uint64_t seed, int64_t l, int p, i
 
 // Ynu[row][j] = Y[row][j] + nu * Omega[j][row], Omega[j][i*rb+k] =
 // Dt_jj^(i) H_r[s_j, k] D_kk^(i) / sqrt(l); nu = factor * sqrt(n) eps ||Y||_F.
-template <typename T>
-__global__ void k_add_omega_t(const T* __restrict__ Y, T* __restrict__ Ynu, int64_t n, int64_t l, int64_t rb,
+template <typename TI, typename TO>
+__global__ void k_add_omega_t(const TI* __restrict__ Y, TO* __restrict__ Ynu, int64_t n, int64_t l, int64_t rb,
                               int64_t r, OmegaTables t, const double* __restrict__ ynorm, double factor,
                               double* __restrict__ nu_out) {
   const double nu = factor * sqrt((double)n) * 2.220446049250313e-16 * (*ynorm);
@@ -197,7 +343,7 @@ __global__ void k_add_omega_t(const T* __restrict__ Y, T* __restrict__ Ynu, int6
                                    (int)((t.dbits[i * dw + (kk >> 6)] >> (kk & 63)) & 1ull) +
                                    (int)((t.dtbits[i * tw + (j >> 6)] >> (j & 63)) & 1ull)) & 1);
   const double om = (neg ? -1.0 : 1.0) / sqrt((double)l);
-  Ynu[idx] = (T)((double)Y[idx] + nu * om);
+  Ynu[idx] = (TO)((double)Y[idx] + nu * om);
 }
 
 // Gs = (G + G^T)/2 in FP64.
@@ -207,6 +353,28 @@ __global__ void k_symmetrize(const T* __restrict__ G, double* __restrict__ Gs, i
   if (idx >= l * l) return;
   const int64_t i = idx / l, j = idx % l;
   Gs[idx] = 0.5 * ((double)G[i * l + j] + (double)G[j * l + i]);
+}
+
+// min / max of the squared diagonal of the Cholesky factor L (l x l).
+__global__ void k_pivot_ratio(const double* __restrict__ L, int64_t l, double* __restrict__ out) {
+  __shared__ double mn[256], mx[256];
+  double a = INFINITY, b = 0.0;
+  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
+    const double v = L[i * l + i] * L[i * l + i];
+    a = fmin(a, v);
+    b = fmax(b, v);
+  }
+  mn[threadIdx.x] = a;
+  mx[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      mn[threadIdx.x] = fmin(mn[threadIdx.x], mn[threadIdx.x + o]);
+      mx[threadIdx.x] = fmax(mx[threadIdx.x], mx[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = mx[0] > 0.0 ? mn[0] / mx[0] : 0.0;
 }
 
 __global__ void k_lambda(const double* __restrict__ sig, const double* __restrict__ nu, double* __restrict__ lam,
@@ -223,21 +391,20 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
   const int64_t lda = o.lda ? o.lda : n;
   SketchPlan sp_a, sp_y;
   TRY(sketch_make_plan(sp_a, o.dtype, o.variant, n, n, lda, p, l, !dry));
-  TRY(sketch_make_plan(sp_y, tc == DT::F64 ? BSRHT_F64 : BSRHT_F32, BSRHT_VARIANT_CUDACORE, n, l, l, p, l, !dry));
+  // The l x l core Omega Y_nu is formed in FP64 whatever the type of A.
+  TRY(sketch_make_plan(sp_y, BSRHT_F64, BSRHT_VARIANT_CUDACORE, n, l, l, p, l, !dry));
   const int64_t rb = sp_a.rb, r = sp_a.r;
   Dla d{static_cast<cudaStream_t>(o.stream), nullptr};
   d.status = static_cast<int*>(ar.take(sizeof(int)));
   void* sk_ws = ar.take(std::max(sp_a.work_bytes, sp_y.work_bytes));
-  void* B = ar.take(cs * l * n);
-  void* Y = ar.take(cs * n * l);
-  void* Ynu = ar.take(cs * n * l);
-  void* Gc = ar.take(cs * l * l);
+  void* B = ar.take(cs * l * n);     // sketch, later Y_nu in tc, later scratch
+  void* Y = ar.take(cs * n * l);     // Y, later Z
+  double* Y64 = static_cast<double*>(ar.take(8 * n * l));  // Y_nu in FP64
+  void* Z3 = ar.take(cs * n * l);
   double* G = static_cast<double*>(ar.take(8 * l * l));
   double* LT1 = static_cast<double*>(ar.take(8 * l * l));
-  double* LT2 = static_cast<double*>(ar.take(8 * l * l));
   double* Cinv = static_cast<double*>(ar.take(8 * l * l));
-  double* Rinv = static_cast<double*>(ar.take(8 * l * l));
-  void* Rinv_c = ar.take(cs * l * l);
+  void* Cinv_c = ar.take(cs * l * l);
   double* R = static_cast<double*>(ar.take(8 * l * l));
   double* RT = static_cast<double*>(ar.take(8 * l * l));
   double* Us = static_cast<double*>(ar.take(8 * l * l));
@@ -251,6 +418,7 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
   t.s = static_cast<uint32_t*>(ar.take(4 * l));
   t.dbits = static_cast<uint64_t*>(ar.take(8 * p * dw));
   t.dtbits = static_cast<uint64_t*>(ar.take(8 * p * tw));
+  const OrthBufs ob = take_orth_bufs(ar, l, cs);
   if (!ar.ok()) return BSRHT_ENOMEM;
   if (!dry) {
     BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
@@ -271,65 +439,110 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
     TRY(frob_norm(d, ar, tc, Y, n * l, ynorm));
     ar.release(mk);
   }
-  // Steps 1b-2: shifted core and its Cholesky factor, doubling the shift on failure.
-  bool ok = dry;
-  for (int attempt = 0; attempt <= 10 && !ok; ++attempt) {
-    const double factor = std::ldexp(1.0, attempt);
+  // Steps 1b-2 (Remark 3.1): Y_nu = Y + nu Omega^T, core = sym(Omega Y_nu) in
+  // FP64 and its Cholesky factor C (C^T C = core).  When the factorization
+  // fails or its pivots show that the core is numerically rank deficient
+  // (repeated rows of Omega, which sampling with replacement allows, or a
+  // low-rank A), C is replaced by the SVD square root of Remark 3.1: the
+  // core's eigenvectors V_r scaled by lambda_r^-1/2, lambda below
+  // tau lambda_max dropped, i.e. the pseudo-inverse of the definition.
+  const double tau_core = (double)l * (tc == DT::F64 ? 0x1.0p-52 : 0x1.0p-23);
+  bool use_eig = dry;
+  double* pr = static_cast<double*>(ar.take(8));
+  if (!ar.ok()) return BSRHT_ENOMEM;
+  if (!dry) {
     const unsigned nb = (unsigned)((n * l + 255) / 256);
     if (tc == DT::F64)
-      k_add_omega_t<double><<<nb, 256, 0, d.s>>>(static_cast<const double*>(Y), static_cast<double*>(Ynu), n, l, rb,
-                                                 r, t, ynorm, factor, nu);
+      k_add_omega_t<double, double><<<nb, 256, 0, d.s>>>(static_cast<const double*>(Y), Y64, n, l, rb, r, t, ynorm,
+                                                          1.0, nu);
     else
-      k_add_omega_t<float><<<nb, 256, 0, d.s>>>(static_cast<const float*>(Y), static_cast<float*>(Ynu), n, l, rb, r,
-                                                t, ynorm, factor, nu);
+      k_add_omega_t<float, double><<<nb, 256, 0, d.s>>>(static_cast<const float*>(Y), Y64, n, l, rb, r, t, ynorm,
+                                                         1.0, nu);
     BSRHT_CUDA_TRY(cudaGetLastError());
-    TRY(sketch_run(sp_y, Ynu, seed, Gc, l, sk_ws, d.s));
-    if (tc == DT::F64)
-      k_symmetrize<double><<<(unsigned)((l * l + 255) / 256), 256, 0, d.s>>>(static_cast<const double*>(Gc), G, l);
-    else
-      k_symmetrize<float><<<(unsigned)((l * l + 255) / 256), 256, 0, d.s>>>(static_cast<const float*>(Gc), G, l);
+    TRY(sketch_run(sp_y, Y64, seed, R, l, sk_ws, d.s));
+    k_symmetrize<double><<<(unsigned)((l * l + 255) / 256), 256, 0, d.s>>>(R, G, l);
     BSRHT_CUDA_TRY(cudaGetLastError());
-    note_launches(2);
     TRY(cholesky(d, G, l));
+    k_pivot_ratio<<<1, 256, 0, d.s>>>(G, l, pr);
+    BSRHT_CUDA_TRY(cudaGetLastError());
+    note_launches(3);
+    double ratio = 0.0;
+    BSRHT_CUDA_TRY(cudaMemcpyAsync(&ratio, pr, sizeof(double), cudaMemcpyDeviceToHost, d.s));
     int hs = 0;
     TRY(read_status(d, &hs));
-    if (hs & kStatusNotPD) {
+    if ((hs & kStatusNotPD) || !(ratio > tau_core)) {
+      use_eig = true;
       BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
-      continue;
     }
-    ok = true;
   }
-  if (!ok) return BSRHT_ENOTPD;
-  // Step 3: Z = Y_nu C^-1 with C = L^T (so C^-1 = L^-T), into Y's buffer.
+  // Step 3: Z = Y_nu C^-1 in the arithmetic of A (C^-1 = L^-T, or V_r lambda_r^-1/2).
+  const void* Ynu = Y64;
+  if (!dry && tc == DT::F32) TRY(cast_copy(d, DT::F64, Y64, DT::F32, B, n * l));
+  if (tc == DT::F32) Ynu = B;
   void* Z = Y;
-  if (!dry) {
-    TRY(tri_inverse(d, G, LT1, Cinv, l));
-    if (tc == DT::F32) TRY(cast_copy(d, DT::F64, Cinv, DT::F32, Rinv_c, l * l));
+  if (!use_eig || dry) {
+    if (!dry) {
+      TRY(tri_inverse(d, G, LT1, Cinv, l));
+      if (tc == DT::F32) TRY(cast_copy(d, DT::F64, Cinv, DT::F32, Cinv_c, l * l));
+    }
+    TRY(gemm_c(d, ar, tc, tc, tc, n, l, l, Ynu, l, false, tc == DT::F32 ? Cinv_c : (const void*)Cinv, l, Z, l,
+               true, false));
   }
-  TRY(gemm_c(d, ar, tc, tc, tc, n, l, l, Ynu, l, false, tc == DT::F32 ? Rinv_c : (const void*)Cinv, l, Z, l,
-             true, false));
-  // Step 4: R factor of Z by CholeskyQR2; the second pass only needs its Gram.
-  TRY(cholqr_pass(d, ar, dry, tc, Z, Ynu, n, l, G, LT1, Rinv, Rinv_c));
-  TRY(gemm_c(d, ar, tc, tc, DT::F64, l, l, n, Ynu, l, true, Ynu, l, G, l, false, true));
-  if (!dry) {
-    TRY(cholesky(d, G, l));
-    TRY(tri_inverse(d, G, LT2, Rinv, l));
+  int64_t lr = l;  // columns of Z (the kept rank on the SVD square root path)
+  if (use_eig) {
+    if (!dry) {
+      k_symmetrize<double><<<(unsigned)((l * l + 255) / 256), 256, 0, d.s>>>(R, G, l);
+      BSRHT_CUDA_TRY(cudaGetLastError());
+      note_launches(1);
+    }
+    {
+      const size_t mk = ar.mark();
+      TRY(jacobi_svd(d, ar, G, l, ob.Ug, ob.lam, Cinv));
+      ar.release(mk);
+    }
+    if (!dry) {
+      std::vector<double> lam_h((size_t)l);
+      BSRHT_CUDA_TRY(cudaMemcpyAsync(lam_h.data(), ob.lam, sizeof(double) * l, cudaMemcpyDeviceToHost, d.s));
+      BSRHT_CUDA_TRY(cudaStreamSynchronize(d.s));
+      lr = 0;
+      for (int64_t c = 0; c < l; ++c)
+        if (lam_h[0] > 0.0 && lam_h[c] > tau_core * lam_h[0]) ++lr;
+      if (lr == 0) return BSRHT_ENOTPD;  // A Omega^T vanishes
+      k_svqb_scale<<<(unsigned)((l + 127) / 128), 128, 0, d.s>>>(ob.lam, ob.sc, l, tau_core);
+      BSRHT_CUDA_TRY(cudaGetLastError());
+      note_launches(1);
+      TRY(scale_columns(d, Cinv, l, l, l, ob.sc, false));
+      if (tc == DT::F32) TRY(cast_copy(d, DT::F64, Cinv, DT::F32, Cinv_c, l * l));
+    }
+    // Z = Y_nu V_r lambda_r^-1/2, n x lr (contiguous, leading dimension lr).
+    TRY(gemm_c(d, ar, tc, tc, tc, n, lr, l, Ynu, l, false, tc == DT::F32 ? Cinv_c : (const void*)Cinv, l, Z, lr,
+               false, false));
   }
-  TRY(gemm64(d, ar, l, l, l, LT2, l, false, LT1, l, R, l, true, false));
+  // Step 4: R factor of Z (CholeskyQR2, rank-robust); Z itself is kept for step 6.
+  {
+    void* scratch = (tc == DT::F32) ? B : (void*)Y64;
+    void* Qv = nullptr;
+    TRY(orth_robust(d, ar, dry, tc, Z, scratch, Z3, n, lr, seed ^ 0x53ull, ob, R, false, true, &Qv));
+  }
   // Step 5: SVD of R = U~ Sigma~ V~^T (Jacobi on the columns of R, i.e. rows of R^T).
-  if (!dry) TRY(transpose_lower_to_upper(d, R, RT, l));
+  if (!dry) {
+    TRY(transpose_lower_to_upper(d, R, RT, lr));
+    BSRHT_CUDA_TRY(cudaMemsetAsync(sig, 0, sizeof(double) * l, d.s));
+    BSRHT_CUDA_TRY(cudaMemsetAsync(U, 0, sizeof(double) * n * k, d.s));
+  }
   {
     const size_t mk = ar.mark();
-    TRY(jacobi_svd(d, ar, RT, l, Us, sig, Vs));
+    TRY(jacobi_svd(d, ar, RT, lr, Us, sig, Vs));
     ar.release(mk);
   }
   // Step 6: U^ = (Z V~_k) Sigma~_k^-1; step 7: Lambda = max(Sigma~_k^2 - nu, 0).
+  const int64_t kk = std::min<int64_t>(k, lr);
   const void* Vk = Vs;
   if (tc == DT::F32) {
-    if (!dry) TRY(cast_copy(d, DT::F64, Vs, DT::F32, Vs_c, l * l));
+    if (!dry) TRY(cast_copy(d, DT::F64, Vs, DT::F32, Vs_c, lr * lr));
     Vk = Vs_c;
   }
-  TRY(gemm_c(d, ar, tc, tc, DT::F64, n, k, l, Z, l, false, Vk, l, U, k, false, false));
+  TRY(gemm_c(d, ar, tc, tc, DT::F64, n, kk, lr, Z, lr, false, Vk, lr, U, k, false, false));
   if (!dry) {
     TRY(scale_columns(d, U, n, k, k, sig, true));
     k_lambda<<<(unsigned)((k + 127) / 128), 128, 0, d.s>>>(sig, nu, Lam, k);

@@ -35,7 +35,15 @@ def _gap_ok(s, i, rel=1e-3):
 
 
 def test_rsvd_small_fp64_matches_oracle(lib):
-    """n=4096, m=256, sigma_i = exp(-i/10), p=4, l=128, k=20, seed 0."""
+    """n=4096, m=256, sigma_i = exp(-i/10), p=4, l=128, k=20, seed 0.
+
+    With l = 128 samples out of r = 1024 (with replacement, Sec. 2) two rows
+    of this Omega repeat up to sign, so range(B^T) has dimension 126 and both
+    sides complete the basis Q with arbitrary directions (Householder on both
+    sides, but rounding decides them). A Q_extra then differs between the
+    sides by up to sigma_{l-1}(A) ~ 3e-6, which moves the computed singular
+    vectors by O(sigma_{l-1} / gap) (1e-6 measured, 2e-5 allowed) while the
+    singular values, second order in that change, agree to 1e-10."""
     a, _ = synth.haar_spectrum(4096, 256, seed=1235)
     u, s, v = lib.bsrht_rsvd(torch.from_numpy(a).cuda(), 20, 128, 4, 0)
     torch.cuda.synchronize()
@@ -44,11 +52,11 @@ def test_rsvd_small_fp64_matches_oracle(lib):
     assert np.max(np.abs(s - sr)) <= 1e-10 * sr[0]
     for i in range(20):
         if _gap_ok(sr, i):
-            assert np.linalg.norm(u[:, i] - ur[:, i]) <= 1e-8
-            assert np.linalg.norm(v[:, i] - vr[:, i]) <= 1e-8
+            assert np.linalg.norm(u[:, i] - ur[:, i]) <= 2e-5
+            assert np.linalg.norm(v[:, i] - vr[:, i]) <= 2e-5
     approx = (u * s) @ v.T
     ref = (ur * sr) @ vr.T
-    assert np.linalg.norm(approx - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert np.linalg.norm(approx - ref) <= 2e-5 * np.linalg.norm(ref)
 
 
 @pytest.mark.parametrize("p", [1, 4, 16])
@@ -138,11 +146,21 @@ def test_nystrom_exact_recovery_fp64(lib):
     assert np.linalg.norm(a - (u * lam) @ u.T) <= 1e-9 * np.linalg.norm(a)
 
 
+def _fp32_eig_tol(n, lam1):
+    """FP32 eigenvalue tolerance: the tall products (sketch, Z = Y C^-1, the Gram
+    of Z) accumulate over up to n terms in FP32, so each computed eigenvalue
+    of the rank-l Nystrom matrix carries an absolute error up to about
+    8 sqrt(n) 2^-24 lambda_1; differences add with random signs over k."""
+    return 8.0 * np.sqrt(n) * 2.0 ** -24 * lam1
+
+
 @pytest.mark.parametrize("k", [100, 200, 400])
 def test_nystrom_kernel_subsample_fp32(lib, k):
     """The kernel workload's 4096-point subsample (784-dim uniform points, RBF
-    with the median bandwidth), p = 8, l = 600: trace-norm error tr(A) - sum(Lambda)
-    (exact because the residual is PSD, Sec. 3.2) against the oracle's."""
+    with the median bandwidth), p = 8, l = 600 (> r = 512, so Omega repeats
+    rows and the core is singular): trace-norm error tr(A) - sum(Lambda), exact
+    because the residual is PSD (Sec. 3.2), against the oracle run with the
+    same FP32 rank threshold for Remark 3.1's SVD square root."""
     x = synth.rbf_points(4096, 784, seed=1238)
     h = synth.rbf_bandwidth(x)
     a64 = synth.rbf_kernel(x, h)
@@ -150,9 +168,30 @@ def test_nystrom_kernel_subsample_fp32(lib, k):
     u, lam = lib.bsrht_nystrom(torch.from_numpy(a32).cuda(), k, 600, 8, 0)
     torch.cuda.synchronize()
     u, lam = u.cpu().numpy(), lam.cpu().numpy()
-    ur, lr, _ = orl.nystrom(a32.astype(np.float64), k, 600, 8, 0)
+    ur, lr, _ = orl.nystrom(a32.astype(np.float64), k, 600, 8, 0, unit_roundoff=2.0 ** -23)
     tr = np.trace(a32.astype(np.float64))
-    err, err_ref = tr - lam.sum(), tr - lr.sum()
-    assert abs(err - err_ref) <= 1e-4 * err_ref
-    assert np.max(np.abs(lam - lr)) <= 2e-5 * lr[0]
+    tol = _fp32_eig_tol(4096, lr[0])
+    assert np.max(np.abs(lam - lr)) <= tol
+    assert abs((tr - lam.sum()) - (tr - lr.sum())) <= np.sqrt(k) * tol
     assert np.linalg.norm(u.T @ u - np.eye(k)) <= 1e-4
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("p", [1, 8])
+def test_nystrom_repeated_sketch_rows(lib, dtype, p):
+    """l > sqrt(r): repeated rows of Omega make the core singular; both sides
+    take Remark 3.1's SVD square root (same rank threshold) and agree on the
+    eigenvalues and the trace error."""
+    x = synth.rbf_points(2048, 16, seed=7).astype(np.float64)
+    a = synth.rbf_kernel(x, synth.rbf_bandwidth(x))
+    k, l, n = 150, 300, 2048
+    u, lam = lib.bsrht_nystrom(torch.from_numpy(a).to(dtype).cuda(), k, l, p, 5)
+    torch.cuda.synchronize()
+    lam = lam.cpu().numpy()
+    a_in = torch.from_numpy(a).to(dtype).double().numpy()
+    ur_ = 2.0 ** -52 if dtype == torch.float64 else 2.0 ** -23
+    _, lr, _ = orl.nystrom(a_in, k, l, p, 5, unit_roundoff=ur_)
+    tr = np.trace(a_in)
+    tol = 1e-10 * lr[0] if dtype == torch.float64 else _fp32_eig_tol(n, lr[0])
+    assert np.max(np.abs(lam - lr)) <= tol
+    assert abs((tr - lam.sum()) - (tr - lr.sum())) <= np.sqrt(k) * tol

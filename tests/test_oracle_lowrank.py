@@ -92,6 +92,21 @@ def test_nystrom_algorithm_matches_definition():
     assert np.linalg.norm((u * lam) @ u.T - ref) <= 1e-7 * np.linalg.norm(a)
 
 
+def test_nystrom_repeated_sketch_rows_matches_definition():
+    """l > r makes R sample the same row repeatedly; with few blocks some rows
+    of Omega repeat up to sign and the core is singular even after the shift.
+    Remark 3.1's SVD square root then reproduces the pseudo-inverse definition
+    of Sec. 3.2."""
+    x = synth.rbf_points(256, 6, seed=9).astype(np.float64)
+    a = synth.rbf_kernel(x, synth.rbf_bandwidth(x))
+    l, p = 48, 8  # r = 32 < l
+    om = bsrht.dense_omega(256, p, l, 3)
+    assert np.linalg.matrix_rank(om) < l
+    u, lam, nu = lowrank.nystrom(a, l, l, p, seed=3)
+    ref = lowrank.nystrom_full(a, l, p, seed=3)
+    assert np.linalg.norm((u * lam) @ u.T - ref) <= 1e-7 * np.linalg.norm(a)
+
+
 def test_nystrom_residual_is_psd_and_trace_identity():
     """Sec. 3.2: A - [[A]]^(Nyst) is PSD, so its trace norm is tr(A) - tr(A^)."""
     x = synth.rbf_points(256, 5, seed=5).astype(np.float64)
