@@ -129,7 +129,8 @@ int bsrht_sketch_workspace(int64_t n, int64_t m, int32_t p, int64_t l,
  *   - All calls on one device share the array: calls whose kernels overlap on
  *     the GPU (other streams, other host threads) race and corrupt each
  *     other's results, so serialise them on one stream.  The array keeps the
- *     last call's contents; the sketch overwrites every slot it reads.
+ *     last call's contents; the sketch overwrites every slot it reads and
+ *     clears its status word at the start of each call.
  */
 int bsrht_sketch_noalloc(const void* A, int64_t n, int64_t m, int32_t p,
                          int64_t l, uint64_t seed, void* out,

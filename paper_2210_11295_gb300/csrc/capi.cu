@@ -114,7 +114,7 @@ int bsrht_sketch(const void* A, int64_t n, int64_t m, int32_t p, int64_t l, uint
   const bsrht_opts o = opts_or_default(opts);
   if ((!A && m > 0) || (!out && m > 0)) return BSRHT_EINVAL;
   SketchPlan pl;
-  int st = sketch_make_plan(pl, o.dtype, o.variant, n, m, o.lda, p, l, true);
+  int st = sketch_make_plan(pl, o.dtype, o.variant, n, m, o.lda, p, l, true, A);
   if (st != BSRHT_OK) return st;
   if (m == 0) return BSRHT_OK;
   void* work = nullptr;

@@ -238,7 +238,7 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
   const size_t cs = dt_size(tc);
   const int64_t lda = o.lda ? o.lda : m;
   SketchPlan sp;
-  TRY(sketch_make_plan(sp, o.dtype, o.variant, n, m, lda, p, l, !dry));
+  TRY(sketch_make_plan(sp, o.dtype, o.variant, n, m, lda, p, l, !dry, dry ? nullptr : A));
   Dla d{static_cast<cudaStream_t>(o.stream), nullptr};
   d.status = static_cast<int*>(ar.take(sizeof(int)));
   void* sk_ws = ar.take(sp.work_bytes);
@@ -390,7 +390,7 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
   const size_t cs = dt_size(tc);
   const int64_t lda = o.lda ? o.lda : n;
   SketchPlan sp_a, sp_y;
-  TRY(sketch_make_plan(sp_a, o.dtype, o.variant, n, n, lda, p, l, !dry));
+  TRY(sketch_make_plan(sp_a, o.dtype, o.variant, n, n, lda, p, l, !dry, dry ? nullptr : A));
   // The l x l core Omega Y_nu is formed in FP64 whatever the type of A.
   TRY(sketch_make_plan(sp_y, BSRHT_F64, BSRHT_VARIANT_CUDACORE, n, l, l, p, l, !dry));
   const int64_t rb = sp_a.rb, r = sp_a.r;

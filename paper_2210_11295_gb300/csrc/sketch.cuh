@@ -10,7 +10,7 @@ namespace bsrht {
 struct SketchPlan {
   int dtype = 0;      // bsrht_dtype of A
   int variant = 1;    // 1 = CUDA-core butterflies (K1), 2 = tensor cores (K2)
-  int path = 0;       // 0 = chunked FWHT kernel, 1 = small-r direct kernel
+  int path = 0;       // 0 = chunked FWHT kernel, 1 = small-r direct kernel, 2 = TMA-fed chunked kernel
   int inst = 0;       // kernel instance id within the dtype family
   int W = 0, NT = 0, R2 = 0, JM = 0, NRL = 0;
   int64_t n = 0, m = 0, lda = 0, l = 0;
@@ -23,14 +23,18 @@ struct SketchPlan {
   int G = 0;          // CTAs of the chunked kernel (persistent, one wave)
   int64_t jgroup = 0; // sketch rows handled per launch
   size_t smem = 0;    // dynamic shared memory per CTA
-  size_t part_bytes = 0;  // partial-sum scratch
+  size_t part_bytes = 0;  // partial-sum scratch (path 2 then: status word, D and Dt sign tables)
+  size_t dtab_bytes = 0;  // path 2: D^(i) sign table
+  size_t dttab_bytes = 0; // path 2: Dt^(i) sign table (one sketch-row group)
   size_t work_bytes = 0;  // total scratch
 };
 
 // Fills plan for the given sizes; returns a bsrht status. When
 // query_device is false, no CUDA call is made and G is an upper bound.
+// A (may be null) decides whether the TMA path's alignment rules hold; with
+// A null the plan's work_bytes covers both the TMA and the plain path.
 int sketch_make_plan(SketchPlan& plan, int dtype, int variant, int64_t n, int64_t m,
-                     int64_t lda, int p, int64_t l, bool query_device);
+                     int64_t lda, int p, int64_t l, bool query_device, const void* A = nullptr);
 
 // Enqueues the sketch on stream; work must hold plan.work_bytes.
 int sketch_run(const SketchPlan& plan, const void* A, uint64_t seed, void* out, int64_t ldo,
@@ -63,5 +67,9 @@ int sketch_launch_f64(const SketchPlan& plan, const SketchArgs& a, void* out, in
                       cudaStream_t stream);
 int sketch_occupancy_f32(const SketchPlan& plan);
 int sketch_occupancy_f64(const SketchPlan& plan);
+// TMA-fed path (sketch_tma.cu): W = 32, NT = 512, R2 = 512, JM in {32, 64}.
+int sketch_occupancy_tma(const SketchPlan& plan);
+int sketch_launch_tma(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo, int* err,
+                      uint64_t* dtab, uint64_t* dttab, cudaStream_t stream);
 
 }  // namespace bsrht

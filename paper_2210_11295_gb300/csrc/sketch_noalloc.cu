@@ -13,8 +13,8 @@
 // one file-scope device array of kNoAllocScratchBytes.  Every device that
 // loads the library holds this array until the process exits.  All calls on
 // a device share it and it keeps the last call's contents; the sketch writes
-// every partial-sum slot before reading it, so nothing needs to start at
-// zero.  Two calls whose kernels overlap on the GPU (different streams, or
+// every partial-sum slot before reading it and clears its one status word at
+// the start of each call, so nothing else needs to start at zero.  Two calls whose kernels overlap on the GPU (different streams, or
 // different host threads on one device) race on the array and give wrong
 // results: serialise them on one stream.
 #include <mutex>
@@ -63,7 +63,7 @@ extern "C" int bsrht_sketch_noalloc(const void* A, int64_t n, int64_t m, int32_t
   if (opts) o = *opts;
   if ((!A && m > 0) || (!out && m > 0)) return BSRHT_EINVAL;
   SketchPlan pl;
-  int st = sketch_make_plan(pl, o.dtype, o.variant, n, m, o.lda, p, l, true);
+  int st = sketch_make_plan(pl, o.dtype, o.variant, n, m, o.lda, p, l, true, A);
   if (st != BSRHT_OK) return st;
   if (m == 0) return BSRHT_OK;
   if (pl.work_bytes > kNoAllocScratchBytes) return BSRHT_ENOMEM;

@@ -25,8 +25,38 @@ int num_sms() {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// The TMA path needs 16-byte aligned rows: base address and row stride.
+static bool tma_layout_ok(int dtype, const void* A, int64_t lda) {
+  const size_t es = dtype == BSRHT_F32 ? 4 : 2;
+  if ((lda * (int64_t)es) % 16 != 0) return false;
+  return A == nullptr || (reinterpret_cast<uintptr_t>(A) % 16) == 0;
+}
+
+static int make_plan_tma(SketchPlan& pl, bool query_device) {
+  pl.path = 2;
+  pl.W = 32;
+  pl.NT = 512;
+  pl.R2 = 512;
+  pl.JM = pl.l <= 512 ? 32 : 64;
+  pl.NRL = pl.NT / pl.W;
+  pl.jgroup = std::min<int64_t>(pl.l, (int64_t)pl.JM * pl.NRL);
+  pl.nch = (pl.rb + pl.R2 - 1) / pl.R2;
+  pl.C = (int64_t)pl.p * pl.nch;
+  pl.P = (pl.m + pl.W - 1) / pl.W;
+  pl.T = pl.P * pl.C;
+  int occ = query_device ? sketch_occupancy_tma(pl) : 0;
+  if (occ <= 0) occ = 1;
+  int64_t g = (int64_t)num_sms() * occ;
+  pl.G = (int)std::max<int64_t>(1, std::min<int64_t>(g, std::max<int64_t>(pl.T, 1)));
+  pl.part_bytes = align_up(4 * (size_t)(pl.G + pl.P) * (size_t)pl.jgroup * pl.W, 256);
+  pl.dtab_bytes = align_up(4 * (size_t)pl.p * (size_t)pl.nch * 16, 256);
+  pl.dttab_bytes = align_up(8 * (size_t)pl.p * (size_t)((pl.jgroup + 63) / 64), 256);
+  pl.work_bytes = pl.part_bytes + 256 + pl.dtab_bytes + pl.dttab_bytes;
+  return BSRHT_OK;
+}
+
 int sketch_make_plan(SketchPlan& pl, int dtype, int variant, int64_t n, int64_t m, int64_t lda,
-                     int p, int64_t l, bool query_device) {
+                     int p, int64_t l, bool query_device, const void* A) {
   if (dtype < BSRHT_F64 || dtype > BSRHT_F16) return BSRHT_EINVAL;
   if (n < 1 || m < 0 || p < 1 || (int64_t)p > n || l < 1 || l > n) return BSRHT_EINVAL;
   if (lda == 0) lda = m;
@@ -93,13 +123,23 @@ int sketch_make_plan(SketchPlan& pl, int dtype, int variant, int64_t n, int64_t 
   pl.G = (int)std::max<int64_t>(1, std::min<int64_t>(g, std::max<int64_t>(pl.T, 1)));
   pl.part_bytes = align_up(elem * (size_t)(pl.G + pl.P) * (size_t)pl.jgroup * pl.W, 256);
   pl.work_bytes = pl.part_bytes;
+  // FP32-arithmetic inputs with blocks of at least one 512-row chunk and
+  // TMA-compatible rows take the TMA-fed kernel; the plain kernel stays the
+  // fallback, so a plan made without A reserves scratch for both.
+  if (!f64 && pl.r >= 512 && tma_layout_ok(dtype, A, lda)) {
+    SketchPlan t = pl;
+    make_plan_tma(t, query_device);
+    const size_t plain = pl.work_bytes;
+    pl = t;
+    if (A == nullptr) pl.work_bytes = std::max(pl.work_bytes, plain);
+  }
   return BSRHT_OK;
 }
 
 int sketch_run(const SketchPlan& pl, const void* A, uint64_t seed, void* out, int64_t ldo, void* work,
                cudaStream_t stream) {
   if (pl.m == 0) return BSRHT_OK;
-  if (pl.path == 0 && pl.work_bytes > 0 && work == nullptr) return BSRHT_ENOMEM;
+  if (pl.path != 1 && pl.work_bytes > 0 && work == nullptr) return BSRHT_ENOMEM;
   for (int64_t j0 = 0; j0 < pl.l; j0 += pl.jgroup) {
     SketchArgs a;
     a.A = A;
@@ -117,8 +157,18 @@ int sketch_run(const SketchPlan& pl, const void* A, uint64_t seed, void* out, in
     a.T = pl.T;
     a.G = pl.G;
     a.part = work;
-    const int st = pl.dtype == BSRHT_F64 ? sketch_launch_f64(pl, a, out, ldo, stream)
-                                         : sketch_launch_f32(pl, a, out, ldo, stream);
+    int st;
+    if (pl.path == 2) {
+      char* w = static_cast<char*>(work);
+      int* err = reinterpret_cast<int*>(w + pl.part_bytes);
+      uint64_t* dtab = reinterpret_cast<uint64_t*>(w + pl.part_bytes + 256);
+      uint64_t* dttab = reinterpret_cast<uint64_t*>(w + pl.part_bytes + 256 + pl.dtab_bytes);
+      if (j0 == 0) BSRHT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), stream));
+      st = sketch_launch_tma(pl, a, out, ldo, err, dtab, dttab, stream);
+    } else {
+      st = pl.dtype == BSRHT_F64 ? sketch_launch_f64(pl, a, out, ldo, stream)
+                                 : sketch_launch_f32(pl, a, out, ldo, stream);
+    }
     if (st != BSRHT_OK) return st;
   }
   return BSRHT_OK;

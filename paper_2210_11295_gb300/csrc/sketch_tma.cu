@@ -1,0 +1,446 @@
+// Block SRHT sketch, CUDA-core variant with a TMA-fed shared-memory ring
+// (the streaming form of K1 used when A's layout allows 2-D TMA).
+//
+// Same arithmetic as k_sketch_chunked (see sketch_kernels.cuh): per R2-row
+// chunk of a W-column panel, D^(i) signs, the R2-point Walsh-Hadamard
+// transform (tensor form of H, Sec. 2) and the sampled rows with the outer
+// Kronecker-factor and Dt^(i) signs, accumulated over the chunks a CTA owns
+// (eq. 2.4 block sum), partials reduced in a fixed order.  Here one thread
+// streams the chunks with cp.async.bulk.tensor into a STAGES-deep ring
+// guarded by mbarriers, so HBM reads of later chunks overlap the butterflies
+// and the gather of the current one.  FP32 inputs are transformed in place
+// in the staged chunk; 16-bit inputs are widened into a separate FP32 tile.
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "sketch.cuh"
+#include "sketch_kernels.cuh"
+#include "tma.cuh"
+
+namespace bsrht {
+
+namespace {
+
+constexpr uint32_t kWaitLimit = 1u << 22;  // bounded mbarrier waits (each try_wait may sleep)
+
+// Ring depth: three 64 KB FP32 stages, or four 32 KB 16-bit stages plus the
+// 64 KB FP32 tile.
+template <typename Tin>
+constexpr int stages_for() {
+  return sizeof(Tin) == 4 ? 3 : 4;
+}
+
+template <typename Tin, int W, int NT, int R2, int JM, int STAGES>
+struct TmaShape {
+  static constexpr int NRL = NT / W;
+  static constexpr int E = R2 / NRL;
+  static constexpr int Q = E / NRL;
+  static constexpr int LOG_R2 = ilog2c(R2);
+  static constexpr int JG = JM * NRL;
+  static constexpr int DW = R2 / 64;
+  static constexpr bool kInPlace = sizeof(Tin) == 4;
+  static constexpr int BOXR = R2 < 256 ? R2 : 256;
+  static constexpr size_t stage_bytes = sizeof(Tin) * (size_t)R2 * W;
+  static constexpr size_t tile_bytes = kInPlace ? 0 : sizeof(float) * (size_t)R2 * W;
+  static constexpr size_t meta_bytes = 2 * sizeof(uint32_t) * JG + sizeof(uint64_t) * STAGES;
+  static constexpr size_t smem_bytes() { return STAGES * stage_bytes + tile_bytes + meta_bytes + 128; }
+  static_assert(NT % W == 0 && E >= NRL && E % NRL == 0, "thread layout");
+  static_assert(R2 >= 64 && R2 % BOXR == 0, "chunk rows");
+  static_assert(JG % 64 == 0, "sketch-row groups on 64-bit words");
+};
+
+template <typename Tin>
+__device__ __forceinline__ float widen(Tin v) {
+  if constexpr (sizeof(Tin) == 4)
+    return v;
+  else
+    return Elem<Tin>::to_f32(v);
+}
+
+// Sign tables for the TMA path.  dmtab[(i*nch + a)*16 + rl] holds, at bit e,
+// the D^(i) sign of row rl + 16e of chunk a of block i (the 32 rows a thread
+// of row lane rl owns); dttab holds the Dt^(i) words of the launch's sketch
+// rows.
+__global__ void k_sign_tables(uint64_t seed, int p, int64_t nch, int64_t j0, int64_t tw, uint32_t* __restrict__ dmtab,
+                              uint64_t* __restrict__ dttab) {
+  const int64_t nm = (int64_t)p * nch * 16;
+  const int64_t total = nm + (int64_t)p * tw;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    if (idx < nm) {
+      const int rl = (int)(idx & 15);
+      const int64_t ia = idx >> 4, i = ia / nch, a = ia - i * nch;
+      uint32_t m = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {  // rows 64w + 16q + rl, q < 4
+        const uint64_t x = (sign_word(seed, kStreamD, (uint64_t)i, (uint64_t)(a * 8 + w)) >> rl) & 0x0001000100010001ull;
+        m |= ((uint32_t)(x | (x >> 15) | (x >> 30) | (x >> 45)) & 0xFu) << (4 * w);
+      }
+      dmtab[idx] = m;
+    } else {
+      const int64_t e = idx - nm, i = e / tw, w = e - i * tw;
+      dttab[e] = sign_word(seed, kStreamDt, (uint64_t)i, (uint64_t)((j0 >> 6) + w));
+    }
+  }
+}
+
+template <typename Tin, int W, int NT, int R2, int JM, int STAGES>
+__global__ void __launch_bounds__(NT, 1)
+    k_sketch_tma(const __grid_constant__ CUtensorMap tmap, SketchArgs g, const uint32_t* __restrict__ dmtab,
+                 const uint64_t* __restrict__ dttab, int64_t tw, int* __restrict__ err) {
+  using S = TmaShape<Tin, W, NT, R2, JM, STAGES>;
+  constexpr int NRL = S::NRL, E = S::E, Q = S::Q, JG = S::JG, BOXR = S::BOXR;
+  static_assert(W == 32 && NRL == 16 && E == 32 && R2 == 512, "sign masks assume 16 row lanes x 32 rows");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((128 - (reinterpret_cast<uintptr_t>(smem_raw) & 127)) & 127);
+  Tin* stage = reinterpret_cast<Tin*>(base);                                   // [STAGES][R2][W]
+  float* tile_sep = reinterpret_cast<float*>(base + STAGES * S::stage_bytes);  // [R2][W] (16-bit inputs)
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(base + STAGES * S::stage_bytes + S::tile_bytes);  // s_lo * W
+  uint32_t* s_hi = s_off + JG;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_hi + JG);
+
+  const int tid = threadIdx.x;
+  const int cg = tid % W;  // == lane
+  const int rl = tid / W;  // == warp
+  const int jn = (int)g.jn;
+  const int64_t t_begin = (int64_t)blockIdx.x * g.T / g.G;
+  const int64_t t_end = (int64_t)(blockIdx.x + 1) * g.T / g.G;
+  const int64_t ntiles = t_end - t_begin;
+
+  // Tile t = (panel pc, block i, chunk a) in panel-major order; iterators
+  // advance without divisions.
+  struct TileIt {
+    int64_t pc, i, a;
+    __device__ void next(int64_t nch, int p) {
+      if (++a == nch) {
+        a = 0;
+        if (++i == p) {
+          i = 0;
+          ++pc;
+        }
+      }
+    }
+  };
+  auto tile_at = [&](int64_t t) {
+    TileIt it;
+    it.pc = t / g.C;
+    const int64_t c = t - it.pc * g.C;
+    it.i = c / g.nch;
+    it.a = c - it.i * g.nch;
+    return it;
+  };
+  TileIt iss = tile_at(t_begin);  // next tile to issue (thread 0 only)
+  int64_t issued = 0;
+  auto issue_next = [&]() {  // TMA for the CTA's next tile into stage issued % STAGES
+    const int s = (int)(issued % STAGES);
+    Tin* dst = stage + (size_t)s * R2 * W;
+    mbar_arrive_expect_tx(&bar[s], (uint32_t)S::stage_bytes);
+    const int32_t x = (int32_t)(iss.pc * W);
+    const int64_t y0 = iss.i * g.rb + iss.a * R2;
+#pragma unroll
+    for (int h = 0; h < R2 / BOXR; ++h)
+      tma_load_2d(dst + (size_t)h * BOXR * W, &tmap, &bar[s], x, (int32_t)(y0 + h * BOXR));
+    iss.next(g.nch, g.p);
+    ++issued;
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  for (int jl = tid; jl < JG; jl += NT) {
+    uint32_t off = 0, hi = 0;
+    if (jl < jn) {
+      const uint64_t sv = sample_word(g.seed, (uint64_t)(g.j0 + jl)) & (uint64_t)(g.r - 1);
+      off = (uint32_t)(sv & (R2 - 1)) * W;
+      hi = (uint32_t)(sv >> S::LOG_R2);
+    }
+    s_off[(jl % NRL) * JM + jl / NRL] = off;  // [row lane][u]: jl = rl + NRL * u
+    s_hi[jl] = hi;
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int64_t k = 0; k < STAGES && k < ntiles; ++k) issue_next();
+
+  // Lane cg of row lane rl evaluates the outer-factor sign of sketch row
+  // jl = rl + NRL * (32 h + cg); its s_hi never changes, its Dt^(i) word only
+  // with the block.
+  uint32_t my_hi[JM / 32];
+  uint64_t my_dt[JM / 32];
+  int64_t dt_block = -1;
+#pragma unroll
+  for (int h = 0; h < JM / 32; ++h) {
+    const int jl = rl + NRL * (32 * h + cg);
+    my_hi[h] = s_hi[jl];
+    my_dt[h] = 0;
+  }
+
+  float acc[JM];
+#pragma unroll
+  for (int u = 0; u < JM; ++u) acc[u] = 0.f;
+  int64_t cur_pc = -1;
+  float* part = static_cast<float*>(g.part);
+  auto flush = [&](int64_t pc) {
+    float* dst = part + ((int64_t)blockIdx.x + pc) * (int64_t)jn * W + cg;
+#pragma unroll
+    for (int u = 0; u < JM; ++u) {
+      const int jl = rl + NRL * u;
+      if (jl < jn) dst[(int64_t)jl * W] = acc[u];
+    }
+  };
+
+  TileIt cur = tile_at(t_begin);
+  uint32_t dmask_next = ntiles > 0 ? __ldg(dmtab + (cur.i * g.nch + cur.a) * 16 + rl) : 0u;
+  int s = 0;
+  uint32_t parity = 0;
+  for (int64_t k = 0; k < ntiles; ++k, cur.next(g.nch, g.p)) {
+    const int64_t pc = cur.pc, i = cur.i, a = cur.a;
+    if (pc != cur_pc) {
+      if (cur_pc >= 0) flush(cur_pc);
+#pragma unroll
+      for (int u = 0; u < JM; ++u) acc[u] = 0.f;
+      cur_pc = pc;
+    }
+    const int64_t rows_i = min(g.rb, g.n - i * g.rb);
+    const int64_t row0 = a * R2;
+    const int nvalid = (int)min((int64_t)R2, rows_i - row0);
+    // This thread's 32 D^(i) signs (rows rl + 16e) and, by a warp ballot, the
+    // outer-factor x Dt^(i) signs of its row lane's sketch rows jl = rl + 16u.
+    const uint32_t dmask = dmask_next;
+    {  // prefetch the next chunk's D mask
+      TileIt nx = cur;
+      nx.next(g.nch, g.p);
+      if (k + 1 < ntiles) dmask_next = __ldg(dmtab + (nx.i * g.nch + nx.a) * 16 + rl);
+    }
+    if (i != dt_block) {
+#pragma unroll
+      for (int h = 0; h < JM / 32; ++h) {
+        const int jl = rl + NRL * (32 * h + cg);
+        my_dt[h] = jl < jn ? __ldg(dttab + i * tw + (jl >> 6)) : 0ull;
+      }
+      dt_block = i;
+    }
+    uint32_t gmask[JM / 32];
+#pragma unroll
+    for (int h = 0; h < JM / 32; ++h) {
+      const int jl = rl + NRL * (32 * h + cg);
+      const uint32_t sg = (uint32_t)((__popc(my_hi[h] & (uint32_t)a) + (int)((my_dt[h] >> (jl & 63)) & 1ull)) & 1);
+      gmask[h] = __ballot_sync(0xffffffffu, jl < jn ? sg : 0u);
+    }
+    const bool ok = mbar_wait_bounded(&bar[s], parity, kWaitLimit);
+
+    Tin* st = stage + (size_t)s * R2 * W;
+    float* tile = S::kInPlace ? reinterpret_cast<float*>(st) : tile_sep;
+    // Register phase: rows rl + NRL*e, D^(i) signs, high log2(E) bits.
+    float v[E];
+    if (nvalid == R2) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const float x = widen<Tin>(st[(rl + NRL * e) * W + cg]);
+        v[e] = __int_as_float(__float_as_int(x) ^ (int)((dmask << (31 - e)) & 0x80000000u));
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int rr = rl + NRL * e;
+        const float x = rr < nvalid ? widen<Tin>(st[rr * W + cg]) : 0.f;
+        v[e] = __int_as_float(__float_as_int(x) ^ (int)((dmask << (31 - e)) & 0x80000000u));
+      }
+    }
+    fwht_regs<float, E>(v);
+#pragma unroll
+    for (int e = 0; e < E; ++e) tile[(rl + NRL * e) * W + cg] = v[e];
+    // One barrier both publishes the register phase and makes a failed
+    // (bounded) wait CTA-uniform: data read after a failed wait is garbage
+    // but nothing reaches global memory before this check.
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(err, 1);
+        for (int64_t kk = (issued - STAGES < k ? k : issued - STAGES); kk < issued; ++kk)
+          mbar_wait_bounded(&bar[kk % STAGES], (uint32_t)((kk / STAGES) & 1), kWaitLimit);
+      }
+      __syncthreads();
+      return;
+    }
+    // In place (FP32): every thread has finished the previous chunk, so its
+    // stage is free; refill it (the 16-bit path refills at the chunk end).
+    if constexpr (S::kInPlace) {
+      if (tid == 0 && k >= 1 && issued < ntiles) {
+        fence_proxy_async_smem();
+        issue_next();
+      }
+    }
+    // Exchange phase: rows NRL*h + b, low log2(NRL) bits.
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      float w2[NRL];
+      const int h = rl * Q + q;
+#pragma unroll
+      for (int b = 0; b < NRL; ++b) w2[b] = tile[(NRL * h + b) * W + cg];
+      fwht_regs<float, NRL>(w2);
+#pragma unroll
+      for (int b = 0; b < NRL; ++b) tile[(NRL * h + b) * W + cg] = w2[b];
+    }
+    __syncthreads();
+    // Sampled rows (offsets s_lo * W) with the signs of gmask.
+    const uint4* offv = reinterpret_cast<const uint4*>(s_off + rl * JM);
+    const float* tcol = tile + cg;
+#pragma unroll
+    for (int u4 = 0; u4 < JM / 4; ++u4) {
+      const uint4 o = offv[u4];
+      const uint32_t oo[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int u = 4 * u4 + q;
+        const float tv = tcol[oo[q]];
+        const uint32_t sb = (gmask[u >> 5] << (31 - (u & 31))) & 0x80000000u;
+        acc[u] += __int_as_float(__float_as_int(tv) ^ (int)sb);
+      }
+    }
+    if constexpr (!S::kInPlace) {
+      __syncthreads();  // stage s and the separate tile are free again
+      if (tid == 0 && issued < ntiles) {
+        fence_proxy_async_smem();
+        issue_next();
+      }
+    }
+    if (++s == STAGES) {
+      s = 0;
+      parity ^= 1u;
+    }
+  }
+  if (cur_pc >= 0) flush(cur_pc);
+}
+
+// Fixed-order reduce; NaN output if any CTA reported a failed wait.
+template <int W>
+__global__ void k_sketch_reduce_checked(SketchArgs g, float* __restrict__ out, int64_t ldo, float scale,
+                                        const int* __restrict__ err) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = g.jn * g.m;
+  if (idx >= total) return;
+  const int64_t jl = idx / g.m;
+  const int64_t col = idx - jl * g.m;
+  if (*err) {
+    out[(g.j0 + jl) * ldo + col] = __int_as_float(0x7fc00000);
+    return;
+  }
+  const int64_t pc = col / W;
+  const int cw = (int)(col - pc * W);
+  const int64_t lo = pc * g.C, hi = lo + g.C;
+  int64_t cta = lo * g.G / g.T;
+  if (cta > 0) --cta;
+  while (cta < g.G && (cta + 1) * g.T / g.G <= lo) ++cta;
+  const float* part = static_cast<const float*>(g.part);
+  float s = 0.f;
+  for (; cta < g.G && cta * g.T / g.G < hi; ++cta) s += part[((cta + pc) * g.jn + jl) * W + cw];
+  out[(g.j0 + jl) * ldo + col] = s * scale;
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static std::once_flag once;
+  static EncodeFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+template <typename Tin, int JM>
+int launch_tma(const SketchPlan& plan, const SketchArgs& a, const CUtensorMap& map, int* err, uint64_t* dtab,
+               uint64_t* dttab, void* out, int64_t ldo, cudaStream_t stream) {
+  constexpr int W = 32, NT = 512, R2 = 512, STAGES = stages_for<Tin>();
+  using S = TmaShape<Tin, W, NT, R2, JM, STAGES>;
+  auto kern = k_sketch_tma<Tin, W, NT, R2, JM, STAGES>;
+  const size_t smem = S::smem_bytes();
+  BSRHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t tw = (a.jn + 63) / 64;
+  const int64_t tot = (int64_t)plan.p * (plan.nch * 16 + tw);
+  uint32_t* dmtab = reinterpret_cast<uint32_t*>(dtab);
+  k_sign_tables<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, stream>>>(a.seed, plan.p, plan.nch,
+                                                                                          a.j0, tw, dmtab, dttab);
+  BSRHT_CUDA_TRY(cudaGetLastError());
+  kern<<<plan.G, NT, smem, stream>>>(map, a, dmtab, dttab, tw, err);
+  BSRHT_CUDA_TRY(cudaGetLastError());
+  const int64_t total = a.jn * a.m;
+  const float scale = (float)(1.0 / sqrt((double)plan.l));
+  k_sketch_reduce_checked<W><<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(a, static_cast<float*>(out), ldo,
+                                                                                  scale, err);
+  BSRHT_CUDA_TRY(cudaGetLastError());
+  note_launches(3);
+  return BSRHT_OK;
+}
+
+template <typename Tin, int JM>
+int occ_tma() {
+  constexpr int W = 32, NT = 512, R2 = 512, STAGES = stages_for<Tin>();
+  using S = TmaShape<Tin, W, NT, R2, JM, STAGES>;
+  auto kern = k_sketch_tma<Tin, W, NT, R2, JM, STAGES>;
+  const size_t smem = S::smem_bytes();
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess) return 0;
+  return occ;
+}
+
+}  // namespace
+
+bool make_tensor_map_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dtype, size_t elem_bytes,
+                        uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_cols, uint32_t box_rows) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {ld * elem_bytes};
+  const cuuint32_t box[2] = {box_cols, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+
+int sketch_occupancy_tma(const SketchPlan& plan) {
+  switch (plan.dtype) {
+    case BSRHT_F32: return plan.JM == 32 ? occ_tma<float, 32>() : occ_tma<float, 64>();
+    case BSRHT_BF16: return plan.JM == 32 ? occ_tma<__nv_bfloat16, 32>() : occ_tma<__nv_bfloat16, 64>();
+    case BSRHT_F16: return plan.JM == 32 ? occ_tma<__half, 32>() : occ_tma<__half, 64>();
+  }
+  return 0;
+}
+
+int sketch_launch_tma(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo, int* err,
+                      uint64_t* dtab, uint64_t* dttab, cudaStream_t stream) {
+  CUtensorMap map;
+  const CUtensorMapDataType dt = plan.dtype == BSRHT_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : plan.dtype == BSRHT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  const size_t es = plan.dtype == BSRHT_F32 ? 4 : 2;
+  if (!make_tensor_map_2d(&map, a.A, dt, es, (uint64_t)plan.n, (uint64_t)plan.m, (uint64_t)plan.lda, 32,
+                          256))
+    return BSRHT_EUNSUP;
+  switch (plan.dtype) {
+    case BSRHT_F32:
+      return plan.JM == 32 ? launch_tma<float, 32>(plan, a, map, err, dtab, dttab, out, ldo, stream)
+                           : launch_tma<float, 64>(plan, a, map, err, dtab, dttab, out, ldo, stream);
+    case BSRHT_BF16:
+      return plan.JM == 32 ? launch_tma<__nv_bfloat16, 32>(plan, a, map, err, dtab, dttab, out, ldo, stream)
+                           : launch_tma<__nv_bfloat16, 64>(plan, a, map, err, dtab, dttab, out, ldo, stream);
+    case BSRHT_F16:
+      return plan.JM == 32 ? launch_tma<__half, 32>(plan, a, map, err, dtab, dttab, out, ldo, stream)
+                           : launch_tma<__half, 64>(plan, a, map, err, dtab, dttab, out, ldo, stream);
+  }
+  return BSRHT_EINVAL;
+}
+
+}  // namespace bsrht

@@ -110,12 +110,24 @@ def lowrank_noise(n: int, m: int, rank: int = 1000, noise: float = 1e-4,
     return np.ascontiguousarray(a.astype(dtype))
 
 
+def _orthonormalize_device(g, torch):
+    """Orthonormal basis of the columns of the tall device matrix g: Gram on
+    the device, eigen-decomposition of the small Gram on the host (numpy),
+    then g V diag(lambda^-1/2) twice (Gaussian g is well conditioned)."""
+    for _ in range(2):
+        gram = (g.T @ g).double().cpu().numpy()
+        lam, v = np.linalg.eigh(0.5 * (gram + gram.T))
+        w = torch.from_numpy(v / np.sqrt(lam)).to(device=g.device, dtype=g.dtype)
+        g = g @ w
+    return g
+
+
 def lowrank_noise_device(n: int, m: int, rank: int = 1000, noise: float = 1e-4,
                          seed: int = 1236, dtype=None, device="cuda"):
     """Device version of :func:`lowrank_noise` (torch; same distribution).
 
-    Built in FP32 (FP64 when ``dtype`` is float64) in row panels so that the
-    peak extra memory stays near one copy of A.
+    G1 and G2 are Gaussian factors with orthonormalised columns; A is built in
+    row panels so that the peak extra memory stays near one copy of A.
     """
     import torch
 
@@ -124,12 +136,8 @@ def lowrank_noise_device(n: int, m: int, rank: int = 1000, noise: float = 1e-4,
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
     rank = min(rank, n, m)
-    g1 = torch.randn(n, rank, generator=gen, device=device, dtype=work)
-    g1, r1 = torch.linalg.qr(g1)
-    g1 *= torch.sign(torch.diagonal(r1)).clamp(min=0) * 2 - 1
-    g2 = torch.randn(m, rank, generator=gen, device=device, dtype=work)
-    g2, r2 = torch.linalg.qr(g2)
-    g2 *= torch.sign(torch.diagonal(r2)).clamp(min=0) * 2 - 1
+    g1 = _orthonormalize_device(torch.randn(n, rank, generator=gen, device=device, dtype=work), torch)
+    g2 = _orthonormalize_device(torch.randn(m, rank, generator=gen, device=device, dtype=work), torch)
     sigma = torch.arange(1, rank + 1, device=device, dtype=work) ** -2.0
     g2s = (g2 * sigma).T.contiguous()
     a = torch.empty(n, m, device=device, dtype=dtype)
