@@ -304,6 +304,15 @@ def run_ours(args):
     step_ms = t_start.elapsed_time(t_end) / args.steps
     step_ms = max_over_ranks(world, step_ms)
 
+    # Per-stage times of one extra traced step (library CUDA events).
+    stages = None
+    if mode == "full":
+        lib.bsrht_profile_enable(True)
+        step(10_000)
+        torch.cuda.synchronize()
+        stages = {name: round(ms, 3) for name, ms in lib.bsrht_profile_stages()}
+        lib.bsrht_profile_enable(False)
+
     # End to end through the C ABI from pinned host buffers.
     a_host = a.cpu().pin_memory()
     e2e_ms = None
@@ -369,6 +378,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
     }
+    if stages:
+        line["stages_ms"] = stages
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:

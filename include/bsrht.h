@@ -185,6 +185,16 @@ int bsrht_nystrom_workspace(int64_t n, int32_t k, int64_t l, int32_t p,
  * The caller must make sure no call that uses the pool is still running. */
 int bsrht_release_pool(void);
 
+/* Stage tracing of bsrht_rsvd / bsrht_nystrom for the calling host thread:
+ * when enabled, each call records CUDA events between its stages on its
+ * stream (sketch, orthogonalisation of the sketch, second pass, tall QR,
+ * small SVD, output factors; Nystrom: sketch, core, Z, tall QR, small SVD,
+ * factors).  bsrht_profile_stages waits for those events and returns up to
+ * cap stage names (32 bytes each, NUL-terminated, in names) and durations in
+ * milliseconds (ms); *count receives the number of stages of the last call. */
+int bsrht_profile_enable(int on);
+int bsrht_profile_stages(char* names, double* ms, int cap, int* count);
+
 /* Number of CUDA kernels the library has launched in this process (all
  * devices, all threads).  Diagnostic counter for benchmarks and tests. */
 uint64_t bsrht_kernel_launches(void);

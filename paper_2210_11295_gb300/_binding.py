@@ -69,6 +69,9 @@ def _load() -> ctypes.CDLL:
         "bsrht_nystrom_workspace": (ctypes.c_int, [i64, i32, i64, i32, po, ctypes.POINTER(sz)]),
         "bsrht_release_pool": (ctypes.c_int, []),
         "bsrht_kernel_launches": (ctypes.c_uint64, []),
+        "bsrht_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+        "bsrht_profile_stages": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -207,6 +210,25 @@ def bsrht_nystrom(a: torch.Tensor, k: int, l: int, p: int, seed: int, variant: i
 def bsrht_kernel_launches() -> int:
     """Cumulative count of CUDA kernels the library has launched."""
     return int(lib.bsrht_kernel_launches())
+
+
+def bsrht_profile_enable(on: bool = True) -> None:
+    """Record CUDA events between the stages of bsrht_rsvd / bsrht_nystrom."""
+    _check(lib.bsrht_profile_enable(1 if on else 0), "bsrht_profile_enable")
+
+
+def bsrht_profile_stages() -> list[tuple[str, float]]:
+    """(stage name, milliseconds) of the last traced call on this thread."""
+    cap = 64
+    names = ctypes.create_string_buffer(32 * cap)
+    ms = (ctypes.c_double * cap)()
+    cnt = ctypes.c_int(0)
+    _check(lib.bsrht_profile_stages(names, ms, cap, ctypes.byref(cnt)), "bsrht_profile_stages")
+    out = []
+    for i in range(min(cnt.value, cap)):
+        nm = names.raw[32 * i:32 * i + 32].split(b"\0", 1)[0].decode()
+        out.append((nm, float(ms[i])))
+    return out
 
 
 def bsrht_release_pool() -> None:

@@ -2,6 +2,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 #include "dla.cuh"
@@ -279,9 +280,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // One-sided (Hestenes) Jacobi on the columns of M with round-robin pairs;
-// one warp per column pair, a grid-wide barrier between rounds.
-__global__ void k_jacobi(double* __restrict__ M, double* __restrict__ V, int l, int lp, double tol,
-                         int max_sweeps, int* __restrict__ rot_counts, int* __restrict__ status) {
+// one warp per column pair, a grid-wide barrier between rounds.  A warp loads
+// its two columns of M and of V into registers (JR values per lane), forms
+// the three inner products, rotates in registers and stores once, so each
+// round costs one round trip to L2 instead of one per element.
+template <int JR>
+__global__ void k_jacobi(double* __restrict__ M, double* __restrict__ V, int l, int lp, double tol, int max_sweeps,
+                         int* __restrict__ rot_counts, int* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
   const int lane = threadIdx.x & 31;
   const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
@@ -297,41 +302,41 @@ __global__ void k_jacobi(double* __restrict__ M, double* __restrict__ V, int l, 
           q = t;
         }
         if (q >= l) continue;  // padding column
-        double* a = M + (int64_t)p * l;
-        double* b = M + (int64_t)q * l;
-        double al0 = 0, al1 = 0, be0 = 0, be1 = 0, ga0 = 0, ga1 = 0;
-        int i = lane;
-        for (; i + 32 < l; i += 64) {
-          const double x0 = a[i], y0 = b[i], x1 = a[i + 32], y1 = b[i + 32];
-          al0 = fma(x0, x0, al0);
-          be0 = fma(y0, y0, be0);
-          ga0 = fma(x0, y0, ga0);
-          al1 = fma(x1, x1, al1);
-          be1 = fma(y1, y1, be1);
-          ga1 = fma(x1, y1, ga1);
+        double* __restrict__ a = M + (int64_t)p * l;
+        double* __restrict__ b = M + (int64_t)q * l;
+        double* __restrict__ va = V + (int64_t)p * l;
+        double* __restrict__ vb = V + (int64_t)q * l;
+        double x[JR], y[JR], vx[JR], vy[JR];
+#pragma unroll
+        for (int e = 0; e < JR; ++e) {
+          const int r = lane + 32 * e;
+          const bool in = r < l;
+          x[e] = in ? a[r] : 0.0;
+          y[e] = in ? b[r] : 0.0;
+          vx[e] = in ? va[r] : 0.0;
+          vy[e] = in ? vb[r] : 0.0;
         }
-        if (i < l) {
-          const double x0 = a[i], y0 = b[i];
-          al0 = fma(x0, x0, al0);
-          be0 = fma(y0, y0, be0);
-          ga0 = fma(x0, y0, ga0);
+        double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+        for (int e = 0; e < JR; ++e) {
+          al = fma(x[e], x[e], al);
+          be = fma(y[e], y[e], be);
+          ga = fma(x[e], y[e], ga);
         }
-        const double alpha = warp_sum(al0 + al1), beta = warp_sum(be0 + be1), gamma = warp_sum(ga0 + ga1);
+        const double alpha = warp_sum(al), beta = warp_sum(be), gamma = warp_sum(ga);
         if (gamma == 0.0 || !(fabs(gamma) > tol * sqrt(alpha * beta))) continue;
         const double zeta = (beta - alpha) / (2.0 * gamma);
         const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-        for (int r = lane; r < l; r += 32) {
-          const double x = a[r], y = b[r];
-          a[r] = c * x - s * y;
-          b[r] = s * x + c * y;
-        }
-        double* va = V + (int64_t)p * l;
-        double* vb = V + (int64_t)q * l;
-        for (int r = lane; r < l; r += 32) {
-          const double x = va[r], y = vb[r];
-          va[r] = c * x - s * y;
-          vb[r] = s * x + c * y;
+#pragma unroll
+        for (int e = 0; e < JR; ++e) {
+          const int r = lane + 32 * e;
+          if (r < l) {
+            a[r] = c * x[e] - s * y[e];
+            b[r] = s * x[e] + c * y[e];
+            va[r] = c * vx[e] - s * vy[e];
+            vb[r] = s * vx[e] + c * vy[e];
+          }
         }
         if (lane == 0) atomicAdd(&rot_counts[sweep], 1);
       }
@@ -397,17 +402,32 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
   k_init_identity_cols<<<blocks_for(l * l, 256), 256, 0, d.s>>>(Vc, l);
   DLA_LAUNCH_CHECK();
   int li = (int)l, lp = (int)(l + (l & 1));
-  double tol = 1e-15;
-  int dev = 0, occ = 0;
-  BSRHT_CUDA_TRY(cudaGetDevice(&dev));
-  const int threads = 256;
-  BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi, threads, 0));
-  const int pairs = lp / 2;
-  int blocks = std::max(1, std::min((pairs + threads / 32 - 1) / (threads / 32), num_sms() * std::max(occ, 1)));
+  // Rotate only while the cosine of the pair exceeds sqrt(l) eps (the usual
+  // one-sided Jacobi threshold); a tighter one keeps rotating at noise level.
+  double tol = std::max(1e-15, std::sqrt((double)l) * 0x1.0p-52);
   int msw = max_sweeps;
+  // One column pair per warp, two warps per block: spreads the l/2 pairs of a
+  // round over as many SMs as possible (FP64 throughput is per SM).
+  const int threads = 64;
+  const int pairs = lp / 2;
   void* args[] = {&colsM, &Vc, &li, &lp, &tol, &msw, &rot, (void*)&d.status};
+  auto launch = [&](auto kern) -> int {
+    int occ = 0;
+    BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0));
+    const int blocks =
+        std::max(1, std::min((pairs + threads / 32 - 1) / (threads / 32), num_sms() * std::max(occ, 1)));
+    BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(threads), args, 0, d.s));
+    return BSRHT_OK;
+  };
   if (l > 1) {
-    BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(blocks), dim3(threads), args, 0, d.s));
+    int st;
+    if (l <= 128) st = launch(k_jacobi<4>);
+    else if (l <= 256) st = launch(k_jacobi<8>);
+    else if (l <= 512) st = launch(k_jacobi<16>);
+    else if (l <= 1024) st = launch(k_jacobi<32>);
+    else if (l <= 2048) st = launch(k_jacobi<64>);
+    else return BSRHT_EUNSUP;
+    if (st != BSRHT_OK) return st;
   }
   k_col_norms<<<blocks_for(l, 8), 256, 0, d.s>>>(colsM, sig, l);
   DLA_LAUNCH_CHECK();

@@ -68,6 +68,18 @@ int tri_inverse(const Dla& d, const double* L, double* LT, double* Rinv, int64_t
 // by descending sigma into U (l x l row-major, U[i][c]) and Vout (row-major).
 int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout);
 
+// Tensor-core (tcgen05) GEMM in FP32 accuracy (three TF32 products):
+// C (M x N, FP32 or FP64 in tc_out, ldc) = A (M x K, FP32, lda) * B, with B
+// either K x N (FP32 or FP64, ldb; transposed into scratch) or, when
+// b_kmajor, given as Bt = B^T (N x K, FP32, ldb).  gram: C = A A^T (B = A^T),
+// only tiles on or above the diagonal are formed and the rest mirrored.
+// A and Bt need 16-byte aligned rows (gemm_tc_eligible).
+int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, DT tb,
+            const void* B, int64_t ldb, bool b_kmajor, DT tc_out, void* C, int64_t ldc, bool gram);
+bool gemm_tc_eligible(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda);
+// Bt (N x ldk, FP32) = B^T for B K x N (FP32 or FP64, ldb); Bt[:, K:ldk] = 0.
+int transpose_to_f32(const Dla& d, DT tb, const void* B, int64_t K, int64_t N, int64_t ldb, float* Bt, int64_t ldk);
+
 // Householder QR of the tall FP64 X (rows x l, rows >= l), X overwritten by
 // the reflectors; Q (rows x l, orthonormal columns) is formed explicitly.
 // Robust to rank deficiency (a zero column gives an identity reflector).

@@ -1,0 +1,145 @@
+// Host side of the tcgen05 3xTF32 GEMM (gemm_tc.cuh).
+#include <algorithm>
+
+#include "dla.cuh"
+#include "gemm_tc.cuh"
+#include "sketch.cuh"
+
+namespace bsrht {
+
+#define TRY_TC(expr)                   \
+  do {                                 \
+    const int st_ = (expr);            \
+    if (st_ != BSRHT_OK) return st_;   \
+  } while (0)
+
+namespace {
+
+// Bt[n][k] = B[k][n] in FP32 (B is K x N, FP32 or FP64, leading dimension
+// ldb); columns k in [K, ldk) are zero.
+template <typename TB>
+__global__ void k_transpose_f32(const TB* __restrict__ B, int64_t K, int64_t N, int64_t ldb, float* __restrict__ Bt,
+                                int64_t ldk) {
+  __shared__ float tile[32][33];
+  const int64_t k0 = (int64_t)blockIdx.x * 32, nb = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t k = k0 + r, n = nb + tx;
+    tile[r][tx] = (k < K && n < N) ? (float)B[k * ldb + n] : 0.f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t n = nb + r, k = k0 + tx;
+    if (n < N && k < ldk) Bt[n * ldk + k] = tile[tx][r];
+  }
+}
+
+// Fixed-order sum of the split-K partials; for a Gram product the tiles
+// skipped below the diagonal are read from their mirror images.
+template <typename TC>
+__global__ void k_tc_reduce(const float* __restrict__ P, TC* __restrict__ C, int64_t M, int64_t N, int64_t ldc,
+                            int splits, int gram) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * N) return;
+  const int64_t i = idx / N, j = idx - i * N;
+  int64_t si = i, sj = j;
+  if (gram && tc::tile_below_diagonal(i / tc::BM, j / tc::BN)) {
+    si = j;
+    sj = i;
+  }
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += (double)P[(int64_t)z * M * N + si * N + sj];
+  C[i * ldc + j] = (TC)s;
+}
+
+template <typename TC>
+int launch_tc(const Dla& d, const CUtensorMap& ma, const CUtensorMap& mb, tc::GemmTcArgs g, dim3 grid) {
+  const size_t smem = tc::smem_bytes();
+  BSRHT_CUDA_TRY(cudaFuncSetAttribute(tc::k_gemm_tf32x3<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  tc::k_gemm_tf32x3<TC><<<grid, tc::THREADS, smem, d.s>>>(ma, mb, g);
+  BSRHT_CUDA_TRY(cudaGetLastError());
+  return BSRHT_OK;
+}
+
+}  // namespace
+
+bool gemm_tc_eligible(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda) {
+  return M >= 1 && N >= 1 && K >= 8 && (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0;
+}
+
+int transpose_to_f32(const Dla& d, DT tb, const void* B, int64_t K, int64_t N, int64_t ldb, float* Bt, int64_t ldk) {
+  dim3 g((unsigned)((ldk + 31) / 32), (unsigned)((N + 31) / 32));
+  if (tb == DT::F32)
+    k_transpose_f32<float><<<g, 256, 0, d.s>>>(static_cast<const float*>(B), K, N, ldb, Bt, ldk);
+  else if (tb == DT::F64)
+    k_transpose_f32<double><<<g, 256, 0, d.s>>>(static_cast<const double*>(B), K, N, ldb, Bt, ldk);
+  else
+    return BSRHT_EUNSUP;
+  BSRHT_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  return BSRHT_OK;
+}
+
+int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, DT tb,
+            const void* B, int64_t ldb, bool b_kmajor, DT tc_out, void* C, int64_t ldc, bool gram) {
+  if (M <= 0 || N <= 0) return BSRHT_OK;
+  if (tc_out != DT::F32 && tc_out != DT::F64) return BSRHT_EUNSUP;
+  const float* Bt = static_cast<const float*>(B);
+  int64_t ldk = ldb;
+  if (!b_kmajor) {
+    ldk = (K + 3) / 4 * 4;
+    float* bt = static_cast<float*>(ar.take(sizeof(float) * (size_t)N * ldk));
+    if (!ar.ok()) return BSRHT_ENOMEM;
+    if (!ar.measure) TRY_TC(transpose_to_f32(d, tb, B, K, N, ldb, bt, ldk));
+    Bt = bt;
+  } else if (tb != DT::F32 || (ldk % 4) != 0) {
+    return BSRHT_EUNSUP;
+  }
+  const int64_t tm = (M + tc::BM - 1) / tc::BM, tn = (N + tc::BN - 1) / tc::BN;
+  int64_t tiles = 0;
+  for (int64_t bm = 0; bm < tm; ++bm)
+    for (int64_t bn = 0; bn < tn; ++bn) tiles += (gram && tc::tile_below_diagonal(bm, bn)) ? 0 : 1;
+  const int64_t nkb = (K + tc::BK - 1) / tc::BK;
+  // Split K when the tiles alone do not fill the GPU, and in any case so
+  // that no CTA folds more than 256 K blocks into its FP32 running sums.
+  int64_t splits = 1;
+  const int64_t target = (int64_t)num_sms();
+  if (tiles < target && nkb >= 16) splits = std::max<int64_t>(1, std::min<int64_t>((target + tiles - 1) / tiles, nkb / 8));
+  splits = std::max<int64_t>(splits, (nkb + 255) / 256);
+  if (gram && splits == 1) splits = 2;  // the mirror is applied by the reduce
+  splits = std::min<int64_t>(splits, 65535);
+  float* P = nullptr;
+  if (splits > 1) {
+    P = static_cast<float*>(ar.take(sizeof(float) * (size_t)splits * M * N));
+    if (!ar.ok()) return BSRHT_ENOMEM;
+  }
+  int* err = static_cast<int*>(ar.take(256));
+  if (!ar.ok()) return BSRHT_ENOMEM;
+  if (ar.measure) return BSRHT_OK;
+  CUtensorMap ma, mb;
+  if (!make_tensor_map_2d(&ma, A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)M, (uint64_t)K, (uint64_t)lda, tc::BK,
+                          tc::BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !make_tensor_map_2d(&mb, Bt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)N, (uint64_t)K, (uint64_t)ldk, tc::BK,
+                          tc::BN, CU_TENSOR_MAP_SWIZZLE_128B))
+    return BSRHT_EUNSUP;
+  BSRHT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), d.s));
+  if (tm * tn > 0x7FFFFFFF) return BSRHT_EUNSUP;
+  dim3 grid((unsigned)(tm * tn), 1u, (unsigned)splits);
+  tc::GemmTcArgs g{M, N, K, splits > 1 ? (void*)P : C, ldc, gram ? 1 : 0, err};
+  int st = (tc_out == DT::F32 || splits > 1) ? launch_tc<float>(d, ma, mb, g, grid) : launch_tc<double>(d, ma, mb, g, grid);
+  if (st != BSRHT_OK) return st;
+  int launches = 1;
+  if (splits > 1) {
+    const unsigned nb = (unsigned)((M * N + 255) / 256);
+    if (tc_out == DT::F32)
+      k_tc_reduce<float><<<nb, 256, 0, d.s>>>(P, static_cast<float*>(C), M, N, ldc, (int)splits, gram ? 1 : 0);
+    else
+      k_tc_reduce<double><<<nb, 256, 0, d.s>>>(P, static_cast<double*>(C), M, N, ldc, (int)splits, gram ? 1 : 0);
+    BSRHT_CUDA_TRY(cudaGetLastError());
+    ++launches;
+  }
+  note_launches(launches);
+  return BSRHT_OK;
+}
+
+}  // namespace bsrht

@@ -1,0 +1,318 @@
+// Tensor-core GEMM for the tall products of the low-rank drivers:
+//   C[M x N] = A[M x K] * B[K x N]  in FP32 accuracy on tcgen05 (TF32 MMAs).
+//
+// A (M x K) and Bt = B^T (N x K) are FP32 with K contiguous (K-major) and
+// are read by TMA with the 128-byte swizzle.  Each tile is split in shared
+// memory into a TF32-exact hi part (low 13 mantissa bits cleared) and lo =
+// x - hi, and the product is accumulated in TMEM as
+//   A_hi B_hi + A_hi B_lo + A_lo B_hi
+// (three TF32 MMAs; the dropped A_lo B_lo term and the TF32 truncation of the
+// lo parts leave a relative error of about 2^-21 per product, FP32 level).
+//
+// The tensor core's FP32 accumulation rounds toward zero, so an accumulator
+// that runs over all of K drifts by about (number of MMAs) x 2^-24 of its
+// value (1e-4 at K = 4096, worse on the all-positive sums of a Gram
+// diagonal).  Each K block of 32 (12 MMAs) is therefore accumulated into a
+// fresh TMEM buffer (two buffers, ping-pong) and the epilogue warps add it
+// into an FP32 running sum held in registers, rounding to nearest.
+//
+// CTA: 256 threads.  Warp 0 allocates TMEM and issues the TMA loads (one
+// thread), warp 1 issues the MMAs (one thread), warps 4-7 split the tiles,
+// fold the finished K blocks (tcgen05.ld of their 32 TMEM lanes) and store
+// the rows.  Tile 128 x 128 (UMMA M=128, N=128, K=8), K blocks of 32, a
+// 3-stage ring.  gridDim.z > 1 splits K: CTA z writes an FP32 partial to
+// C + z * M * N (leading dimension N) for a fixed-order FP64 reduce.  With
+// `gram` set (C = A A^T) tiles entirely below the diagonal are skipped.
+#pragma once
+
+#include <cuda.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "tma.cuh"
+
+namespace bsrht {
+
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3, THREADS = 256;
+constexpr uint32_t A_BYTES = BM * BK * 4;   // 16 KB
+constexpr uint32_t B_BYTES = BN * BK * 4;   // 16 KB
+constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo (hi parts via TMA)
+constexpr uint32_t TMEM_COLS = 2 * BN;      // two accumulator buffers
+constexpr uint32_t kWait = 1u << 24;
+constexpr size_t smem_bytes() { return 1024 + (size_t)STAGES * STAGE_BYTES + 256; }
+static_assert(STAGES * STAGE_BYTES + 1024 + 256 <= 227 * 1024, "shared memory");
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes in 8-row atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D FP32, A/B TF32, both K-major, M = BM, N = BN.
+constexpr uint32_t idesc_tf32() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct GemmTcArgs {
+  int64_t M, N, K;
+  void* C;      // TC output, or FP32 partials when gridDim.z > 1
+  int64_t ldc;
+  int gram;
+  int* err;
+};
+
+__host__ __device__ __forceinline__ bool tile_below_diagonal(int64_t bm, int64_t bn) {
+  return bm * BM >= (bn + 1) * BN;
+}
+
+// In-place split of n16 16-byte groups: hi keeps the TF32 bits, lo = x - hi.
+__device__ __forceinline__ void split_tf32(uint4* __restrict__ hi, uint4* __restrict__ lo, int t, int n16) {
+  for (int idx = t; idx < n16; idx += 128) {
+    const uint4 x = hi[idx];
+    uint4 h, l;
+    h.x = x.x & 0xFFFFE000u;
+    h.y = x.y & 0xFFFFE000u;
+    h.z = x.z & 0xFFFFE000u;
+    h.w = x.w & 0xFFFFE000u;
+    l.x = __float_as_uint(__uint_as_float(x.x) - __uint_as_float(h.x));
+    l.y = __float_as_uint(__uint_as_float(x.y) - __uint_as_float(h.y));
+    l.z = __float_as_uint(__uint_as_float(x.z) - __uint_as_float(h.z));
+    l.w = __float_as_uint(__uint_as_float(x.w) - __uint_as_float(h.w));
+    hi[idx] = h;
+    lo[idx] = l;
+  }
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gemm_tf32x3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, GemmTcArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(smem_raw) & 1023)) & 1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+  uint64_t* ready = full + STAGES;
+  uint64_t* empty = ready + STAGES;
+  uint64_t* accf = empty + STAGES;    // [2] K block finished in buffer b
+  uint64_t* accfree = accf + 2;       // [2] buffer b folded by the epilogue
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfree + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // blockIdx.x enumerates tiles row-major, so the N tiles of one row band run
+  // side by side and share its A tile through L2.
+  const int64_t tn = (g.N + BN - 1) / BN;
+  const int64_t bm = (int64_t)blockIdx.x / tn, bn = (int64_t)blockIdx.x - bm * tn;
+  const int64_t m0 = bm * BM, n0 = bn * BN;
+  if (g.gram && tile_below_diagonal(bm, bn)) return;  // uniform: before any barrier
+  const int nkb_all = (int)((g.K + BK - 1) / BK);
+  const int kb0 = (int)((int64_t)nkb_all * blockIdx.z / gridDim.z);
+  const int kb1 = (int)((int64_t)nkb_all * (blockIdx.z + 1) / gridDim.z);
+  const int nkb = kb1 - kb0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&ready[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&accfree[b], 4);
+    }
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool failed = false;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int issued = 0;
+      for (int kb = 0; kb < nkb && !failed; ++kb) {
+        const int s = kb % STAGES, u = kb / STAGES;
+        if (u > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)((u - 1) & 1), kWait)) {
+          failed = true;
+          break;
+        }
+        unsigned char* st = base + (size_t)s * STAGE_BYTES;
+        mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
+        const int32_t kx = (kb0 + kb) * BK;
+        tma_load_2d(st, &mapA, &full[s], kx, (int32_t)m0);
+        tma_load_2d(st + 2 * A_BYTES, &mapB, &full[s], kx, (int32_t)n0);
+        issued = kb + 1;
+      }
+      if (failed) {
+        // Shared memory must not be released under copies still landing.
+        for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+          if (!mbar_wait_bounded(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1), kWait)) atomicOr(g.err, 4);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idesc = idesc_tf32();
+      int issued = 0;
+      for (int kb = 0; kb < nkb && !failed; ++kb) {
+        const int s = kb % STAGES, u = kb / STAGES, b = kb & 1;
+        if (!mbar_wait_bounded(&ready[s], (uint32_t)(u & 1), kWait) ||
+            (kb >= 2 && !mbar_wait_bounded(&accfree[b], (uint32_t)(((kb >> 1) - 1) & 1), kWait))) {
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_hi = smem_u32(base + (size_t)s * STAGE_BYTES);
+        const uint32_t a_lo = a_hi + A_BYTES;
+        const uint32_t b_hi = a_hi + 2 * A_BYTES;
+        const uint32_t b_lo = b_hi + B_BYTES;
+        const uint32_t d = tmem + (uint32_t)(b * BN);
+#pragma unroll
+        for (int kk = 0; kk < BK / 8; ++kk) {
+          const uint32_t off = kk * 32;  // 8 TF32 values along K
+          mma_tf32(d, desc_sw128(a_hi + off), desc_sw128(b_hi + off), idesc, kk > 0 ? 1u : 0u);
+          mma_tf32(d, desc_sw128(a_hi + off), desc_sw128(b_lo + off), idesc, 1u);
+          mma_tf32(d, desc_sw128(a_lo + off), desc_sw128(b_hi + off), idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+        mma_commit(&accf[b]);
+        issued = kb + 1;
+      }
+      // Never free TMEM under MMAs that may still be running: the last
+      // commit covers every MMA this thread issued (on the normal path its
+      // phase has already completed and the wait returns at once).
+      if (issued > 0) {
+        const int kb = issued - 1;
+        if (!mbar_wait_bounded(&accf[kb & 1], (uint32_t)((kb >> 1) & 1), kWait)) atomicOr(g.err, 2);
+      }
+    }
+  } else if (warp >= 4) {
+    const int t = threadIdx.x - 128;  // 0..127
+    const int wl = warp - 4;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * wl) << 16);
+    float run[BN];
+#pragma unroll
+    for (int i = 0; i < BN; ++i) run[i] = 0.f;
+    // Adds the finished K block kb (TMEM buffer kb & 1) into run[] and hands
+    // the buffer back to the MMA issuer.
+    // Waits are made warp-uniform: tcgen05.ld is a warp-collective.
+    auto fold = [&](int kb) -> bool {
+      const bool ok = mbar_wait_bounded(&accf[kb & 1], (uint32_t)((kb >> 1) & 1), kWait);
+      if (!__all_sync(0xffffffffu, ok)) return false;
+      tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(lane_base + (uint32_t)((kb & 1) * BN + 32 * c), v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) run[32 * c + q] += v[q];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accfree[kb & 1]);
+      return true;
+    };
+    for (int kb = 0; kb < nkb && !failed; ++kb) {
+      const int s = kb % STAGES, u = kb / STAGES;
+      const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(u & 1), kWait);
+      if (!__all_sync(0xffffffffu, ok)) {
+        failed = true;
+        break;
+      }
+      unsigned char* st = base + (size_t)s * STAGE_BYTES;
+      split_tf32(reinterpret_cast<uint4*>(st), reinterpret_cast<uint4*>(st + A_BYTES), t, (int)(A_BYTES / 16));
+      split_tf32(reinterpret_cast<uint4*>(st + 2 * A_BYTES), reinterpret_cast<uint4*>(st + 2 * A_BYTES + B_BYTES), t,
+                 (int)(B_BYTES / 16));
+      fence_proxy_async_smem();
+      mbar_arrive(&ready[s]);
+      if (kb > 0 && !fold(kb - 1)) failed = true;
+    }
+    if (!failed && nkb > 0 && !fold(nkb - 1)) failed = true;
+    // This warp's 32 TMEM lanes are tile rows 32 * wl + lane.
+    const int64_t row = m0 + 32 * wl + lane;
+    if (!failed && row < g.M) {
+      const int64_t ncol = g.N - n0;
+      if (gridDim.z > 1) {
+        float* dst = static_cast<float*>(g.C) + (int64_t)blockIdx.z * g.M * g.N + row * g.N + n0;
+        if (ncol >= BN && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+          for (int q = 0; q < BN / 4; ++q)
+            reinterpret_cast<float4*>(dst)[q] = make_float4(run[4 * q], run[4 * q + 1], run[4 * q + 2], run[4 * q + 3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < BN; ++q)
+            if (q < ncol) dst[q] = run[q];
+        }
+      } else {
+        TC* dst = static_cast<TC*>(g.C) + row * g.ldc + n0;
+        if (sizeof(TC) == 4 && ncol >= BN && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+          for (int q = 0; q < BN / 4; ++q)
+            reinterpret_cast<float4*>(dst)[q] = make_float4(run[4 * q], run[4 * q + 1], run[4 * q + 2], run[4 * q + 3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < BN; ++q)
+            if (q < ncol) dst[q] = (TC)run[q];
+        }
+      }
+    }
+  }
+  if (failed) atomicOr(g.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+}  // namespace tc
+}  // namespace bsrht

@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "dla.cuh"
 #include "sketch.cuh"
+#include "trace.cuh"
 
 namespace bsrht {
 
@@ -51,6 +52,44 @@ int gemm_c(const Dla& d, Arena& ar, DT ta, DT tc, DT tout, int64_t M, int64_t N,
                       tri_b, gram);
   ar.release(mk);
   return st;
+}
+
+// Tall product on tensor cores (FP32 data, FP32 accuracy) when the layout
+// allows it: C (M x N, tout) = A (M x K, FP32) * B (K x N, B64 in FP64 or B32
+// in FP32).  Falls back to the CUDA-core GEMM with B32.
+bool use_tc(DT tc, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda) {
+  return tc == DT::F32 && M >= 256 && gemm_tc_eligible(M, N, K, A, lda);
+}
+
+int tall_gemm(const Dla& d, Arena& ar, DT ta, DT tc, DT tout, int64_t M, int64_t N, int64_t K, const void* A,
+              int64_t lda, const double* B64, const void* B32, int64_t ldb, void* C, int64_t ldc, bool tri_b) {
+  if (ta == DT::F32 && use_tc(tc, M, N, K, A, lda) && B64 != nullptr) {
+    const size_t mk = ar.mark();
+    const int st = gemm_tc(d, ar, M, N, K, static_cast<const float*>(A), lda, DT::F64, B64, ldb, false, tout, C, ldc,
+                           false);
+    ar.release(mk);
+    return st;
+  }
+  return gemm_c(d, ar, ta, tc, tout, M, N, K, A, lda, false, tc == DT::F64 ? (const void*)B64 : B32, ldb, C, ldc,
+                tri_b, false);
+}
+
+// G (l x l, FP64) = X^T X for the tall X (rows x l, type tc); the tensor-core
+// path writes X^T into `scratch` (rows x l elements) first.
+int tall_gram(const Dla& d, Arena& ar, bool dry, DT tc, const void* X, int64_t rows, int64_t l, void* scratch,
+              double* G) {
+  if (use_tc(tc, l, l, rows, scratch, rows) && (rows % 4) == 0 && (l % 4) == 0) {
+    if (!dry) {
+      const int st = transpose_to_f32(d, DT::F32, X, rows, l, l, static_cast<float*>(scratch), rows);
+      if (st != BSRHT_OK) return st;
+    }
+    const size_t mk = ar.mark();
+    const int st = gemm_tc(d, ar, l, l, rows, static_cast<const float*>(scratch), rows, DT::F32, scratch, rows, true,
+                           DT::F64, G, l, true);
+    ar.release(mk);
+    return st;
+  }
+  return gemm_c(d, ar, tc, tc, DT::F64, l, l, rows, X, l, true, X, l, G, l, false, true);
 }
 
 int read_status(const Dla& d, int* host) {
@@ -126,9 +165,9 @@ OrthBufs take_orth_bufs(Arena& ar, int64_t l, size_t cs) {
 int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void* Z, int64_t rows, int64_t l,
                 uint64_t seed, const OrthBufs& b, double* R, bool need_q, bool keep_x, void** Qout) {
   const void* RinvB = (tc == DT::F32) ? b.Rinv_c : (const void*)b.Rinv;
-  // ---- fast path: CholeskyQR2
+  // ---- fast path: CholeskyQR2 (Z serves as scratch for the transposed Grams)
   bool fast = true;
-  TRY(gemm_c(d, ar, tc, tc, DT::F64, l, l, rows, X, l, true, X, l, b.G, l, false, true));
+  TRY(tall_gram(d, ar, dry, tc, X, rows, l, Z, b.G));
   if (!dry) {
     TRY(cholesky(d, b.G, l));
     int hs = 0;
@@ -143,8 +182,8 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
       TRY(tri_inverse(d, b.G, b.LT1, b.Rinv, l));
       if (tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
     }
-    TRY(gemm_c(d, ar, tc, tc, tc, rows, l, l, X, l, false, RinvB, l, Y, l, true, false));
-    TRY(gemm_c(d, ar, tc, tc, DT::F64, l, l, rows, Y, l, true, Y, l, b.G, l, false, true));
+    TRY(tall_gemm(d, ar, tc, tc, tc, rows, l, l, X, l, b.Rinv, RinvB, l, Y, l, true));
+    TRY(tall_gram(d, ar, dry, tc, Y, rows, l, Z, b.G));
     if (!dry) {
       TRY(cholesky(d, b.G, l));
       int hs = 0;
@@ -160,7 +199,7 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
         if (tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
       }
       void* dst = keep_x ? Z : X;
-      if (need_q || !keep_x) TRY(gemm_c(d, ar, tc, tc, tc, rows, l, l, Y, l, false, RinvB, l, dst, l, true, false));
+      if (need_q || !keep_x) TRY(tall_gemm(d, ar, tc, tc, tc, rows, l, l, Y, l, b.Rinv, RinvB, l, dst, l, true));
       if (R) TRY(gemm64(d, ar, l, l, l, b.LT2, l, false, b.LT1, l, R, l, true, false));
       *Qout = dst;
       if (!dry) return BSRHT_OK;
@@ -260,35 +299,41 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
   if (!dry) BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
 
   // Step 1: B = Omega A (l x m); the paper's Y is B^T.
+  if (!dry) trace_begin(d.s);
   if (!dry) TRY(sketch_run(sp, A, seed, B, m, sk_ws, d.s));
+  if (!dry) trace_mark(d.s, "sketch");
   // Step 2: Q = orth(B^T) in FP64 (X1 = B^T, m x l).
   if (!dry) TRY(transpose_cast(d, tc, B, l, m, m, DT::F64, X1, l));
   void* Qv = nullptr;
   TRY(orth_robust(d, ar, dry, DT::F64, X1, X2, X3, m, l, seed ^ 0x51ull, ob, nullptr, true, false, &Qv));
   const double* Q = static_cast<const double*>(Qv);  // m x l, FP64
+  if (!dry) trace_mark(d.s, "orth_sketch");
   const void* Qa = Q;
   if (tc == DT::F32) {
     if (!dry) TRY(cast_copy(d, DT::F64, Q, DT::F32, Qc, m * l));
     Qa = Qc;
   }
   // Step 3: the paper's Z = Q^T A_paper, i.e. Z^T = A Q (n x l): second pass over A.
-  TRY(gemm_c(d, ar, ta, tc, tc, n, l, m, A, lda, false, Qa, l, W1, l, false, false));
+  TRY(tall_gemm(d, ar, ta, tc, tc, n, l, m, A, lda, Q, Qa, l, W1, l, false));
+  if (!dry) trace_mark(d.s, "second_pass");
   // Step 4: Z^T = P R (CholeskyQR2, rank-robust).
   void* Pv = nullptr;
   TRY(orth_robust(d, ar, dry, tc, W1, W2, W3, n, l, seed ^ 0x52ull, ob, R, true, false, &Pv));
+  if (!dry) trace_mark(d.s, "tall_qr");
   // Step 5: SVD of R^T; the columns of R^T are the rows of R.
   {
     const size_t mk = ar.mark();
     TRY(jacobi_svd(d, ar, R, l, Us, sig, Vs));
     ar.release(mk);
   }
+  if (!dry) trace_mark(d.s, "small_svd");
   // Step 6: U = P V~_k, V = Q U~_k, S = Sigma~_k.
   const void* Vk = Vs;
   if (tc == DT::F32) {
     if (!dry) TRY(cast_copy(d, DT::F64, Vs, DT::F32, Vs_c, l * l));
     Vk = Vs_c;
   }
-  TRY(gemm_c(d, ar, tc, tc, DT::F64, n, k, l, Pv, l, false, Vk, l, U, k, false, false));
+  TRY(tall_gemm(d, ar, tc, tc, DT::F64, n, k, l, Pv, l, Vs, Vk, l, U, k, false));
   TRY(gemm64(d, ar, m, k, l, Q, l, false, Us, l, V, k));
   if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(S, sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, d.s));
   {
@@ -296,6 +341,7 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
     TRY(sign_normalize(d, ar, U, n, k, V, m));
     ar.release(mk);
   }
+  if (!dry) trace_mark(d.s, "factors");
   if (dry) return BSRHT_OK;
   int hs = 0;
   TRY(read_status(d, &hs));
@@ -423,7 +469,9 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
   if (!dry) {
     BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
     // Step 1: Y = A Omega^T = (Omega A)^T for symmetric A.
+    trace_begin(d.s);
     TRY(sketch_run(sp_a, A, seed, B, n, sk_ws, d.s));
+    trace_mark(d.s, "sketch");
     TRY(transpose_cast(d, tc, B, l, n, n, tc, Y, l));
     {
       const size_t mk = ar.mark();
@@ -475,6 +523,7 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
       BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
     }
   }
+  if (!dry) trace_mark(d.s, "core");
   // Step 3: Z = Y_nu C^-1 in the arithmetic of A (C^-1 = L^-T, or V_r lambda_r^-1/2).
   const void* Ynu = Y64;
   if (!dry && tc == DT::F32) TRY(cast_copy(d, DT::F64, Y64, DT::F32, B, n * l));
@@ -485,8 +534,8 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
       TRY(tri_inverse(d, G, LT1, Cinv, l));
       if (tc == DT::F32) TRY(cast_copy(d, DT::F64, Cinv, DT::F32, Cinv_c, l * l));
     }
-    TRY(gemm_c(d, ar, tc, tc, tc, n, l, l, Ynu, l, false, tc == DT::F32 ? Cinv_c : (const void*)Cinv, l, Z, l,
-               true, false));
+    TRY(tall_gemm(d, ar, tc, tc, tc, n, l, l, Ynu, l, Cinv, tc == DT::F32 ? Cinv_c : (const void*)Cinv, l, Z, l,
+                  true));
   }
   int64_t lr = l;  // columns of Z (the kept rank on the SVD square root path)
   if (use_eig) {
@@ -515,15 +564,17 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
       if (tc == DT::F32) TRY(cast_copy(d, DT::F64, Cinv, DT::F32, Cinv_c, l * l));
     }
     // Z = Y_nu V_r lambda_r^-1/2, n x lr (contiguous, leading dimension lr).
-    TRY(gemm_c(d, ar, tc, tc, tc, n, lr, l, Ynu, l, false, tc == DT::F32 ? Cinv_c : (const void*)Cinv, l, Z, lr,
-               false, false));
+    TRY(tall_gemm(d, ar, tc, tc, tc, n, lr, l, Ynu, l, Cinv, tc == DT::F32 ? Cinv_c : (const void*)Cinv, l, Z, lr,
+                  false));
   }
+  if (!dry) trace_mark(d.s, "z");
   // Step 4: R factor of Z (CholeskyQR2, rank-robust); Z itself is kept for step 6.
   {
     void* scratch = (tc == DT::F32) ? B : (void*)Y64;
     void* Qv = nullptr;
     TRY(orth_robust(d, ar, dry, tc, Z, scratch, Z3, n, lr, seed ^ 0x53ull, ob, R, false, true, &Qv));
   }
+  if (!dry) trace_mark(d.s, "tall_qr");
   // Step 5: SVD of R = U~ Sigma~ V~^T (Jacobi on the columns of R, i.e. rows of R^T).
   if (!dry) {
     TRY(transpose_lower_to_upper(d, R, RT, lr));
@@ -535,6 +586,7 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
     TRY(jacobi_svd(d, ar, RT, lr, Us, sig, Vs));
     ar.release(mk);
   }
+  if (!dry) trace_mark(d.s, "small_svd");
   // Step 6: U^ = (Z V~_k) Sigma~_k^-1; step 7: Lambda = max(Sigma~_k^2 - nu, 0).
   const int64_t kk = std::min<int64_t>(k, lr);
   const void* Vk = Vs;
@@ -542,7 +594,7 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
     if (!dry) TRY(cast_copy(d, DT::F64, Vs, DT::F32, Vs_c, lr * lr));
     Vk = Vs_c;
   }
-  TRY(gemm_c(d, ar, tc, tc, DT::F64, n, kk, lr, Z, lr, false, Vk, lr, U, k, false, false));
+  TRY(tall_gemm(d, ar, tc, tc, DT::F64, n, kk, lr, Z, lr, Vs, Vk, lr, U, k, false));
   if (!dry) {
     TRY(scale_columns(d, U, n, k, k, sig, true));
     k_lambda<<<(unsigned)((k + 127) / 128), 128, 0, d.s>>>(sig, nu, Lam, k);
@@ -554,6 +606,7 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
     TRY(sign_normalize(d, ar, U, n, k, nullptr, 0));
     ar.release(mk);
   }
+  if (!dry) trace_mark(d.s, "factors");
   if (dry) return BSRHT_OK;
   int hs = 0;
   TRY(read_status(d, &hs));
