@@ -235,6 +235,20 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- our arm
+# DRAM bytes of one bsrht_sketch call from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum of k_sketch_tma), captured at n = 2^18 (4.2956 GB
+# read, 0.0119 GB of partials written) and scaled to n = 2^20 by the rows
+# processed (reads grow with n, the partials do not).  Valid only for the
+# FP32 kernel at m = 4096, p = 4, l = 512 as it stood when captured.
+SKETCH_TRAFFIC_F32_N2E20_M4096 = 4 * 4.2956e9 + 0.0119e9
+
+
+def sketch_traffic(args, mode):
+    if (args.dtype, args.n, args.m, args.p, args.l) == ("f32", 1 << 20, 4096, 4, 512):
+        return SKETCH_TRAFFIC_F32_N2E20_M4096
+    return None
+
+
 def run_ours(args):
     import torch
 
@@ -369,8 +383,8 @@ def run_ours(args):
         "sketch": {"ms": round(sketch_ms, 4), "gbs": round(achieved, 2),
                    "frac_of_measured_peak": round(achieved / peak, 4)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "k_sketch_chunked + k_sketch_reduce (one bsrht_sketch call)",
+                     "frac": round(achieved / peak, 4), "traffic": sketch_traffic(args, mode),
+                     "kernel": "k_sign_tables + k_sketch_tma + k_sketch_reduce_checked (one bsrht_sketch call)",
                      "peak_kind": peak_kind},
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
         "e2e": {"value": round(total_bytes_all / (e2e_ms * 1e-3) / 1e9, 3) if e2e_ms else None, "unit": "GB/s",
