@@ -202,6 +202,110 @@ uint64_t bsrht_kernel_launches(void);
 /* Library version, e.g. "0.1.0" (static storage). */
 const char* bsrht_version(void);
 
+/* ---- sketch autotuner -------------------------------------------------
+ * Times every kernel instance that can run the sketch of these sizes (the
+ * TMA-fed kernel and the chunked kernels with each chunk length R2 <= r,
+ * i.e. tile shape and FWHT split) on A itself, two runs each after one
+ * warm-up, with CUDA events on opts->stream, and records the fastest for the
+ * shape class (dtype, r, ceil(log2 m), l <= 512 or not, TMA-compatible rows).
+ * Later plans of that class (bsrht_sketch, the *_workspace queries, the
+ * server) use the recorded choice.  Writes only library scratch; A is read.
+ * *choice: the instance picked (-1 = the TMA-fed kernel, else the chunked
+ * instance index); *best_ms: its time.  Synchronous with opts->stream.
+ * Returns EINVAL on bad sizes, ENOMEM if scratch cannot be allocated.      */
+int bsrht_sketch_autotune(const void* A, int64_t n, int64_t m, int32_t p, int64_t l, const bsrht_opts* opts,
+                          int32_t* choice, double* best_ms);
+/* Forgets every recorded choice (plans fall back to the built-in rules).   */
+int bsrht_sketch_autotune_reset(void);
+
+/* ---- serving loop -----------------------------------------------------
+ * A server owns a device pool of hbm_budget bytes for request scratch and a
+ * set of executor threads, each with its own CUDA stream.  Requests (sketch,
+ * Algorithm 1 RSVD, Algorithm 2 Nystrom) are submitted at any time and run
+ * as soon as an executor is free and their scratch fits in the free part of
+ * the pool (first fit; requests that fit may pass one that does not yet, up
+ * to a bounded number of times, so a large request is not starved).  Work of
+ * different requests overlaps on the device through the executors' streams.
+ * Small sketches (too few tiles to fill the GPU alone) of the same kernel
+ * instance are packed, up to max_group at a time, into one persistent
+ * grouped FWHT launch; sketch launches are replayed from captured CUDA
+ * graphs (one executable graph per shape, updated in place for new
+ * pointers).  A and all outputs are caller-owned device buffers that must
+ * stay valid until the request completes; the server never writes to A.
+ * The executors' streams are not ordered after the caller's streams: A must
+ * be completely written (its producer synchronized) before bsrht_submit,
+ * and the outputs may be read once bsrht_poll / bsrht_wait report the
+ * request done.
+ * Latency = submit to observed completion on the host.                     */
+typedef struct bsrht_server bsrht_server;
+
+typedef enum bsrht_request_kind {
+  BSRHT_REQ_SKETCH = 0,  /* out = Omega A (l x m; F64 if A is F64, else F32) */
+  BSRHT_REQ_RSVD = 1,    /* U (n x k), S (k), V (m x k), FP64 (bsrht_rsvd)  */
+  BSRHT_REQ_NYSTROM = 2  /* U (n x k), S = Lambda (k), FP64; A is n x n     */
+} bsrht_request_kind;
+
+typedef struct bsrht_request {
+  int32_t kind;     /* bsrht_request_kind                                  */
+  int32_t dtype;    /* bsrht_dtype of A                                    */
+  const void* A;    /* device, n x m row-major (n x n for Nystrom)         */
+  int64_t n, m;     /* m is ignored for Nystrom                            */
+  int64_t lda;      /* 0 = dense rows                                      */
+  int32_t p;        /* number of blocks                                    */
+  int32_t k;        /* target rank (RSVD, Nystrom)                         */
+  int64_t l;        /* sketch rows                                         */
+  uint64_t seed;
+  void* out;        /* sketch output                                       */
+  double* U;
+  double* S;        /* singular values (RSVD) or Lambda (Nystrom)          */
+  double* V;        /* RSVD only                                           */
+} bsrht_request;
+
+typedef struct bsrht_server_opts {
+  size_t hbm_budget;      /* bytes of the scratch pool (cudaMalloc'ed once) */
+  int32_t executors;      /* executor threads / streams (default 4)         */
+  int32_t max_group;      /* sketches per grouped launch, 1..32 (default 16)*/
+  int32_t use_graphs;     /* replay sketch launches from CUDA graphs (1)    */
+  int32_t autotune;       /* autotune each new sketch shape class (1)       */
+  int64_t exec_timeout_ms;/* bounded wait of an executor for its work; on
+                             expiry the request fails with ETIMEDOUT and its
+                             scratch stays reserved (default 600000)         */
+} bsrht_server_opts;
+
+typedef struct bsrht_server_stats {
+  int64_t submitted, completed, failed, pending;
+  int64_t grouped_launches;  /* grouped FWHT launches                       */
+  int64_t grouped_requests;  /* sketches that ran inside them               */
+  int64_t graph_launches;    /* launches replayed from CUDA graphs          */
+  int64_t tuned_classes;     /* shape classes the server autotuned          */
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* latency of completed requests */
+  size_t pool_high_bytes;    /* high-water mark of the scratch pool         */
+} bsrht_server_stats;
+
+void bsrht_server_opts_init(bsrht_server_opts* o);
+/* Server with default options and the given budget on the current device. */
+int bsrht_server_create(size_t hbm_budget, bsrht_server** out);
+int bsrht_server_create_ex(const bsrht_server_opts* o, bsrht_server** out);
+/* Validates and queues a request; *ticket identifies it.  EINVAL on bad
+ * arguments, ENOMEM if its scratch exceeds the whole budget.               */
+int bsrht_submit(bsrht_server* s, const bsrht_request* r, uint64_t* ticket);
+/* *done = 1 once the request finished; the return value is then its status
+ * (BSRHT_OK or the library status of the call), else BSRHT_OK with *done = 0.
+ * EINVAL for an unknown ticket.                                            */
+int bsrht_poll(bsrht_server* s, uint64_t ticket, int* done);
+/* Blocks until the request finished or timeout_us elapsed: its status, or
+ * ETIMEDOUT (the request keeps running).                                   */
+int bsrht_wait(bsrht_server* s, uint64_t ticket, int64_t timeout_us);
+int bsrht_server_stats_get(bsrht_server* s, bsrht_server_stats* out);
+/* Lets queued and running requests finish, joins the executors, frees the
+ * pool and the graphs.  The server must not be used afterwards.            */
+int bsrht_server_destroy(bsrht_server* s);
+
+/* Host-only self-test of the server's first-fit pool allocator (no GPU):
+ * random allocate / free sequences checked against a reference model.
+ * Returns 0 when every invariant held, else the number of violations.     */
+int bsrht_selftest_pool_allocator(uint64_t seed, int32_t steps);
+
 #ifdef __cplusplus
 } /* extern "C" */
 #endif

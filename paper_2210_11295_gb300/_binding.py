@@ -48,6 +48,57 @@ class Opts(ctypes.Structure):
     ]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+        ("A", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("m", ctypes.c_int64),
+        ("lda", ctypes.c_int64),
+        ("p", ctypes.c_int32),
+        ("k", ctypes.c_int32),
+        ("l", ctypes.c_int64),
+        ("seed", ctypes.c_uint64),
+        ("out", ctypes.c_void_p),
+        ("U", ctypes.c_void_p),
+        ("S", ctypes.c_void_p),
+        ("V", ctypes.c_void_p),
+    ]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget", ctypes.c_size_t),
+        ("executors", ctypes.c_int32),
+        ("max_group", ctypes.c_int32),
+        ("use_graphs", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
+        ("exec_timeout_ms", ctypes.c_int64),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64),
+        ("completed", ctypes.c_int64),
+        ("failed", ctypes.c_int64),
+        ("pending", ctypes.c_int64),
+        ("grouped_launches", ctypes.c_int64),
+        ("grouped_requests", ctypes.c_int64),
+        ("graph_launches", ctypes.c_int64),
+        ("tuned_classes", ctypes.c_int64),
+        ("p50_ms", ctypes.c_double),
+        ("p99_ms", ctypes.c_double),
+        ("mean_ms", ctypes.c_double),
+        ("max_ms", ctypes.c_double),
+        ("pool_high_bytes", ctypes.c_size_t),
+    ]
+
+
+REQ_SKETCH, REQ_RSVD, REQ_NYSTROM = 0, 1, 2
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -72,6 +123,18 @@ def _load() -> ctypes.CDLL:
         "bsrht_profile_enable": (ctypes.c_int, [ctypes.c_int]),
         "bsrht_profile_stages": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                                  ctypes.POINTER(ctypes.c_int)]),
+        "bsrht_sketch_autotune": (ctypes.c_int, [vp, i64, i64, i32, i64, po, ctypes.POINTER(i32),
+                                                 ctypes.POINTER(ctypes.c_double)]),
+        "bsrht_sketch_autotune_reset": (ctypes.c_int, []),
+        "bsrht_server_opts_init": (None, [ctypes.POINTER(ServerOpts)]),
+        "bsrht_server_create": (ctypes.c_int, [sz, ctypes.POINTER(vp)]),
+        "bsrht_server_create_ex": (ctypes.c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]),
+        "bsrht_submit": (ctypes.c_int, [vp, ctypes.POINTER(Request), ctypes.POINTER(u64)]),
+        "bsrht_poll": (ctypes.c_int, [vp, u64, ctypes.POINTER(ctypes.c_int)]),
+        "bsrht_wait": (ctypes.c_int, [vp, u64, i64]),
+        "bsrht_server_stats_get": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
+        "bsrht_server_destroy": (ctypes.c_int, [vp]),
+        "bsrht_selftest_pool_allocator": (ctypes.c_int, [u64, i32]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -233,3 +296,113 @@ def bsrht_profile_stages() -> list[tuple[str, float]]:
 
 def bsrht_release_pool() -> None:
     _check(lib.bsrht_release_pool(), "bsrht_release_pool")
+
+
+def bsrht_sketch_autotune(a: torch.Tensor, p: int, l: int) -> tuple[int, float]:
+    """Times the sketch kernel instances on `a` and records the fastest for
+    its shape class; returns (choice, ms) with choice -1 = TMA-fed kernel."""
+    o = make_opts(a)
+    c = ctypes.c_int32(0)
+    t = ctypes.c_double(0.0)
+    _check(lib.bsrht_sketch_autotune(_dptr(a), a.shape[0], a.shape[1], int(p), int(l), ctypes.byref(o),
+                                     ctypes.byref(c), ctypes.byref(t)), "bsrht_sketch_autotune")
+    return int(c.value), float(t.value)
+
+
+def bsrht_sketch_autotune_reset() -> None:
+    _check(lib.bsrht_sketch_autotune_reset(), "bsrht_sketch_autotune_reset")
+
+
+def bsrht_selftest_pool_allocator(seed: int, steps: int) -> int:
+    return int(lib.bsrht_selftest_pool_allocator(int(seed), int(steps)))
+
+
+class Server:
+    """The library's serving loop (bsrht_server_*): requests run on the
+    server's own executor streams; tensors passed to submit_* must stay alive
+    (and untouched) until the request is done."""
+
+    def __init__(self, hbm_budget: int, executors: int = 4, max_group: int = 16, use_graphs: bool = True,
+                 autotune: bool = True, exec_timeout_ms: int = 600_000):
+        o = ServerOpts()
+        lib.bsrht_server_opts_init(ctypes.byref(o))
+        o.hbm_budget = int(hbm_budget)
+        o.executors = int(executors)
+        o.max_group = int(max_group)
+        o.use_graphs = 1 if use_graphs else 0
+        o.autotune = 1 if autotune else 0
+        o.exec_timeout_ms = int(exec_timeout_ms)
+        h = ctypes.c_void_p()
+        _check(lib.bsrht_server_create_ex(ctypes.byref(o), ctypes.byref(h)), "bsrht_server_create_ex")
+        self._h = h
+        self._keep: dict[int, tuple] = {}
+
+    def _submit(self, r: Request, keep: tuple) -> int:
+        t = ctypes.c_uint64(0)
+        _check(lib.bsrht_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "bsrht_submit")
+        self._keep[int(t.value)] = keep
+        return int(t.value)
+
+    @staticmethod
+    def _base(a: torch.Tensor, kind: int, p: int, l: int, seed: int, k: int = 0) -> Request:
+        if a.dim() != 2 or a.stride(1) != 1 or a.dtype not in _DTYPES or not a.is_cuda:
+            raise ValueError("A must be a row-major 2-D CUDA tensor of f64/f32/bf16/f16")
+        r = Request()
+        r.kind = kind
+        r.dtype = _DTYPES[a.dtype]
+        r.A = a.data_ptr()
+        r.n, r.m = a.shape
+        r.lda = int(a.stride(0)) if a.shape[0] > 1 else int(a.shape[1])
+        r.p, r.k, r.l, r.seed = int(p), int(k), int(l), int(seed)
+        return r
+
+    def submit_sketch(self, a: torch.Tensor, p: int, l: int, seed: int, out: torch.Tensor) -> int:
+        if out.shape != (l, a.shape[1]) or not out.is_contiguous() or out.dtype != sketch_out_dtype(a.dtype):
+            raise ValueError("out must be a contiguous l x m tensor of the sketch dtype")
+        r = self._base(a, REQ_SKETCH, p, l, seed)
+        r.out = out.data_ptr()
+        return self._submit(r, (a, out))
+
+    def submit_rsvd(self, a: torch.Tensor, k: int, l: int, p: int, seed: int,
+                    outs: tuple[torch.Tensor, torch.Tensor, torch.Tensor]) -> int:
+        u, sv, v = outs
+        r = self._base(a, REQ_RSVD, p, l, seed, k)
+        r.U, r.S, r.V = u.data_ptr(), sv.data_ptr(), v.data_ptr()
+        return self._submit(r, (a, u, sv, v))
+
+    def submit_nystrom(self, a: torch.Tensor, k: int, l: int, p: int, seed: int,
+                       outs: tuple[torch.Tensor, torch.Tensor]) -> int:
+        u, lam = outs
+        r = self._base(a, REQ_NYSTROM, p, l, seed, k)
+        r.U, r.S = u.data_ptr(), lam.data_ptr()
+        return self._submit(r, (a, u, lam))
+
+    def poll(self, ticket: int) -> tuple[bool, int]:
+        d = ctypes.c_int(0)
+        st = lib.bsrht_poll(self._h, int(ticket), ctypes.byref(d))
+        return bool(d.value), int(st)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0) -> int:
+        """The request's status (BSRHT_OK = 0), or BSRHT_ETIMEDOUT."""
+        st = int(lib.bsrht_wait(self._h, int(ticket), int(timeout_s * 1e6)))
+        if st != BSRHT_ETIMEDOUT:
+            self._keep.pop(int(ticket), None)
+        return st
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib.bsrht_server_stats_get(self._h, ctypes.byref(s)), "bsrht_server_stats_get")
+        return {name: getattr(s, name) for name, _ in ServerStats._fields_}
+
+    def close(self) -> None:
+        if self._h:
+            _check(lib.bsrht_server_destroy(self._h), "bsrht_server_destroy")
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+

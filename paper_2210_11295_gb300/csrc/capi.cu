@@ -123,6 +123,31 @@ int bsrht_sketch(const void* A, int64_t n, int64_t m, int32_t p, int64_t l, uint
   return sketch_run(pl, A, seed, out, m, work, static_cast<cudaStream_t>(o.stream));
 }
 
+int bsrht_sketch_autotune(const void* A, int64_t n, int64_t m, int32_t p, int64_t l, const bsrht_opts* opts,
+                          int32_t* choice, double* best_ms) {
+  const bsrht_opts o = opts_or_default(opts);
+  if (!A || m < 1 || n < 1 || p < 1 || l < 1) return BSRHT_EINVAL;
+  const size_t wb = sketch_autotune_work_bytes(o.dtype, n, m, o.lda, p, l);
+  const size_t ob = (size_t)l * (size_t)m * (o.dtype == BSRHT_F64 ? 8 : 4);
+  const size_t wpad = (wb + 255) / 256 * 256;
+  void* base = nullptr;
+  int st = pool_get(wpad + ob, &base);
+  if (st != BSRHT_OK) return st;
+  int c = -1;
+  double t = 0.0;
+  st = sketch_autotune(A, o.dtype, n, m, o.lda, p, l, base, wb, static_cast<char*>(base) + wpad,
+                       static_cast<cudaStream_t>(o.stream), &c, &t);
+  if (st != BSRHT_OK) return st;
+  if (choice) *choice = c;
+  if (best_ms) *best_ms = t;
+  return BSRHT_OK;
+}
+
+int bsrht_sketch_autotune_reset(void) {
+  sketch_autotune_reset();
+  return BSRHT_OK;
+}
+
 int bsrht_release_pool(void) {
   int dev = 0;
   BSRHT_CUDA_TRY(cudaGetDevice(&dev));

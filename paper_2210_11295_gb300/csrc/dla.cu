@@ -273,7 +273,8 @@ __device__ __forceinline__ int rr_player(int pos, int round, int lp) {
   return 1 + (pos - 1 + round) % (lp - 1);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -283,14 +284,24 @@ __device__ __forceinline__ double warp_sum(double v) {
 // one warp per column pair, a grid-wide barrier between rounds.  A warp loads
 // its two columns of M and of V into registers (JR values per lane), forms
 // the three inner products, rotates in registers and stores once, so each
-// round costs one round trip to L2 instead of one per element.
-template <int JR>
-__global__ void k_jacobi(double* __restrict__ M, double* __restrict__ V, int l, int lp, double tol, int max_sweeps,
+// round costs one round trip to L2 instead of one per element.  A pair is
+// rotated while |x.y| > tol sqrt(x.x y.y); the sweeps stop after one in
+// which no rotation exceeded tol_stop (>= tol), i.e. once only rounding-level
+// rotations are left.  Two columns that are both numerically zero (norm at
+// most tiny_rel ||M||_F, *fnorm = ||M||_F) are left alone: rounding keeps
+// their directions random and rotating them would never converge.
+// `status` (may be null) gets kStatusNoConv if max_sweeps ran out.
+template <typename T, int JR>
+__global__ void k_jacobi(T* __restrict__ M, T* __restrict__ V, int l, int lp, double tol, double tol_stop,
+                         const double* __restrict__ fnorm, double tiny_rel, int max_sweeps,
                          int* __restrict__ rot_counts, int* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
   const int lane = threadIdx.x & 31;
   const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+  const T ttol = (T)tol, tstop = (T)tol_stop;
+  const double tiny = tiny_rel * fnorm[0];
+  const T tiny2 = (T)(tiny * tiny);
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     for (int round = 0; round < lp - 1; ++round) {
@@ -302,32 +313,35 @@ __global__ void k_jacobi(double* __restrict__ M, double* __restrict__ V, int l, 
           q = t;
         }
         if (q >= l) continue;  // padding column
-        double* __restrict__ a = M + (int64_t)p * l;
-        double* __restrict__ b = M + (int64_t)q * l;
-        double* __restrict__ va = V + (int64_t)p * l;
-        double* __restrict__ vb = V + (int64_t)q * l;
-        double x[JR], y[JR], vx[JR], vy[JR];
+        T* __restrict__ a = M + (int64_t)p * l;
+        T* __restrict__ b = M + (int64_t)q * l;
+        T* __restrict__ va = V + (int64_t)p * l;
+        T* __restrict__ vb = V + (int64_t)q * l;
+        T x[JR], y[JR], vx[JR], vy[JR];
 #pragma unroll
         for (int e = 0; e < JR; ++e) {
           const int r = lane + 32 * e;
           const bool in = r < l;
-          x[e] = in ? a[r] : 0.0;
-          y[e] = in ? b[r] : 0.0;
-          vx[e] = in ? va[r] : 0.0;
-          vy[e] = in ? vb[r] : 0.0;
+          x[e] = in ? a[r] : (T)0;
+          y[e] = in ? b[r] : (T)0;
+          vx[e] = in ? va[r] : (T)0;
+          vy[e] = in ? vb[r] : (T)0;
         }
-        double al = 0.0, be = 0.0, ga = 0.0;
+        T al = 0, be = 0, ga = 0;
 #pragma unroll
         for (int e = 0; e < JR; ++e) {
           al = fma(x[e], x[e], al);
           be = fma(y[e], y[e], be);
           ga = fma(x[e], y[e], ga);
         }
-        const double alpha = warp_sum(al), beta = warp_sum(be), gamma = warp_sum(ga);
-        if (gamma == 0.0 || !(fabs(gamma) > tol * sqrt(alpha * beta))) continue;
-        const double zeta = (beta - alpha) / (2.0 * gamma);
-        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        const T alpha = warp_sum(al), beta = warp_sum(be), gamma = warp_sum(ga);
+        if (alpha <= tiny2 && beta <= tiny2) continue;
+        const T gnorm = sqrt(alpha * beta);
+        if (gamma == (T)0 || !(fabs(gamma) > ttol * gnorm)) continue;
+        const bool significant = fabs(gamma) > tstop * gnorm;
+        const T zeta = (beta - alpha) / ((T)2 * gamma);
+        const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+        const T c = (T)1 / sqrt((T)1 + t * t), s = c * t;
 #pragma unroll
         for (int e = 0; e < JR; ++e) {
           const int r = lane + 32 * e;
@@ -338,18 +352,19 @@ __global__ void k_jacobi(double* __restrict__ M, double* __restrict__ V, int l, 
             vb[r] = s * vx[e] + c * vy[e];
           }
         }
-        if (lane == 0) atomicAdd(&rot_counts[sweep], 1);
+        if (lane == 0 && significant) atomicAdd(&rot_counts[sweep], 1);
       }
       grid.sync();
     }
     if (*((volatile int*)&rot_counts[sweep]) == 0) break;
   }
-  if (sweep >= max_sweeps && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusNoConv);
+  if (status && sweep >= max_sweeps && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusNoConv);
 }
 
-__global__ void k_init_identity_cols(double* V, int64_t l) {
+template <typename T>
+__global__ void k_init_identity_cols(T* V, int64_t l) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < l * l) V[idx] = (idx / l == idx % l) ? 1.0 : 0.0;
+  if (idx < l * l) V[idx] = (idx / l == idx % l) ? (T)1 : (T)0;
 }
 
 __global__ void k_col_norms(const double* __restrict__ M, double* __restrict__ sigma, int64_t l) {
@@ -390,52 +405,136 @@ __global__ void k_svd_finish(const double* __restrict__ M, const double* __restr
   if (i == 0) sig_out[r] = s;
 }
 
-int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout) {
-  const int max_sweeps = 40;
-  double* Vc = static_cast<double*>(ar.take(sizeof(double) * l * l));
-  double* sig = static_cast<double*>(ar.take(sizeof(double) * l));
-  int* perm = static_cast<int*>(ar.take(sizeof(int) * l));
-  int* rot = static_cast<int*>(ar.take(sizeof(int) * max_sweeps));
-  if (!ar.ok()) return BSRHT_ENOMEM;
-  if (ar.measure) return BSRHT_OK;
-  BSRHT_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(int) * max_sweeps, d.s));
-  k_init_identity_cols<<<blocks_for(l * l, 256), 256, 0, d.s>>>(Vc, l);
-  DLA_LAUNCH_CHECK();
-  int li = (int)l, lp = (int)(l + (l & 1));
-  // Rotate only while the cosine of the pair exceeds sqrt(l) eps (the usual
-  // one-sided Jacobi threshold); a tighter one keeps rotating at noise level.
-  double tol = std::max(1e-15, std::sqrt((double)l) * 0x1.0p-52);
-  int msw = max_sweeps;
+#define TRY_DLA(expr)                   \
+  do {                                  \
+    const int st_ = (expr);             \
+    if (st_ != BSRHT_OK) return st_;    \
+  } while (0)
+
+// The mixed-precision path (FP32 Jacobi, FP64 polish) above this order.
+constexpr int64_t kJacobiMixedMin = 64;
+
+__global__ void k_ns_coeff(double* __restrict__ G, int64_t l) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < l * l) G[idx] = (idx / l == idx % l ? 1.5 : 0.0) - 0.5 * G[idx];
+}
+
+namespace {
+
+template <typename T>
+int launch_jacobi(const Dla& d, T* cols, T* Vc, int64_t l, double tol, double tol_stop, const double* fnorm,
+                  double tiny_rel, int max_sweeps, int* rot, int* status) {
+  int li = (int)l, lp = (int)(l + (l & 1)), msw = max_sweeps;
   // One column pair per warp, two warps per block: spreads the l/2 pairs of a
   // round over as many SMs as possible (FP64 throughput is per SM).
   const int threads = 64;
   const int pairs = lp / 2;
-  void* args[] = {&colsM, &Vc, &li, &lp, &tol, &msw, &rot, (void*)&d.status};
+  void* args[] = {&cols, &Vc, &li, &lp, &tol, &tol_stop, &fnorm, &tiny_rel, &msw, &rot, &status};
   auto launch = [&](auto kern) -> int {
     int occ = 0;
     BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0));
     const int blocks =
         std::max(1, std::min((pairs + threads / 32 - 1) / (threads / 32), num_sms() * std::max(occ, 1)));
     BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(threads), args, 0, d.s));
+    note_launches(1);
     return BSRHT_OK;
   };
-  if (l > 1) {
-    int st;
-    if (l <= 128) st = launch(k_jacobi<4>);
-    else if (l <= 256) st = launch(k_jacobi<8>);
-    else if (l <= 512) st = launch(k_jacobi<16>);
-    else if (l <= 1024) st = launch(k_jacobi<32>);
-    else if (l <= 2048) st = launch(k_jacobi<64>);
-    else return BSRHT_EUNSUP;
+  if (l <= 1) return BSRHT_OK;
+  if (l <= 128) return launch(k_jacobi<T, 4>);
+  if (l <= 256) return launch(k_jacobi<T, 8>);
+  if (l <= 512) return launch(k_jacobi<T, 16>);
+  if (l <= 1024) return launch(k_jacobi<T, 32>);
+  if (l <= 2048) return launch(k_jacobi<T, 64>);
+  return BSRHT_EUNSUP;
+}
+
+}  // namespace
+
+int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout) {
+  if (l > 2048) return BSRHT_EUNSUP;
+  const int max_sweeps = 40;
+  // Rotate only while the cosine of the pair exceeds sqrt(l) eps (the usual
+  // one-sided Jacobi threshold); a tighter one keeps rotating at noise level.
+  const double tol = std::max(1e-15, std::sqrt((double)l) * 0x1.0p-52);
+  const bool mixed = l > kJacobiMixedMin;
+  double* Vc = static_cast<double*>(ar.take(sizeof(double) * l * l));
+  double* sig = static_cast<double*>(ar.take(sizeof(double) * l));
+  int* perm = static_cast<int*>(ar.take(sizeof(int) * l));
+  int* rot = static_cast<int*>(ar.take(sizeof(int) * 2 * max_sweeps));
+  double* fnorm = static_cast<double*>(ar.take(sizeof(double)));
+  float *M32 = nullptr, *V32 = nullptr;
+  double *S2 = nullptr, *G = nullptr, *Y = nullptr;
+  if (mixed) {
+    M32 = static_cast<float*>(ar.take(sizeof(float) * l * l));
+    V32 = static_cast<float*>(ar.take(sizeof(float) * l * l));
+    S2 = static_cast<double*>(ar.take(sizeof(double) * l * l));
+    G = static_cast<double*>(ar.take(sizeof(double) * l * l));
+    Y = static_cast<double*>(ar.take(sizeof(double) * l * l));
+  }
+  if (!ar.ok()) return BSRHT_ENOMEM;
+  // The l x l products below release their split-K scratch after use.
+  auto gemm64 = [&](const double* A, bool a_trans, const double* B, double* C, bool gram) -> int {
+    const size_t mk = ar.mark();
+    const int st = gemm(d, ar, DT::F64, DT::F64, DT::F64, true, l, l, l, A, l, a_trans, B, l, C, l, 1.0, 0.0,
+                        false, gram);
+    ar.release(mk);
+    return st;
+  };
+  {
+    const size_t mk = ar.mark();
+    const int st = frob_norm(d, ar, DT::F64, colsM, l * l, fnorm);
+    ar.release(mk);
     if (st != BSRHT_OK) return st;
   }
-  k_col_norms<<<blocks_for(l, 8), 256, 0, d.s>>>(colsM, sig, l);
+  if (ar.measure) {
+    if (mixed) {
+      TRY_DLA(gemm64(nullptr, true, nullptr, nullptr, true));
+      TRY_DLA(gemm64(nullptr, false, nullptr, nullptr, false));
+    }
+    return BSRHT_OK;
+  }
+  BSRHT_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(int) * 2 * max_sweeps, d.s));
+  double* cols = colsM;
+  if (mixed) {
+    // 1. FP32 one-sided Jacobi on a copy of M: V32 ~ the right singular
+    //    vectors to FP32 accuracy, at 64x the FP64 rate of this GPU.
+    TRY_DLA(cast_copy(d, DT::F64, colsM, DT::F32, M32, l * l));
+    k_init_identity_cols<float><<<blocks_for(l * l, 256), 256, 0, d.s>>>(V32, l);
+    DLA_LAUNCH_CHECK();
+    const double tol32 = 16.0 * std::sqrt((double)l) * 0x1.0p-24;
+    TRY_DLA(launch_jacobi<float>(d, M32, V32, l, tol32, tol32, fnorm, (double)l * 0x1.0p-24, 20, rot + max_sweeps,
+                                 nullptr));
+    // 2. Make it orthogonal in FP64: with S = V0^T (the column storage),
+    //    two Newton-Schulz steps S <- 1.5 S - 0.5 S (S^T S) take the
+    //    orthogonality error from ~1e-6 to rounding level.
+    TRY_DLA(cast_copy(d, DT::F32, V32, DT::F64, Vc, l * l));
+    for (int it = 0; it < 2; ++it) {
+      TRY_DLA(gemm64(Vc, true, Vc, G, true));  // G = S^T S
+      k_ns_coeff<<<blocks_for(l * l, 256), 256, 0, d.s>>>(G, l);  // G <- 1.5 I - 0.5 G
+      DLA_LAUNCH_CHECK();
+      note_launches(1);
+      TRY_DLA(gemm64(Vc, false, G, S2, false));
+      std::swap(Vc, S2);
+    }
+    // 3. Y = (M V0)^T in column storage: Y = S T with T = M^T the column
+    //    storage of M.  The FP64 Jacobi below starts from V = V0, so its
+    //    rotations compose onto V0 and M V = U Sigma holds for the result.
+    TRY_DLA(gemm64(Vc, false, colsM, Y, false));
+    cols = Y;
+  } else {
+    k_init_identity_cols<double><<<blocks_for(l * l, 256), 256, 0, d.s>>>(Vc, l);
+    DLA_LAUNCH_CHECK();
+  }
+  // 4. FP64 one-sided Jacobi (from V0 it converges in a few sweeps).
+  TRY_DLA(launch_jacobi<double>(d, cols, Vc, l, tol, 16.0 * tol, fnorm, (double)l * 0x1.0p-53, max_sweeps, rot,
+                                d.status));
+  k_col_norms<<<blocks_for(l, 8), 256, 0, d.s>>>(cols, sig, l);
   DLA_LAUNCH_CHECK();
   k_rank_desc<<<blocks_for(l, 256), 256, 0, d.s>>>(sig, perm, l);
   DLA_LAUNCH_CHECK();
-  k_svd_finish<<<blocks_for(l * l, 256), 256, 0, d.s>>>(colsM, Vc, sig, perm, U, Vout, sigma, l);
+  k_svd_finish<<<blocks_for(l * l, 256), 256, 0, d.s>>>(cols, Vc, sig, perm, U, Vout, sigma, l);
   DLA_LAUNCH_CHECK();
-  note_launches(l > 1 ? 5 : 4);
+  note_launches(4);
   return BSRHT_OK;
 }
 

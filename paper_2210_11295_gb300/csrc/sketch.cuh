@@ -7,6 +7,9 @@
 
 namespace bsrht {
 
+// Upper bound on the sketches of one grouped launch (a kernel parameter).
+constexpr int kMaxGroup = 32;
+
 struct SketchPlan {
   int dtype = 0;      // bsrht_dtype of A
   int variant = 1;    // 1 = CUDA-core butterflies (K1), 2 = tensor cores (K2)
@@ -42,6 +45,26 @@ int sketch_run(const SketchPlan& plan, const void* A, uint64_t seed, void* out, 
 
 int num_sms();
 
+// Autotuner: times every candidate instance on A (scratch work, output out
+// of l x m) and records the fastest for the shape class; see
+// bsrht_sketch_autotune.  work must hold sketch_autotune_work_bytes.
+int sketch_autotune(const void* A, int dtype, int64_t n, int64_t m, int64_t lda, int p, int64_t l, void* work,
+                    size_t work_bytes, void* out, cudaStream_t stream, int* choice, double* best_ms);
+size_t sketch_autotune_work_bytes(int dtype, int64_t n, int64_t m, int64_t lda, int p, int64_t l);
+void sketch_autotune_reset();
+
+// Grouped launches: several sketches of one dtype family in one persistent
+// launch of the chunked kernel.  The plan is the plain-kernel plan of the
+// sizes; EUNSUP if they need more than one sketch-row group.
+int sketch_make_plan_grouped(SketchPlan& plan, int dtype, int64_t n, int64_t m, int64_t lda, int p, int64_t l);
+// Scratch of one sketch inside a grouped launch.
+size_t sketch_group_work_bytes(const SketchPlan& plan);
+// Enqueues nreq (<= kMaxGroup) sketches with equal dtype and kernel
+// instance; outs[q] is l x m row-major, works[q] holds
+// sketch_group_work_bytes(*plans[q]).
+int sketch_group_run(const SketchPlan* const* plans, const void* const* A, const uint64_t* seeds, void* const* outs,
+                     void* const* works, int nreq, cudaStream_t stream);
+
 }  // namespace bsrht
 
 namespace bsrht {
@@ -60,7 +83,12 @@ constexpr K1Inst kInstF64[] = {{512, 1024, 16}, {256, 512, 16}, {256, 256, 32}, 
                                {128, 64, 32}};
 
 struct SketchArgs;
+struct SketchGroup;
 // Per-family launchers (sketch_f32.cu / sketch_f64.cu).
+int sketch_group_launch_f32(const SketchPlan& plan, const SketchGroup& grp, int G, int64_t max_out,
+                            cudaStream_t stream);
+int sketch_group_launch_f64(const SketchPlan& plan, const SketchGroup& grp, int G, int64_t max_out,
+                            cudaStream_t stream);
 int sketch_launch_f32(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo,
                       cudaStream_t stream);
 int sketch_launch_f64(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo,

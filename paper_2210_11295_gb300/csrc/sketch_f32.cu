@@ -1,4 +1,6 @@
 // K1 sketch instances with FP32 arithmetic: A in f32, bf16 or f16.
+#include <algorithm>
+
 #include "sketch.cuh"
 #include "sketch_kernels.cuh"
 
@@ -71,6 +73,21 @@ int occ_typed(int inst) {
   return 0;
 }
 
+
+template <typename Tin, int NT, int R2, int JM>
+int launch_grouped(const SketchGroup& grp, int G, int64_t max_out, cudaStream_t stream) {
+  using S = K1Shape<Tin, float, kW32, NT, R2, JM>;
+  auto kern = k_sketch_grouped<Tin, float, kW32, NT, R2, JM>;
+  const size_t smem = S::smem_bytes();
+  BSRHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<G, NT, smem, stream>>>(grp);
+  BSRHT_CUDA_TRY(cudaGetLastError());
+  const unsigned bx = (unsigned)std::min<int64_t>((max_out + 255) / 256, 1024);
+  k_sketch_reduce_grouped<float, float, kW32><<<dim3(bx, (unsigned)grp.nreq), 256, 0, stream>>>(grp);
+  BSRHT_CUDA_TRY(cudaGetLastError());
+  note_launches(2);
+  return BSRHT_OK;
+}
 }  // namespace
 
 int sketch_launch_f32(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo,
@@ -90,6 +107,33 @@ int sketch_occupancy_f32(const SketchPlan& plan) {
     case BSRHT_F16: return occ_typed<__half>(plan.inst);
   }
   return 0;
+}
+
+
+namespace {
+template <typename Tin>
+int group_typed(const SketchPlan& plan, const SketchGroup& grp, int G, int64_t max_out, cudaStream_t stream) {
+  switch (plan.inst) {
+    case 0: return launch_grouped<Tin, 512, 1024, 32>(grp, G, max_out, stream);
+    case 1: return launch_grouped<Tin, 512, 512, 64>(grp, G, max_out, stream);
+    case 2: return launch_grouped<Tin, 512, 256, 64>(grp, G, max_out, stream);
+    case 3: return launch_grouped<Tin, 128, 128, 64>(grp, G, max_out, stream);
+    case 4: return launch_grouped<Tin, 128, 64, 64>(grp, G, max_out, stream);
+    case 5: return launch_grouped<Tin, 128, 32, 64>(grp, G, max_out, stream);
+    case 6: return launch_grouped<Tin, 128, 16, 64>(grp, G, max_out, stream);
+  }
+  return BSRHT_EUNSUP;
+}
+}  // namespace
+
+int sketch_group_launch_f32(const SketchPlan& plan, const SketchGroup& grp, int G, int64_t max_out,
+                            cudaStream_t stream) {
+  switch (plan.dtype) {
+    case BSRHT_F32: return group_typed<float>(plan, grp, G, max_out, stream);
+    case BSRHT_BF16: return group_typed<__nv_bfloat16>(plan, grp, G, max_out, stream);
+    case BSRHT_F16: return group_typed<__half>(plan, grp, G, max_out, stream);
+  }
+  return BSRHT_EINVAL;
 }
 
 }  // namespace bsrht

@@ -17,6 +17,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "sketch.cuh"
 
 namespace bsrht {
 
@@ -30,6 +31,21 @@ struct SketchArgs {
   int64_t nch, C, T;
   int G;
   void* part;      // Tc [(G + P) * jn * W]; slot of (CTA g, panel pc) = g + pc
+  // Grouped launches (several sketches in one persistent launch): this
+  // sketch owns the global tiles [toff, toff + T) of a launch of Gg CTAs over
+  // Tg tiles (CTA c takes [c Tg / Gg, (c + 1) Tg / Gg)), and CTA c writes
+  // partial slot (c - gfirst + pc).  A launch of one sketch has toff = 0,
+  // Tg = T, Gg = G and gfirst = 0.
+  int64_t toff, Tg;
+  int Gg, gfirst;
+  void* out;       // grouped reduce only: output, leading dimension, scale
+  int64_t ldo;
+  double scale;
+};
+
+struct SketchGroup {
+  int nreq;
+  SketchArgs r[kMaxGroup];
 };
 
 // Walsh-Hadamard butterflies over the index of a register array:
@@ -66,11 +82,16 @@ struct K1Shape {
   }
 };
 
+// The tiles of sketch g that CTA `cta` owns (see SketchArgs), with shared
+// memory smem_raw of K1Shape::smem_bytes().
 template <typename Tin, typename Tc, int W, int NT, int R2, int JM>
-__global__ void __launch_bounds__(NT, 1) k_sketch_chunked(SketchArgs g) {
+__device__ __forceinline__ void sketch_chunked_body(const SketchArgs& g, int cta, unsigned char* smem_raw) {
   using S = K1Shape<Tin, Tc, W, NT, R2, JM>;
   constexpr int NRL = S::NRL, E = S::E, Q = S::Q, JG = S::JG, DW = S::DW;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t t_begin = max((int64_t)cta * g.Tg / g.Gg - g.toff, (int64_t)0);
+  const int64_t t_end = min((int64_t)(cta + 1) * g.Tg / g.Gg - g.toff, g.T);
+  if (t_begin >= t_end) return;
+  __syncthreads();  // a previous sketch of this CTA is done with shared memory
   Tc* tile = reinterpret_cast<Tc*>(smem_raw);                        // [R2][W]
   uint32_t* s_lo = reinterpret_cast<uint32_t*>(tile + R2 * W);        // s_j & (R2-1)
   uint32_t* s_hi = s_lo + JG;                                         // s_j >> log2 R2
@@ -89,8 +110,6 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_chunked(SketchArgs g) {
     s_hi[jl] = (uint32_t)(s >> S::LOG_R2);
   }
 
-  const int64_t t_begin = (int64_t)blockIdx.x * g.T / g.G;
-  const int64_t t_end = (int64_t)(blockIdx.x + 1) * g.T / g.G;
   Tc acc[JM];
 #pragma unroll
   for (int u = 0; u < JM; ++u) acc[u] = Tc(0);
@@ -98,7 +117,7 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_chunked(SketchArgs g) {
   Tc* part = static_cast<Tc*>(g.part);
 
   auto flush = [&](int64_t pc) {
-    Tc* dst = part + ((int64_t)blockIdx.x + pc) * (int64_t)jn * W + cg;
+    Tc* dst = part + ((int64_t)(cta - g.gfirst) + pc) * (int64_t)jn * W + cg;
 #pragma unroll
     for (int u = 0; u < JM; ++u) {
       const int jl = rl + NRL * u;
@@ -181,7 +200,37 @@ __global__ void __launch_bounds__(NT, 1) k_sketch_chunked(SketchArgs g) {
   if (cur_pc >= 0) flush(cur_pc);
 }
 
+template <typename Tin, typename Tc, int W, int NT, int R2, int JM>
+__global__ void __launch_bounds__(NT, 1) k_sketch_chunked(SketchArgs g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  sketch_chunked_body<Tin, Tc, W, NT, R2, JM>(g, (int)blockIdx.x, smem_raw);
+}
+
+// Several sketches of one kernel instance in one persistent launch: the
+// tiles of all of them are laid end to end and cut evenly over the CTAs.
+template <typename Tin, typename Tc, int W, int NT, int R2, int JM>
+__global__ void __launch_bounds__(NT, 1) k_sketch_grouped(const __grid_constant__ SketchGroup grp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int q = 0; q < grp.nreq; ++q)
+    sketch_chunked_body<Tin, Tc, W, NT, R2, JM>(grp.r[q], (int)blockIdx.x, smem_raw);
+}
+
 // Fixed-order sum of the per-(CTA, panel) partials and the 1/sqrt(l) scale.
+template <typename Tc, int W>
+__device__ __forceinline__ Tc sketch_reduce_entry(const SketchArgs& g, int64_t jl, int64_t col) {
+  const int64_t pc = col / W;
+  const int cw = (int)(col - pc * W);
+  const int64_t lo = g.toff + pc * g.C, hi = lo + g.C;  // global tile range of panel pc
+  int64_t cta = lo * g.Gg / g.Tg;
+  if (cta > 0) --cta;
+  while (cta < g.Gg && (cta + 1) * g.Tg / g.Gg <= lo) ++cta;
+  const Tc* part = static_cast<const Tc*>(g.part);
+  Tc s = Tc(0);
+  for (; cta < g.Gg && cta * g.Tg / g.Gg < hi; ++cta)
+    s += part[((cta - g.gfirst + pc) * g.jn + jl) * W + cw];
+  return s;
+}
+
 template <typename Tc, typename Tout, int W>
 __global__ void k_sketch_reduce(SketchArgs g, Tout* __restrict__ out, int64_t ldo, Tc scale) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -189,17 +238,21 @@ __global__ void k_sketch_reduce(SketchArgs g, Tout* __restrict__ out, int64_t ld
   if (idx >= total) return;
   const int64_t jl = idx / g.m;
   const int64_t col = idx - jl * g.m;
-  const int64_t pc = col / W;
-  const int cw = (int)(col - pc * W);
-  const int64_t lo = pc * g.C, hi = lo + g.C;  // tile range of panel pc
-  int64_t cta = lo * g.G / g.T;
-  if (cta > 0) --cta;
-  while (cta < g.G && (cta + 1) * g.T / g.G <= lo) ++cta;
-  const Tc* part = static_cast<const Tc*>(g.part);
-  Tc s = Tc(0);
-  for (; cta < g.G && cta * g.T / g.G < hi; ++cta)
-    s += part[((cta + pc) * g.jn + jl) * W + cw];
-  out[(g.j0 + jl) * ldo + col] = (Tout)(s * scale);
+  out[(g.j0 + jl) * ldo + col] = (Tout)(sketch_reduce_entry<Tc, W>(g, jl, col) * scale);
+}
+
+// Reduce of a grouped launch: blockIdx.y selects the sketch.
+template <typename Tc, typename Tout, int W>
+__global__ void k_sketch_reduce_grouped(const __grid_constant__ SketchGroup grp) {
+  const SketchArgs& g = grp.r[blockIdx.y];
+  const int64_t total = g.jn * g.m;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t jl = idx / g.m;
+    const int64_t col = idx - jl * g.m;
+    Tout* out = static_cast<Tout*>(g.out);
+    out[(g.j0 + jl) * g.ldo + col] = (Tout)(sketch_reduce_entry<Tc, W>(g, jl, col) * (Tc)g.scale);
+  }
 }
 
 // Direct kernel for tiny blocks (r below the smallest chunk): each thread

@@ -211,12 +211,15 @@ def rbf_kernel_device(x, h: float, dtype=None, tile: int = 8192):
     return a
 
 
-def request_stream(count: int, seed: int = 1240, rate_hz: float = 100.0):
+def request_stream(count: int, seed: int = 1240, rate_hz: float = 100.0, nystrom_max_log2n: int = 15):
     """Poisson stream of mixed requests (sketch / rSVD / Nystrom).
 
     n = 2^U{14..20}, m log-uniform on [64, 4096], p in {1,2,4,8,16},
-    l log-uniform on [64, 1024] (capped at m for rSVD and n for Nystrom).
-    Returns a list of dicts with arrival time ``t`` in seconds.
+    l log-uniform on [64, 1024], target rank k = max(1, l // 4).  An rSVD
+    needs l <= min(n, m), so l is capped at m there.  A Nystrom request works
+    on an n x n PSD matrix, so its n is drawn from 2^U{14..nystrom_max_log2n}
+    (an n x n FP32 matrix at n = 2^20 would need 4 TB).  Returns a list of
+    dicts with arrival time ``t`` in seconds.
     """
     rng = _rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate_hz, size=count))
@@ -227,6 +230,12 @@ def request_stream(count: int, seed: int = 1240, rate_hz: float = 100.0):
         m = int(round(float(np.exp(rng.uniform(np.log(64), np.log(4096))))))
         p = int((1, 2, 4, 8, 16)[int(rng.integers(0, 5))])
         l = int(round(float(np.exp(rng.uniform(np.log(64), np.log(1024))))))
-        out.append({"t": float(t[i]), "kind": kind, "n": n, "m": m, "p": p, "l": l,
-                    "seed": int(rng.integers(0, 1 << 62))})
+        s = int(rng.integers(0, 1 << 62))
+        if kind == "rsvd":
+            l = min(l, m)
+        if kind == "nystrom":
+            n = 1 << int(rng.integers(14, nystrom_max_log2n + 1))
+            m = n
+        out.append({"t": float(t[i]), "kind": kind, "n": n, "m": m, "p": p, "l": l, "k": max(1, l // 4),
+                    "seed": s})
     return out
