@@ -48,8 +48,16 @@ def parse_args():
     ap.add_argument("--l", type=int, default=512)
     ap.add_argument("--k", type=int, default=100)
     ap.add_argument("--dtype", choices=["f32", "f64", "bf16", "f16"], default="f32")
-    ap.add_argument("--mode", choices=["full", "sketch"], default="full",
-                    help="full = sketch + rSVD (the benchmark step); sketch = sketch only")
+    ap.add_argument("--mode", choices=["full", "sketch", "serve"], default="full",
+                    help="full = sketch + rSVD (the benchmark step); sketch = sketch only; "
+                         "serve = the mixed request stream through the serving loop")
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="requests of the serving stream (serve mode)")
+    ap.add_argument("--serve-compare", type=int, default=120,
+                    help="requests of the reduced stream timed on both the served path and the plain "
+                         "FP64 one-at-a-time path (serve mode)")
+    ap.add_argument("--serve-window", type=int, default=96,
+                    help="most requests in flight at once (client side, serve mode)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=64)
@@ -403,8 +411,247 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------- serving
+class _ServeInputs:
+    """Resident A matrices of the serving stream: one FP32 matrix per size
+    class (n, next power of two >= m) from the config-2 generator (rank
+    min(1000, m_class / 2)), requests take its first m columns; BF16 and FP64
+    copies on demand; one PSD n x n matrix per n for Nystrom requests."""
+
+    def __init__(self):
+        self.base = {}
+        self.copies = {}
+
+    def get(self, kind, n, m, dtype):
+        import torch
+        import synth
+        if kind == "nystrom":
+            key = ("psd", n)
+            if key not in self.base:
+                self.base[key] = synth.psd_lowrank_device(n, rank=min(1000, n // 2), seed=1241 + n)
+        else:
+            mc = 64
+            while mc < m:
+                mc *= 2
+            key = (n, mc)
+            if key not in self.base:
+                self.base[key] = synth.lowrank_noise_device(n, mc, rank=min(1000, mc // 2), seed=1236 + n + mc)
+        src = self.base[key]
+        if dtype != torch.float32:
+            ck = key + (dtype,)
+            if ck not in self.copies:
+                self.copies[ck] = src.to(dtype)
+            src = self.copies[ck]
+        return src if kind == "nystrom" else src[:, :m]
+
+    def bytes(self):
+        return sum(t.numel() * t.element_size() for t in list(self.base.values()) + list(self.copies.values()))
+
+
+def _serve_outputs(req, dtype, lib):
+    import torch
+    n, m, l, k = req["n"], req["m"], req["l"], req["k"]
+    if req["kind"] == "sketch":
+        return (torch.empty(l, m, device="cuda", dtype=lib.sketch_out_dtype(dtype)),)
+    if req["kind"] == "rsvd":
+        return (torch.empty(n, k, device="cuda", dtype=torch.float64), torch.empty(k, device="cuda", dtype=torch.float64),
+                torch.empty(m, k, device="cuda", dtype=torch.float64))
+    return (torch.empty(n, k, device="cuda", dtype=torch.float64), torch.empty(k, device="cuda", dtype=torch.float64))
+
+
+def _serve_run(lib, inputs, reqs, dtypes, rate, window, keep_outputs=False, **server_kw):
+    """Feeds reqs (arrival times scaled to `rate` req/s; inf = all at once)
+    to a fresh server, at most `window` in flight.  Returns (makespan s,
+    latencies arrival->done ms, stats, outputs)."""
+    import torch
+    arrivals = [0.0] * len(reqs)
+    if not math.isinf(rate):
+        t0r = reqs[0]["t"]
+        scale = (len(reqs) / rate) / max(reqs[-1]["t"] - t0r, 1e-9)
+        arrivals = [(r["t"] - t0r) * scale for r in reqs]
+    mats = [inputs.get(r["kind"], r["n"], r["m"], dt) for r, dt in zip(reqs, dtypes)]
+    torch.cuda.synchronize()
+    outs = [None] * len(reqs)
+    tickets = [None] * len(reqs)
+    lat = [None] * len(reqs)
+    with lib.Server(**server_kw) as srv:
+        inflight = []
+        start = time.monotonic()
+        for i, (r, a) in enumerate(zip(reqs, mats)):
+            while len(inflight) >= window:
+                j = inflight.pop(0)
+                srv.wait(tickets[j], 3600.0)
+                if not keep_outputs:
+                    outs[j] = None
+            delay = start + arrivals[i] - time.monotonic()
+            if delay > 0:
+                time.sleep(delay)
+            o = _serve_outputs(r, dtypes[i], lib)
+            if r["kind"] == "sketch":
+                t = srv.submit_sketch(a, r["p"], r["l"], r["seed"], o[0])
+            elif r["kind"] == "rsvd":
+                t = srv.submit_rsvd(a, r["k"], r["l"], r["p"], r["seed"], o)
+            else:
+                t = srv.submit_nystrom(a, r["k"], r["l"], r["p"], r["seed"], o)
+            tickets[i], outs[i] = t, o
+            inflight.append(i)
+        for j in inflight:
+            srv.wait(tickets[j], 3600.0)
+        end = max(srv.times(t)[1] for t in tickets)
+        for i, t in enumerate(tickets):
+            lat[i] = (srv.times(t)[1] - (start + arrivals[i])) * 1e3
+        st = srv.stats()
+        bad = [(i, srv.poll(t)[1]) for i, t in enumerate(tickets) if srv.poll(t)[1] != 0]
+    if bad:
+        detail = "; ".join(f"{reqs[i]} {dtypes[i]}: {lib.strerror(st)}" for i, st in bad[:8])
+        raise RuntimeError(f"{len(bad)} served requests failed: {detail}")
+    return end - start, lat, st, outs
+
+
+def _plain_run(lib, inputs, reqs, rate, keep_outputs=False):
+    """The plain path: FP64 inputs, one direct library call at a time on one
+    stream, no grouping, graphs or tuning; requests queue behind each other."""
+    import torch
+    t0r = reqs[0]["t"]
+    if math.isinf(rate):
+        arrivals = [0.0] * len(reqs)
+    else:
+        scale = (len(reqs) / rate) / max(reqs[-1]["t"] - t0r, 1e-9)
+        arrivals = [(r["t"] - t0r) * scale for r in reqs]
+    mats = [inputs.get(r["kind"], r["n"], r["m"], torch.float64) for r in reqs]
+    torch.cuda.synchronize()
+    lat, outs = [], []
+    start = time.monotonic()
+    for r, a, arr in zip(reqs, mats, arrivals):
+        delay = start + arr - time.monotonic()
+        if delay > 0:
+            time.sleep(delay)
+        if r["kind"] == "sketch":
+            o = (lib.bsrht_sketch(a, r["p"], r["l"], r["seed"]),)
+        elif r["kind"] == "rsvd":
+            o = lib.bsrht_rsvd(a, r["k"], r["l"], r["p"], r["seed"])
+        else:
+            o = lib.bsrht_nystrom(a, r["k"], r["l"], r["p"], r["seed"])
+        torch.cuda.synchronize()
+        lat.append((time.monotonic() - start - arr) * 1e3)
+        outs.append(o if keep_outputs else None)
+    return time.monotonic() - start, lat, outs
+
+
+def _pct(v, q):
+    v = sorted(v)
+    rank = max(1, min(len(v), math.ceil(q / 100.0 * len(v))))
+    return v[rank - 1]
+
+
+def _accuracy(lib, inputs, reqs, outs_served, outs_plain, dtypes):
+    """Per request: sketch -> relative Frobenius difference served vs plain;
+    rSVD -> |err_served - err_plain| / err_plain of ||A - U S V^T||_F;
+    Nystrom -> same on tr(A) - sum(Lambda) (exact trace error, the residual
+    is PSD).  Returns the worst of each kind."""
+    import torch
+    worst = {"sketch": 0.0, "rsvd": 0.0, "nystrom": 0.0}
+    for r, so, po, dt in zip(reqs, outs_served, outs_plain, dtypes):
+        a = inputs.get(r["kind"], r["n"], r["m"], torch.float64)
+        if r["kind"] == "sketch":
+            d = (torch.linalg.norm(so[0].double() - po[0]) / torch.linalg.norm(po[0])).item()
+        elif r["kind"] == "rsvd":
+            def err(o):
+                u, s, v = o
+                return torch.linalg.norm(a - (u * s) @ v.T).item()
+            ep = err(po)
+            d = abs(err(so) - ep) / max(ep, 1e-300)
+        else:
+            tr = torch.trace(a).item()
+            ep = tr - po[1].sum().item()
+            d = abs((tr - so[1].sum().item()) - ep) / max(abs(ep), 1e-300)
+        worst[r["kind"]] = max(worst[r["kind"]], d)
+    return worst
+
+
+def run_serve(args):
+    """Config-5 stream through the serving loop: Poisson arrivals at 0.5x,
+    0.8x and 1.0x of the measured saturation throughput, p50 / p99 latency
+    (arrival to completion) and throughput; then a reduced stream (n <= 2^17,
+    m <= 1024, Nystrom n = 2^14) through both the served path and the plain FP64
+    one-at-a-time path, with their accuracy compared request by request."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2210_11295_gb300 as lib
+
+    torch.cuda.set_device(0)
+    reqs = synth.request_stream(args.serve_requests, seed=1240, rate_hz=1.0)
+    rng = np.random.default_rng(1242)
+    dtypes = [torch.bfloat16 if rng.random() < 0.5 and r["kind"] != "nystrom" else torch.float32 for r in reqs]
+    inputs = _ServeInputs()
+    kw = dict(hbm_budget=24 << 30, executors=4, max_group=16)
+    bytes_a = sum(r["n"] * r["m"] * (2 if dt == torch.bfloat16 else 4) for r, dt in zip(reqs, dtypes))
+    # Warm-up pass (graphs, tuning, allocator) on the first requests, then saturation.
+    _serve_run(lib, inputs, reqs[: min(60, len(reqs))], dtypes, math.inf, args.serve_window, **kw)
+    sat_s, lat_sat, st_sat, _ = _serve_run(lib, inputs, reqs, dtypes, math.inf, args.serve_window, **kw)
+    x_sat = len(reqs) / sat_s
+    points = []
+    for frac in (0.5, 0.8, 1.0):
+        ms, lat, st, _ = _serve_run(lib, inputs, reqs, dtypes, frac * x_sat, args.serve_window, **kw)
+        points.append({"load": frac, "rate_req_s": round(frac * x_sat, 2), "makespan_s": round(ms, 3),
+                       "throughput_req_s": round(len(reqs) / ms, 2), "p50_ms": round(_pct(lat, 50), 3),
+                       "p99_ms": round(_pct(lat, 99), 3),
+                       "grouped_launches": st["grouped_launches"], "grouped_requests": st["grouped_requests"],
+                       "graph_launches": st["graph_launches"]})
+    # Served vs plain FP64 one-at-a-time on the reduced stream.
+    small = [r for r in synth.request_stream(20 * args.serve_compare, seed=1243, rate_hz=1.0, nystrom_max_log2n=14)
+             if r["n"] <= 1 << 17 and (r["m"] <= 1024 or r["kind"] == "nystrom")][: args.serve_compare]
+    sdt = [torch.float32] * len(small)
+    p_s, p_lat, p_outs = _plain_run(lib, inputs, small, math.inf, keep_outputs=True)
+    s_s, s_lat, s_st, s_outs = _serve_run(lib, inputs, small, sdt, math.inf, len(small), keep_outputs=True, **kw)
+    acc = _accuracy(lib, inputs, small, s_outs, p_outs, sdt)
+    rate = 0.8 * len(small) / p_s
+    p2_s, p2_lat, _ = _plain_run(lib, inputs, small, rate)
+    s2_s, s2_lat, _, _ = _serve_run(lib, inputs, small, sdt, rate, len(small), **kw)
+    line = {
+        "metric": "serving: throughput (req/s) and p50/p99 latency (arrival to completion, ms)",
+        "value": round(x_sat, 3), "unit": "req/s", "n_gpus": 1, "higher_is_better": True,
+        "data": "synthetic", "dtype": "f32/bf16 storage, FP32 sketch arithmetic, FP64 QR/SVD/Cholesky",
+        "config": {"workload": f"Poisson stream of {len(reqs)} sketch/rSVD/Nystrom requests, n=2^U{{14..20}}, "
+                               "m log-uniform [64,4096], p in {1,2,4,8,16}, l log-uniform [64,1024], "
+                               "k=l//4, FP32 or BF16 (Nystrom: n<=2^15, FP32 PSD)",
+                   "executors": kw["executors"], "max_group": kw["max_group"], "hbm_budget": kw["hbm_budget"],
+                   "window": args.serve_window, "input_gb": round(inputs.bytes() / 1e9, 2)},
+        "saturation": {"makespan_s": round(sat_s, 3), "throughput_req_s": round(x_sat, 2),
+                       "a_gb_per_s": round(bytes_a / sat_s / 1e9, 2), "p50_ms": round(_pct(lat_sat, 50), 3),
+                       "p99_ms": round(_pct(lat_sat, 99), 3), "grouped_launches": st_sat["grouped_launches"],
+                       "grouped_requests": st_sat["grouped_requests"], "graph_launches": st_sat["graph_launches"],
+                       "tuned_classes": st_sat["tuned_classes"]},
+        "poisson": points,
+        "vs_plain_fp64": {
+            "stream": f"{len(small)} requests with n <= 2^17, m <= 1024, Nystrom n = 2^14 "
+                      "(FP32 served, FP64 plain)",
+            "closed_batch": {"served_req_s": round(len(small) / s_s, 2), "plain_req_s": round(len(small) / p_s, 2),
+                             "speedup": round(p_s / s_s, 2),
+                             "served_p50_ms": round(_pct(s_lat, 50), 3), "served_p99_ms": round(_pct(s_lat, 99), 3),
+                             "plain_p50_ms": round(_pct(p_lat, 50), 3), "plain_p99_ms": round(_pct(p_lat, 99), 3)},
+            "poisson_at_0.8x_plain": {"rate_req_s": round(rate, 2),
+                                      "served_p50_ms": round(_pct(s2_lat, 50), 3),
+                                      "served_p99_ms": round(_pct(s2_lat, 99), 3),
+                                      "plain_p50_ms": round(_pct(p2_lat, 50), 3),
+                                      "plain_p99_ms": round(_pct(p2_lat, 99), 3)},
+            "accuracy_worst": {k: float(f"{v:.3e}") for k, v in acc.items()},
+            "accuracy_note": "sketch: relative Frobenius difference to the FP64 result; rSVD: relative "
+                             "difference of ||A - U S V^T||_F; Nystrom: of tr(A) - sum(Lambda)"},
+        "gpu_launches": int(lib.bsrht_kernel_launches()),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.mode == "serve":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "serve mode has no CPU reference arm"}))
+            return
+        run_serve(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -297,6 +297,9 @@ int bsrht_poll(bsrht_server* s, uint64_t ticket, int* done);
  * ETIMEDOUT (the request keeps running).                                   */
 int bsrht_wait(bsrht_server* s, uint64_t ticket, int64_t timeout_us);
 int bsrht_server_stats_get(bsrht_server* s, bsrht_server_stats* out);
+/* Submit and completion times of a request in seconds of the host's
+ * monotonic clock (CLOCK_MONOTONIC); *done_s = -1 while it is pending.     */
+int bsrht_request_times(bsrht_server* s, uint64_t ticket, double* submit_s, double* done_s);
 /* Lets queued and running requests finish, joins the executors, frees the
  * pool and the graphs.  The server must not be used afterwards.            */
 int bsrht_server_destroy(bsrht_server* s);

@@ -133,6 +133,8 @@ def _load() -> ctypes.CDLL:
         "bsrht_poll": (ctypes.c_int, [vp, u64, ctypes.POINTER(ctypes.c_int)]),
         "bsrht_wait": (ctypes.c_int, [vp, u64, i64]),
         "bsrht_server_stats_get": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
+        "bsrht_request_times": (ctypes.c_int, [vp, u64, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double)]),
         "bsrht_server_destroy": (ctypes.c_int, [vp]),
         "bsrht_selftest_pool_allocator": (ctypes.c_int, [u64, i32]),
     }
@@ -388,6 +390,13 @@ class Server:
         if st != BSRHT_ETIMEDOUT:
             self._keep.pop(int(ticket), None)
         return st
+
+    def times(self, ticket: int) -> tuple[float, float]:
+        """(submit, done) in seconds of the monotonic clock (time.monotonic's);
+        done is -1 while the request is pending."""
+        a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(lib.bsrht_request_times(self._h, int(ticket), ctypes.byref(a), ctypes.byref(b)), "bsrht_request_times")
+        return float(a.value), float(b.value)
 
     def stats(self) -> dict:
         s = ServerStats()

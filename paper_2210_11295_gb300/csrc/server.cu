@@ -436,7 +436,8 @@ int validate_and_size(bsrht_server* sv, const bsrht_request& r, Req& q) {
       q.gplan = gp;
       bytes = sketch_group_work_bytes(gp);
     } else {
-      bytes = pl.work_bytes;
+      // Sized for any instance: the shape class may be tuned before it runs.
+      bytes = std::max(pl.work_bytes, sketch_autotune_work_bytes(r.dtype, r.n, r.m, lda, r.p, r.l));
       if (sv->o.autotune && pl.path != 1) {
         std::lock_guard<std::mutex> lock(sv->mu);
         const int cls = tune_class(r, lda);
@@ -549,6 +550,16 @@ int bsrht_wait(bsrht_server* sv, uint64_t ticket, int64_t timeout_us) {
   if (!sv->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), [&] { return q->done; }))
     return BSRHT_ETIMEDOUT;
   return q->status;
+}
+
+int bsrht_request_times(bsrht_server* sv, uint64_t ticket, double* submit_s, double* done_s) {
+  if (!sv || !submit_s || !done_s) return BSRHT_EINVAL;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return BSRHT_EINVAL;
+  *submit_s = it->second->t_submit;
+  *done_s = it->second->done ? it->second->t_done : -1.0;
+  return BSRHT_OK;
 }
 
 int bsrht_server_stats_get(bsrht_server* sv, bsrht_server_stats* out) {

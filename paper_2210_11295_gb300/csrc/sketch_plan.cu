@@ -202,6 +202,16 @@ int sketch_make_plan(SketchPlan& pl, int dtype, int variant, int64_t n, int64_t 
   }
   int st = make_plan_choice(pl, dtype, n, m, lda, p, l, query_device, A, choice);
   if (st != BSRHT_OK && choice != -2) st = make_plan_choice(pl, dtype, n, m, lda, p, l, query_device, A, -2);
+  if (st == BSRHT_OK && A == nullptr && pl.path != 1) {
+    // Scratch sized without A must also hold whatever plan the autotuner
+    // records for this shape class before the run: reserve the largest.
+    const bool f64 = dtype == BSRHT_F64;
+    for (int c = -1; c < n_instances(f64); ++c) {
+      SketchPlan alt;
+      if (make_plan_choice(alt, dtype, n, m, lda, p, l, query_device, nullptr, c) == BSRHT_OK)
+        pl.work_bytes = std::max(pl.work_bytes, alt.work_bytes);
+    }
+  }
   return st;
 }
 

@@ -151,6 +151,26 @@ def lowrank_noise_device(n: int, m: int, rank: int = 1000, noise: float = 1e-4,
     return a
 
 
+def psd_lowrank_device(n: int, rank: int = 1000, seed: int = 1241, dtype=None, device="cuda"):
+    """Symmetric PSD n x n matrix G diag(i^-2) G^T on the device (G Gaussian
+    with orthonormalised columns): the config-2 spectrum for Nystrom requests."""
+    import torch
+
+    dtype = dtype or torch.float32
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    rank = min(rank, n)
+    g = _orthonormalize_device(torch.randn(n, rank, generator=gen, device=device, dtype=torch.float32), torch)
+    sigma = torch.arange(1, rank + 1, device=device, dtype=torch.float32) ** -2.0
+    a = torch.empty(n, n, device=device, dtype=dtype)
+    gs = (g * sigma).T.contiguous()
+    step = 1 << 14
+    for r0 in range(0, n, step):
+        r1_ = min(n, r0 + step)
+        a[r0:r1_] = (g[r0:r1_] @ gs).to(dtype)
+    return a
+
+
 def rbf_points(n: int, d: int = 784, seed: int = 1238, dtype=np.float32) -> np.ndarray:
     """x_i ~ U[0,1]^d, i < n (row-major n x d)."""
     return _rng(seed).random((n, d)).astype(dtype)

@@ -72,6 +72,8 @@ def test_workspace_query_scales():
     import paper_2210_11295_gb300 as b
     w1 = b.bsrht_sketch_workspace(1 << 20, 4096, 4, 512, torch.float32)
     w2 = b.bsrht_sketch_workspace(1 << 20, 4096, 4, 512, torch.float64)
-    assert 0 < w1 < 64 << 20 and 0 < w2 < 128 << 20
+    # Sized for every kernel instance the autotuner may record (per-CTA
+    # partials of l x 32 columns): well under 2 % of the 16 / 32 GiB input.
+    assert 0 < w1 < 256 << 20 and 0 < w2 < 512 << 20
     # Tiny blocks take the direct path, which needs no scratch.
     assert b.bsrht_sketch_workspace(64, 8, 64, 16, torch.float32) == 0
