@@ -42,11 +42,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=1 << 20)
-    ap.add_argument("--m", type=int, default=4096)
-    ap.add_argument("--p", type=int, default=4)
-    ap.add_argument("--l", type=int, default=512)
-    ap.add_argument("--k", type=int, default=100)
+    # Long aliases: under torchrun, options that prefix one of its own
+    # (--n: --nnodes, --nproc-per-node) are taken as ambiguous by its parser.
+    ap.add_argument("--n", "--rows", dest="n", type=int, default=1 << 20)
+    ap.add_argument("--m", "--cols", dest="m", type=int, default=4096)
+    ap.add_argument("--p", "--blocks", dest="p", type=int, default=4)
+    ap.add_argument("--l", "--sketch-rows", dest="l", type=int, default=512)
+    ap.add_argument("--k", "--target-rank", dest="k", type=int, default=100)
     ap.add_argument("--dtype", choices=["f32", "f64", "bf16", "f16"], default="f32")
     ap.add_argument("--mode", choices=["full", "sketch", "serve"], default="full",
                     help="full = sketch + rSVD (the benchmark step); sketch = sketch only; "
@@ -61,6 +63,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=64)
+    ap.add_argument("--cpu-sample-rows", type=int, default=1 << 14)
     return ap.parse_args()
 
 
@@ -184,29 +187,51 @@ def make_input(args, rank):
 
 
 # --------------------------------------------------------------- CPU oracle
-def cpu_baseline(args, seconds_target=15.0):
-    """The CPU oracle's dense sketch on a column sample of the same workload
-    (the sketch is column-separable), scaled to GB/s of A."""
+def _oracle_sample(args):
+    """The oracle's bounded sample of the workload and its step.
+
+    full mode: Algorithm 1 as the oracle states it (dense-Omega sketch, LAPACK
+    QR and SVD) on the first n_s rows of the same generator (n_s = min(n,
+    2^14) by default), GB/s of those rows; every stage but the l x l SVD
+    grows linearly with the rows, so this slightly flatters nothing but the
+    oracle's fixed costs.  sketch mode: the dense-Omega sketch of an
+    n x cols column slice (the sketch is column-separable)."""
     import numpy as np
     from oracle import bsrht as orc
+    from oracle import lowrank as orl
     import synth
 
-    cols = args.cpu_sample_cols
-    n = args.n
-    a = synth.lowrank_noise(n, cols, rank=min(1000, cols), seed=77).astype(np.float32)
+    elem = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}[args.dtype]
+    if args.mode == "sketch":
+        cols = args.cpu_sample_cols
+        a = synth.lowrank_noise(args.n, cols, rank=min(1000, cols), seed=77).astype(np.float32)
+        step = lambda s: orc.sketch_dense(a, args.p, args.l, seed=s)  # noqa: E731
+        return step, args.n * cols * elem, (f"dense-Omega oracle sketch of an n={args.n} x {cols}-column slice "
+                                            f"(p={args.p}, l={args.l}); GB/s of A")
+    ns = min(args.n, args.cpu_sample_rows)
+    a = synth.lowrank_noise(ns, args.m, rank=min(1000, args.m), seed=77).astype(np.float32).astype(np.float64)
+    l = min(args.l, args.m, ns)
+    k = min(args.k, l)
+    step = lambda s: orl.rsvd(a, k, l, args.p, s)  # noqa: E731
+    return step, ns * args.m * elem, (f"oracle Algorithm 1 (dense-Omega sketch + LAPACK QR/SVD, FP64) on "
+                                      f"n={ns} x m={args.m} rows of the workload generator (p={args.p}, l={l}, "
+                                      f"k={k}); GB/s of A rows")
+
+
+def cpu_baseline(args, seconds_target=15.0):
+    """The CPU oracle on a bounded sample of the same workload, in GB/s of A."""
+    step, nbytes, sample = _oracle_sample(args)
     t0 = time.perf_counter()
     reps = 0
     while True:
-        orc.sketch_dense(a, args.p, args.l, seed=reps)
+        step(reps)
         reps += 1
         if time.perf_counter() - t0 > seconds_target or reps >= 3:
             break
     dt = (time.perf_counter() - t0) / reps
-    elem = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}[args.dtype]
-    gbs = n * cols * elem / dt / 1e9
+    gbs = nbytes / dt / 1e9
     return {"value": round(gbs, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"dense-Omega oracle sketch of an n={n} x {cols}-column slice "
-                      f"(p={args.p}, l={args.l}), {reps} rep(s), {dt:.2f} s each; GB/s of A columns"}
+            "sample": f"{sample}; {reps} rep(s), {dt:.2f} s each"}
 
 
 def run_reference(args):
@@ -214,28 +239,22 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and rank != 0:
         return
-    import numpy as np
-    from oracle import bsrht as orc
-    import synth
-
-    cols = args.cpu_sample_cols
-    a = synth.lowrank_noise(args.n, cols, rank=min(1000, cols), seed=77).astype(np.float32)
+    step, nbytes, sample = _oracle_sample(args)
     for w in range(args.warmup):
-        orc.sketch_dense(a, args.p, args.l, seed=w)
+        step(w)
     times = []
     for s in range(args.steps):
         t0 = time.perf_counter()
-        orc.sketch_dense(a, args.p, args.l, seed=s)
+        step(s)
         times.append(time.perf_counter() - t0)
     dt = statistics.mean(times)
-    elem = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}[args.dtype]
-    gbs = args.n * cols * elem / dt / 1e9
-    sample = (f"each step: dense-Omega oracle sketch of an n={args.n} x {cols}-column slice of the "
-              f"workload (column-separable), GB/s of A")
+    gbs = nbytes / dt / 1e9
+    workload = WORKLOAD if (args.mode == "full" and args.dtype == "f32" and args.n == 1 << 20 and args.m == 4096) \
+        else f"n={args.n} m={args.m} {args.dtype} p={args.p} l={args.l} k={args.k} mode={args.mode}"
     line = {"metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample}, "impl": "reference",
+            "config": {"workload": workload, "sample": sample}, "impl": "reference",
             "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
