@@ -50,9 +50,11 @@ def parse_args():
     ap.add_argument("--l", "--sketch-rows", dest="l", type=int, default=512)
     ap.add_argument("--k", "--target-rank", dest="k", type=int, default=100)
     ap.add_argument("--dtype", choices=["f32", "f64", "bf16", "f16"], default="f32")
-    ap.add_argument("--mode", choices=["full", "sketch", "serve"], default="full",
+    ap.add_argument("--mode", choices=["full", "sketch", "serve", "nystrom"], default="full",
                     help="full = sketch + rSVD (the benchmark step); sketch = sketch only; "
-                         "serve = the mixed request stream through the serving loop")
+                         "serve = the mixed request stream through the serving loop; "
+                         "nystrom = Algorithm 2 on the RBF kernel workload (n = --rows points)")
+    ap.add_argument("--nystrom-ks", default="100,200,400", help="target ranks of the nystrom mode")
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="requests of the serving stream (serve mode)")
     ap.add_argument("--serve-compare", type=int, default=120,
@@ -663,8 +665,82 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_nystrom(args):
+    """Algorithm 2 on the kernel workload: A_ij = exp(-|xi - xj|^2 / (2 h^2)),
+    x_i ~ U[0,1]^784, h = median pairwise distance (seeded 4096-point
+    subsample), FP32 n x n; p, l from the command line (8, 600 for the
+    65536-point case), every k of --nystrom-ks.  Reports the step time, the
+    sketch kernel's HBM rate and the trace error tr(A) - sum(Lambda) (exact:
+    the residual is PSD, Sec. 3.2)."""
+    import torch
+    import synth
+    import paper_2210_11295_gb300 as lib
+
+    torch.cuda.set_device(0)
+    n, p, l = args.n, args.p, args.l
+    x = synth.rbf_points(n, 784, seed=1238)
+    h = synth.rbf_bandwidth(x)
+    a = synth.rbf_kernel_device(torch.from_numpy(x).cuda(), h, dtype=torch.float32)
+    del x
+    torch.cuda.synchronize()
+    tr = float(torch.trace(a.double()).item())
+    stream = torch.cuda.current_stream()
+    results = []
+    for k in [int(v) for v in args.nystrom_ks.split(",")]:
+        ws = torch.empty(lib.bsrht_nystrom_workspace(n, k, l, p, torch.float32), dtype=torch.uint8, device="cuda")
+        u = torch.empty(n, k, device="cuda", dtype=torch.float64)
+        lam = torch.empty(k, device="cuda", dtype=torch.float64)
+        for w in range(args.warmup):
+            lib.bsrht_nystrom(a, k, l, p, w, workspace=ws, outs=(u, lam))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.steps):
+            lib.bsrht_nystrom(a, k, l, p, 100 + i, workspace=ws, outs=(u, lam))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        lib.bsrht_profile_enable(True)
+        lib.bsrht_nystrom(a, k, l, p, 7, workspace=ws, outs=(u, lam))
+        torch.cuda.synchronize()
+        stages = {name: round(t, 3) for name, t in lib.bsrht_profile_stages()}
+        lib.bsrht_profile_enable(False)
+        results.append({"k": k, "ms_per_step": round(ms, 3), "trace_error": tr - float(lam.sum().item()),
+                        "trace_error_rel": (tr - float(lam.sum().item())) / tr, "stages_ms": stages})
+    out = torch.empty(l, n, device="cuda", dtype=torch.float32)
+    sws = torch.empty(max(lib.bsrht_sketch_workspace(n, n, p, l, torch.float32), 1), dtype=torch.uint8,
+                      device="cuda")
+    lib.bsrht_sketch(a, p, l, 0, out=out, workspace=sws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        lib.bsrht_sketch(a, p, l, i, out=out, workspace=sws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sk_ms = e0.elapsed_time(e1) / args.steps
+    peak, peak_kind = peaks()
+    gbs = (n * n * 4 + l * n * 4) / (sk_ms * 1e-3) / 1e9
+    line = {"metric": "Nystrom (Algorithm 2) time at stated trace error; sketch A Omega^T HBM GB/s",
+            "value": results[0]["ms_per_step"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"RBF kernel n={n} (x ~ U[0,1]^784, median bandwidth h={h:.4f}) fp32 p={p} l={l}",
+                       "steps": args.steps, "warmup": args.warmup},
+            "per_k": results,
+            "sketch": {"ms": round(sk_ms, 4), "gbs": round(gbs, 2), "frac_of_measured_peak": round(gbs / peak, 4),
+                       "peak_kind": peak_kind},
+            "trace_A": tr}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.mode == "nystrom":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "nystrom mode has no CPU reference arm"}))
+            return
+        run_nystrom(args)
+        return
     if args.mode == "serve":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "serve mode has no CPU reference arm"}))
