@@ -62,6 +62,8 @@ def parse_args():
                          "FP64 one-at-a-time path (serve mode)")
     ap.add_argument("--serve-window", type=int, default=96,
                     help="most requests in flight at once (client side, serve mode)")
+    ap.add_argument("--variant", choices=["auto", "cudacore", "tensor"], default="auto",
+                    help="sketch kernel: library choice, CUDA-core butterflies (K1) or tensor cores (K2, 16-bit A)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=64)
@@ -306,11 +308,13 @@ def run_ours(args):
         s = torch.empty(k, device=dev, dtype=torch.float64)
         v = torch.empty(m, k, device=dev, dtype=torch.float64)
 
+    variant = {"auto": lib.VARIANT_AUTO, "cudacore": lib.VARIANT_CUDACORE, "tensor": lib.VARIANT_TENSOR}[args.variant]
+
     def step(seed):
         if mode == "full":
-            lib.bsrht_rsvd(a, k, l, p, seed, workspace=rws, outs=(u, s, v))
+            lib.bsrht_rsvd(a, k, l, p, seed, variant=variant, workspace=rws, outs=(u, s, v))
         else:
-            lib.bsrht_sketch(a, p, l, seed, out=out, workspace=ws)
+            lib.bsrht_sketch(a, p, l, seed, out=out, workspace=ws, variant=variant)
 
     for w in range(args.warmup):
         step(w)
@@ -325,7 +329,7 @@ def run_ours(args):
     time.sleep(0.3)
     for i in range(args.steps):
         ev[i][0].record(stream)
-        lib.bsrht_sketch(a, p, l, 1000 + i, out=out, workspace=ws)
+        lib.bsrht_sketch(a, p, l, 1000 + i, out=out, workspace=ws, variant=variant)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     sketch_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
@@ -376,12 +380,12 @@ def run_ours(args):
         for i in range(args.e2e_steps):
             a_dev2.copy_(a_host, non_blocking=True)
             if mode == "full":
-                lib.bsrht_rsvd(a_dev2, k, l, p, i, workspace=rws, outs=(u, s, v))
+                lib.bsrht_rsvd(a_dev2, k, l, p, i, variant=variant, workspace=rws, outs=(u, s, v))
                 hu.copy_(u, non_blocking=True)
                 hs.copy_(s, non_blocking=True)
                 hv.copy_(v, non_blocking=True)
             else:
-                lib.bsrht_sketch(a_dev2, p, l, i, out=out, workspace=ws)
+                lib.bsrht_sketch(a_dev2, p, l, i, out=out, workspace=ws, variant=variant)
                 hb.copy_(out, non_blocking=True)
             torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
@@ -413,7 +417,9 @@ def run_ours(args):
                    "frac_of_measured_peak": round(achieved / peak, 4)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": sketch_traffic(args, mode),
-                     "kernel": "k_sign_tables + k_sketch_tma + k_sketch_reduce_checked (one bsrht_sketch call)",
+                     "kernel": ("k_sketch_chunked + k_sketch_reduce" if args.dtype == "f64" else
+                                "k_sketch_tc + k_sketch_reduce_checked" if args.variant == "tensor" else
+                                "k_sign_tables + k_sketch_tma + k_sketch_reduce_checked") + " (one bsrht_sketch call)",
                      "peak_kind": peak_kind},
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
         "e2e": {"value": round(total_bytes_all / (e2e_ms * 1e-3) / 1e9, 3) if e2e_ms else None, "unit": "GB/s",

@@ -13,7 +13,8 @@ constexpr int kMaxGroup = 32;
 struct SketchPlan {
   int dtype = 0;      // bsrht_dtype of A
   int variant = 1;    // 1 = CUDA-core butterflies (K1), 2 = tensor cores (K2)
-  int path = 0;       // 0 = chunked FWHT kernel, 1 = small-r direct kernel, 2 = TMA-fed chunked kernel
+  int path = 0;       // 0 = chunked FWHT kernel, 1 = small-r direct kernel, 2 = TMA-fed chunked kernel,
+                      // 3 = tensor-core kernel (K2, 16-bit inputs)
   int inst = 0;       // kernel instance id within the dtype family
   int W = 0, NT = 0, R2 = 0, JM = 0, NRL = 0;
   int64_t n = 0, m = 0, lda = 0, l = 0;
@@ -99,5 +100,9 @@ int sketch_occupancy_f64(const SketchPlan& plan);
 int sketch_occupancy_tma(const SketchPlan& plan);
 int sketch_launch_tma(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo, int* err,
                       uint64_t* dtab, uint64_t* dttab, cudaStream_t stream);
+// Tensor-core path (sketch_tc.cu, K2): BF16 / F16, W = 32, R2 = 512.
+int sketch_occupancy_tc(const SketchPlan& plan);
+int sketch_launch_tc(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo, int* err,
+                     cudaStream_t stream);
 
 }  // namespace bsrht

@@ -255,6 +255,31 @@ __global__ void k_sketch_reduce_grouped(const __grid_constant__ SketchGroup grp)
   }
 }
 
+// Fixed-order reduce; NaN output if any CTA reported a failed wait.
+template <int W>
+__global__ void k_sketch_reduce_checked(SketchArgs g, float* __restrict__ out, int64_t ldo, float scale,
+                                        const int* __restrict__ err) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = g.jn * g.m;
+  if (idx >= total) return;
+  const int64_t jl = idx / g.m;
+  const int64_t col = idx - jl * g.m;
+  if (*err) {
+    out[(g.j0 + jl) * ldo + col] = __int_as_float(0x7fc00000);
+    return;
+  }
+  const int64_t pc = col / W;
+  const int cw = (int)(col - pc * W);
+  const int64_t lo = pc * g.C, hi = lo + g.C;
+  int64_t cta = lo * g.G / g.T;
+  if (cta > 0) --cta;
+  while (cta < g.G && (cta + 1) * g.T / g.G <= lo) ++cta;
+  const float* part = static_cast<const float*>(g.part);
+  float s = 0.f;
+  for (; cta < g.G && cta * g.T / g.G < hi; ++cta) s += part[((cta + pc) * g.jn + jl) * W + cw];
+  out[(g.j0 + jl) * ldo + col] = s * scale;
+}
+
 // Direct kernel for tiny blocks (r below the smallest chunk): each thread
 // forms one output entry as the explicit +-1 combination of its column.
 template <typename Tin, typename Tc, typename Tout>

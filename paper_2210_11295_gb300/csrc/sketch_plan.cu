@@ -66,6 +66,35 @@ static int make_plan_tma(SketchPlan& pl, bool query_device) {
   return BSRHT_OK;
 }
 
+// Tensor-core kernel (K2): 16-bit inputs, blocks of at least one 512-row
+// chunk, TMA-compatible rows.
+static bool tc_eligible(const SketchPlan& pl, const void* A) {
+  return (pl.dtype == BSRHT_BF16 || pl.dtype == BSRHT_F16) && pl.r >= 512 && tma_layout_ok(pl.dtype, A, pl.lda);
+}
+
+static int make_plan_tc(SketchPlan& pl, bool query_device) {
+  pl.path = 3;
+  pl.variant = BSRHT_VARIANT_TENSOR;
+  pl.W = 32;
+  pl.NT = 512;
+  pl.R2 = 512;
+  pl.JM = pl.l <= 512 ? 32 : 64;
+  pl.NRL = pl.NT / pl.W;
+  pl.jgroup = std::min<int64_t>(pl.l, (int64_t)pl.JM * pl.NRL);
+  pl.nch = (pl.rb + pl.R2 - 1) / pl.R2;
+  pl.C = (int64_t)pl.p * pl.nch;
+  pl.P = (pl.m + pl.W - 1) / pl.W;
+  pl.T = pl.P * pl.C;
+  int occ = query_device ? sketch_occupancy_tc(pl) : 0;
+  if (occ <= 0) occ = 1;
+  const int64_t g = (int64_t)num_sms() * occ;
+  pl.G = (int)std::max<int64_t>(1, std::min<int64_t>(g, std::max<int64_t>(pl.T, 1)));
+  pl.part_bytes = align_up(4 * (size_t)(pl.G + pl.P) * (size_t)pl.jgroup * pl.W, 256);
+  pl.dtab_bytes = pl.dttab_bytes = 0;
+  pl.work_bytes = pl.part_bytes + 256;  // + the error word
+  return BSRHT_OK;
+}
+
 // Fills the chunked-kernel fields of pl (common sizes already set) for
 // kernel instance inst of the dtype family.
 static void plan_chunked(SketchPlan& pl, int inst, bool query_device) {
@@ -137,7 +166,8 @@ static int default_instance(bool f64, int64_t r, int64_t l) {
   return r2t == 1024 ? 0 : r2t == 512 ? 1 : r2t == 256 ? 2 : r2t == 128 ? 3 : 4;
 }
 
-// choice: -2 = built-in rules, -1 = TMA-fed kernel, >= 0 = chunked instance.
+// choice: -3 = tensor-core kernel, -2 = built-in rules, -1 = TMA-fed kernel,
+// >= 0 = chunked instance.
 static int make_plan_choice(SketchPlan& pl, int dtype, int64_t n, int64_t m, int64_t lda, int p, int64_t l,
                             bool query_device, const void* A, int choice) {
   pl = SketchPlan();
@@ -159,6 +189,10 @@ static int make_plan_choice(SketchPlan& pl, int dtype, int64_t n, int64_t m, int
     pl.W = 32;
     pl.work_bytes = 0;
     return BSRHT_OK;
+  }
+  if (choice == -3) {
+    if (!tc_eligible(pl, A)) return BSRHT_EINVAL;
+    return make_plan_tc(pl, query_device);
   }
   int inst = default_instance(f64, pl.r, l);
   if (choice >= 0) {
@@ -191,9 +225,13 @@ int sketch_make_plan(SketchPlan& pl, int dtype, int variant, int64_t n, int64_t 
   if (n < 1 || m < 0 || p < 1 || (int64_t)p > n || l < 1 || l > n) return BSRHT_EINVAL;
   if (lda == 0) lda = m;
   if (lda < m) return BSRHT_EINVAL;
-  if (variant == BSRHT_VARIANT_TENSOR) return BSRHT_EUNSUP;
   int64_t rb = (n + p - 1) / p, r = 1;
   while (r < rb) r <<= 1;
+  if (variant == BSRHT_VARIANT_TENSOR) {
+    // K2 only: 16-bit A, r >= 512, TMA-compatible rows.
+    const int st = make_plan_choice(pl, dtype, n, m, lda, p, l, query_device, A, -3);
+    return st == BSRHT_OK && pl.path == 3 ? BSRHT_OK : BSRHT_EUNSUP;
+  }
   int choice = -2;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -206,9 +244,9 @@ int sketch_make_plan(SketchPlan& pl, int dtype, int variant, int64_t n, int64_t 
     // Scratch sized without A must also hold whatever plan the autotuner
     // records for this shape class before the run: reserve the largest.
     const bool f64 = dtype == BSRHT_F64;
-    for (int c = -1; c < n_instances(f64); ++c) {
+    for (int c = -3; c < n_instances(f64); ++c) {
       SketchPlan alt;
-      if (make_plan_choice(alt, dtype, n, m, lda, p, l, query_device, nullptr, c) == BSRHT_OK)
+      if (c != -2 && make_plan_choice(alt, dtype, n, m, lda, p, l, query_device, nullptr, c) == BSRHT_OK)
         pl.work_bytes = std::max(pl.work_bytes, alt.work_bytes);
     }
   }
@@ -223,6 +261,7 @@ int sketch_autotune(const void* A, int dtype, int64_t n, int64_t m, int64_t lda,
   if (lda < m) return BSRHT_EINVAL;
   const bool f64 = dtype == BSRHT_F64;
   std::vector<int> cands;
+  if (dtype == BSRHT_BF16 || dtype == BSRHT_F16) cands.push_back(-3);
   cands.push_back(-1);
   for (int i = 0; i < n_instances(f64); ++i) cands.push_back(i);
   cudaEvent_t e0, e1;
@@ -237,7 +276,7 @@ int sketch_autotune(const void* A, int dtype, int64_t n, int64_t m, int64_t lda,
   for (int c : cands) {
     SketchPlan pl;
     if (make_plan_choice(pl, dtype, n, m, lda, p, l, true, A, c) != BSRHT_OK) continue;
-    if (c == -1 && pl.path != 2) continue;
+    if ((c == -1 && pl.path != 2) || (c == -3 && pl.path != 3)) continue;
     if (pl.path == 1) {  // nothing to choose for tiny blocks
       best = -2;
       break;
@@ -276,9 +315,9 @@ int sketch_autotune(const void* A, int dtype, int64_t n, int64_t m, int64_t lda,
 size_t sketch_autotune_work_bytes(int dtype, int64_t n, int64_t m, int64_t lda, int p, int64_t l) {
   size_t w = 0;
   const bool f64 = dtype == BSRHT_F64;
-  for (int c = -1; c < n_instances(f64); ++c) {
+  for (int c = -3; c < n_instances(f64); ++c) {
     SketchPlan pl;
-    if (make_plan_choice(pl, dtype, n, m, lda == 0 ? m : lda, p, l, true, nullptr, c) == BSRHT_OK)
+    if (c != -2 && make_plan_choice(pl, dtype, n, m, lda == 0 ? m : lda, p, l, true, nullptr, c) == BSRHT_OK)
       w = std::max(w, pl.work_bytes);
   }
   return w;
@@ -318,7 +357,11 @@ int sketch_run(const SketchPlan& pl, const void* A, uint64_t seed, void* out, in
     a.ldo = ldo;
     a.scale = 1.0 / std::sqrt((double)pl.l);
     int st;
-    if (pl.path == 2) {
+    if (pl.path == 3) {
+      int* err = reinterpret_cast<int*>(static_cast<char*>(work) + pl.part_bytes);
+      if (j0 == 0) BSRHT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), stream));
+      st = sketch_launch_tc(pl, a, out, ldo, err, stream);
+    } else if (pl.path == 2) {
       char* w = static_cast<char*>(work);
       int* err = reinterpret_cast<int*>(w + pl.part_bytes);
       uint64_t* dtab = reinterpret_cast<uint64_t*>(w + pl.part_bytes + 256);
