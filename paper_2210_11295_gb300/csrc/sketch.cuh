@@ -25,6 +25,7 @@ struct SketchPlan {
   int64_t P = 0;      // column panels
   int64_t T = 0;      // tiles = P * C
   int G = 0;          // CTAs of the chunked kernel (persistent, one wave)
+  int paired = 0;     // TMA-fed paths: CTA pairs share panel pairs (16-bit inputs)
   int64_t jgroup = 0; // sketch rows handled per launch
   size_t smem = 0;    // dynamic shared memory per CTA
   size_t part_bytes = 0;  // partial-sum scratch (path 2 then: status word, D and Dt sign tables)

@@ -41,7 +41,68 @@ struct SketchArgs {
   void* out;       // grouped reduce only: output, leading dimension, scale
   int64_t ldo;
   double scale;
+  // TMA-fed kernels: with `paired` set (16-bit inputs, 64-byte panel rows)
+  // CTAs 2q and 2q + 1 walk the same (panel pair, block, chunk) units on the
+  // two panels of each pair (see TileSched).  P = number of column panels.
+  int paired;
+  int64_t P;
 };
+
+// Tile schedule of the TMA-fed kernels.  Plain: CTA c takes tiles
+// [c T / G, (c + 1) T / G) of the panel-major order (panel, block, chunk)
+// and writes partial slot c + panel.  Paired: units are (panel pair, block,
+// chunk), U = ceil(P / 2) C of them; CTA pair q = c / 2 takes units
+// [q U / Gp, (q + 1) U / Gp) (Gp = G / 2) on panel 2 pp + (c & 1), so the two
+// 64-byte halves of each 128-byte line are fetched at about the same time
+// and one of the two reads hits L2 instead of DRAM; slot = half (Gp + Pp) +
+// q + pp.  (An odd P gives the last pair's second CTA a panel past the end:
+// its loads read zeros and its slots are never reduced.)
+struct TileSched {
+  int64_t begin, end;  // unit range of this CTA
+  int half, step;      // panel = step * (unit / C) + half
+  int64_t slot0;       // slot of panel pc: slot0 + pc / step
+  __device__ __forceinline__ void init(const SketchArgs& g, int cta) {
+    if (!g.paired) {
+      begin = (int64_t)cta * g.T / g.G;
+      end = (int64_t)(cta + 1) * g.T / g.G;
+      half = 0;
+      step = 1;
+      slot0 = cta;
+    } else {
+      const int64_t gp = g.G / 2, pp = (g.P + 1) / 2, u = pp * g.C, q = cta >> 1;
+      half = cta & 1;
+      step = 2;
+      begin = q < gp ? q * u / gp : 0;
+      end = q < gp ? (q + 1) * u / gp : 0;
+      slot0 = half * (gp + pp) + q;
+    }
+  }
+  __device__ __forceinline__ int64_t slot(int64_t pc) const { return slot0 + pc / step; }
+};
+
+// Partial-slot range of panel pc for the reduce: calls f(slot) for every CTA
+// whose units touch the panel, in CTA order.
+template <typename F>
+__device__ __forceinline__ void for_panel_slots(const SketchArgs& g, int64_t pc, F&& f) {
+  int64_t lo, hi, G, U, base;
+  if (!g.paired) {
+    lo = pc * g.C;
+    G = g.G;
+    U = g.T;
+    base = pc;
+  } else {
+    const int64_t pp = (g.P + 1) / 2;
+    lo = (pc >> 1) * g.C;
+    G = g.G / 2;
+    U = pp * g.C;
+    base = (pc & 1) * (G + pp) + (pc >> 1);
+  }
+  hi = lo + g.C;
+  int64_t c = lo * G / U;
+  if (c > 0) --c;
+  while (c < G && (c + 1) * U / G <= lo) ++c;
+  for (; c < G && c * U / G < hi; ++c) f(base + c);
+}
 
 struct SketchGroup {
   int nreq;
@@ -255,7 +316,8 @@ __global__ void k_sketch_reduce_grouped(const __grid_constant__ SketchGroup grp)
   }
 }
 
-// Fixed-order reduce; NaN output if any CTA reported a failed wait.
+// Fixed-order reduce of the TMA-fed kernels' partials; NaN output if any CTA
+// reported a failed wait.
 template <int W>
 __global__ void k_sketch_reduce_checked(SketchArgs g, float* __restrict__ out, int64_t ldo, float scale,
                                         const int* __restrict__ err) {
@@ -270,13 +332,9 @@ __global__ void k_sketch_reduce_checked(SketchArgs g, float* __restrict__ out, i
   }
   const int64_t pc = col / W;
   const int cw = (int)(col - pc * W);
-  const int64_t lo = pc * g.C, hi = lo + g.C;
-  int64_t cta = lo * g.G / g.T;
-  if (cta > 0) --cta;
-  while (cta < g.G && (cta + 1) * g.T / g.G <= lo) ++cta;
   const float* part = static_cast<const float*>(g.part);
   float s = 0.f;
-  for (; cta < g.G && cta * g.T / g.G < hi; ++cta) s += part[((cta + pc) * g.jn + jl) * W + cw];
+  for_panel_slots(g, pc, [&](int64_t slot) { s += part[(slot * g.jn + jl) * W + cw]; });
   out[(g.j0 + jl) * ldo + col] = s * scale;
 }
 

@@ -43,6 +43,18 @@ static bool tma_layout_ok(int dtype, const void* A, int64_t lda) {
   return A == nullptr || (reinterpret_cast<uintptr_t>(A) % 16) == 0;
 }
 
+// 16-bit panels are 64-byte rows: pair the panels (TileSched) when there are
+// at least two CTAs and two panels; sizes the partial-sum scratch.
+static void set_pairing(SketchPlan& pl) {
+  pl.paired = (pl.dtype == BSRHT_BF16 || pl.dtype == BSRHT_F16) && pl.G >= 2 && pl.P >= 2 ? 1 : 0;
+  size_t slots = (size_t)(pl.G + pl.P);
+  if (pl.paired) {
+    pl.G &= ~1;
+    slots = 2 * (size_t)(pl.G / 2 + (pl.P + 1) / 2);
+  }
+  pl.part_bytes = align_up(4 * slots * (size_t)pl.jgroup * pl.W, 256);
+}
+
 static int make_plan_tma(SketchPlan& pl, bool query_device) {
   pl.path = 2;
   pl.W = 32;
@@ -59,7 +71,7 @@ static int make_plan_tma(SketchPlan& pl, bool query_device) {
   if (occ <= 0) occ = 1;
   int64_t g = (int64_t)num_sms() * occ;
   pl.G = (int)std::max<int64_t>(1, std::min<int64_t>(g, std::max<int64_t>(pl.T, 1)));
-  pl.part_bytes = align_up(4 * (size_t)(pl.G + pl.P) * (size_t)pl.jgroup * pl.W, 256);
+  set_pairing(pl);
   pl.dtab_bytes = align_up(4 * (size_t)pl.p * (size_t)pl.nch * 16, 256);
   pl.dttab_bytes = align_up(8 * (size_t)pl.p * (size_t)((pl.jgroup + 63) / 64), 256);
   pl.work_bytes = pl.part_bytes + 256 + pl.dtab_bytes + pl.dttab_bytes;
@@ -89,7 +101,7 @@ static int make_plan_tc(SketchPlan& pl, bool query_device) {
   if (occ <= 0) occ = 1;
   const int64_t g = (int64_t)num_sms() * occ;
   pl.G = (int)std::max<int64_t>(1, std::min<int64_t>(g, std::max<int64_t>(pl.T, 1)));
-  pl.part_bytes = align_up(4 * (size_t)(pl.G + pl.P) * (size_t)pl.jgroup * pl.W, 256);
+  set_pairing(pl);
   pl.dtab_bytes = pl.dttab_bytes = 0;
   pl.work_bytes = pl.part_bytes + 256;  // + the error word
   return BSRHT_OK;
@@ -356,6 +368,8 @@ int sketch_run(const SketchPlan& pl, const void* A, uint64_t seed, void* out, in
     a.out = out;
     a.ldo = ldo;
     a.scale = 1.0 / std::sqrt((double)pl.l);
+    a.paired = (pl.path == 2 || pl.path == 3) ? pl.paired : 0;
+    a.P = pl.P;
     int st;
     if (pl.path == 3) {
       int* err = reinterpret_cast<int*>(static_cast<char*>(work) + pl.part_bytes);
@@ -450,6 +464,8 @@ int sketch_group_run(const SketchPlan* const* plans, const void* const* A, const
     a.out = outs[q];
     a.ldo = pl.m;
     a.scale = 1.0 / std::sqrt((double)pl.l);
+    a.paired = 0;
+    a.P = pl.P;
     toff += pl.T;
   }
   int64_t maxel = 0;

@@ -4,18 +4,19 @@
 // Kronecker factor collapsed to a sign per sampled row), with the chunk
 // transform split by the tensor form of H (Sec. 2):
 //     H_512 = H_4 (x) H_128,   H_128 = H_8 (x) H_16,
-// and H_128 applied on the tensor cores as one dense +-1 operand: per
-// 128-row block of the chunk, D = H_128 X_blk (M = 128, N = 32 columns,
-// K = 128) with tcgen05.mma kind::f16.  +-1 and the 16-bit inputs are exact
+// and H_128 applied on the tensor cores as one dense +-1 operand: the four
+// 128-row blocks of a chunk sit side by side as the columns of one product,
+// D = H_128 [X_0 X_1 X_2 X_3] (M = 128, N = 4 x 32, K = 128), with
+// tcgen05.mma kind::f16.  +-1 and the 16-bit inputs are exact
 // in the operand type and the products accumulate in FP32 in TMEM, so the
 // result is the FP32 transform of the stored values.  The remaining H_4
 // across the four blocks, the sampled rows and their signs run on the CUDA
 // cores as in K1.
 //
-// Per chunk (32 columns of one panel): a TMA load into a 2-stage ring; all
-// threads apply the D^(i) signs while transposing the chunk into the
-// K-major, 128-byte-swizzled B operand; one thread issues 32 MMAs (4 blocks
-// x 8 K-steps of 16) into a double-buffered TMEM accumulator; the previous
+// Per chunk (32 columns of one panel): a TMA load (64-byte swizzle) into a
+// 2-stage ring; all threads apply the D^(i) signs while transposing the
+// chunk (ldmatrix.trans) into the K-major, 128-byte-swizzled B operand; one thread issues 8 MMAs (K-steps of
+// 16) into a double-buffered TMEM accumulator; the previous
 // chunk's accumulator is read back (tcgen05.ld), combined by the radix-4
 // stage into an FP32 tile and gathered into per-thread accumulators while
 // the tensor cores work on the current one.  Waits are bounded; on a failed
@@ -38,7 +39,7 @@ constexpr uint32_t kTcWait = 1u << 22;
 constexpr int kW = 32, kNT = 512, kR2 = 512, kNRL = 16;
 constexpr int kTStride = 36;                       // FP32 tile row stride (floats): conflict-free float4 stores
 constexpr uint32_t kHBytes = 2 * 128 * 128;        // H_128, 16-bit, K-major SW128 (2 K-blocks of 64)
-constexpr uint32_t kBtBytes = 8 * kW * 128;        // chunk^T: 8 K-blocks x 32 rows x 128 B
+constexpr uint32_t kBtBytes = 2 * 128 * 128;       // chunk^T: 2 K-blocks x 128 rows (block, column) x 128 B
 constexpr uint32_t kXBytes = kR2 * kW * 2;         // one staged chunk (row-major, 64-byte rows)
 constexpr uint32_t kTBytes = kR2 * kTStride * 4;   // FP32 transform of the chunk
 constexpr uint32_t kTmemCols = 256;                // 2 buffers x 4 blocks x 32 columns
@@ -54,9 +55,10 @@ struct TcShape {
 
 template <typename Tin>
 constexpr uint32_t idesc_16() {
-  // D FP32, A = B = F16 (0) or BF16 (1), both K-major, N = 32, M = 128.
-  constexpr uint32_t f = sizeof(Tin) == 2 && std::is_same<Tin, __nv_bfloat16>::value ? 1u : 0u;
-  return (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(kW >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  // D FP32, A = B = F16 (0) or BF16 (1), both K-major, N = 128 (the four
+  // 128-row blocks' 32 columns side by side), M = 128.
+  constexpr uint32_t f = std::is_same<Tin, __nv_bfloat16>::value ? 1u : 0u;
+  return (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -68,17 +70,8 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
       : "memory");
 }
 
-// 4 consecutive FP32 columns of this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
-  uint32_t r[4];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(taddr)
-               : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
-}
+// Waits for this thread's outstanding tcgen05.ld.
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Byte offset of element (row n, k) in a K-major operand of 128-byte rows
 // (64 16-bit values) with the 128-byte swizzle; K-blocks of 64 are
@@ -111,27 +104,29 @@ __global__ void __launch_bounds__(kNT, 1)
   const int cg = tid % kW;
   const int rl = tid / kW;  // == warp
   const int jn = (int)g.jn;
-  const int64_t t_begin = (int64_t)blockIdx.x * g.T / g.G;
-  const int64_t t_end = (int64_t)(blockIdx.x + 1) * g.T / g.G;
-  const int64_t ntiles = t_end - t_begin;
+  TileSched sched;
+  sched.init(g, (int)blockIdx.x);
+  const int64_t t_begin = sched.begin;
+  const int64_t ntiles = sched.end - sched.begin;
 
+  const int pstep = sched.step;
   struct TileIt {  // 32-bit fields: panels, blocks and chunks all fit
     int pc, i, a;
-    __device__ void next(int64_t nch, int p) {
+    __device__ void next(int64_t nch, int p, int step) {
       if (++a == nch) {
         a = 0;
         if (++i == p) {
           i = 0;
-          ++pc;
+          pc += step;
         }
       }
     }
   };
-  auto tile_at = [&](int64_t t) {
+  auto tile_at = [&](int64_t t) {  // unit t of the schedule
     TileIt it;
-    const int64_t pc = t / g.C;
-    const int64_t c = t - pc * g.C;
-    it.pc = (int)pc;
+    const int64_t u = t / g.C;
+    const int64_t c = t - u * g.C;
+    it.pc = (int)(u * pstep + sched.half);
     it.i = (int)(c / g.nch);
     it.a = (int)(c - (int64_t)it.i * g.nch);
     return it;
@@ -174,7 +169,7 @@ __global__ void __launch_bounds__(kNT, 1)
     const int64_t y0 = (int64_t)iss.i * g.rb + (int64_t)iss.a * kR2;
     tma_load_2d(dst, &tmap, &full[s], x, (int32_t)y0);
     tma_load_2d(dst + kXBytes / 2, &tmap, &full[s], x, (int32_t)(y0 + 256));
-    iss.next(g.nch, g.p);
+    iss.next(g.nch, g.p, pstep);
     ++issued;
   };
   auto d_words = [&](int buf, const TileIt& t) {  // threads 0..7
@@ -203,7 +198,7 @@ __global__ void __launch_bounds__(kNT, 1)
   int64_t cur_pc = -1;
   float* part = static_cast<float*>(g.part);
   auto flush = [&](int64_t pc) {
-    float* dst = part + ((int64_t)blockIdx.x + pc) * (int64_t)jn * kW + cg;
+    float* dst = part + sched.slot(pc) * (int64_t)jn * kW + cg;
 #pragma unroll
     for (int u = 0; u < JM; ++u) {
       const int jl = rl + kNRL * u;
@@ -215,28 +210,49 @@ __global__ void __launch_bounds__(kNT, 1)
   // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (H_128 output rows b) and
   // columns 8 (w / 4) .. + 7 of each of the four 128-row blocks.
   const int quarter = rl & 3, cgrp = rl >> 2;
+  // Columns per pass: fewer live registers beside 64 accumulators.
+  constexpr int EC = JM == 64 ? 2 : 4;
   auto epilogue = [&](int buf) {
     const int b = 32 * quarter + (tid & 31);
+    const uint32_t tbase = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * 128 + cgrp * 8);
+    float* trow = T + (size_t)b * kTStride + cgrp * 8;
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {  // 4 columns at a time keeps registers low
-      float v[4][4];
+    for (int pass = 0; pass < 8 / EC; ++pass) {
+      uint32_t r[4][EC];
 #pragma unroll
-      for (int blk = 0; blk < 4; ++blk)
-        tmem_ld4(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * 128 + blk * 32 + cgrp * 8 + half * 4),
-                 v[blk]);
+      for (int blk = 0; blk < 4; ++blk) {
+        const uint32_t ta = tbase + (uint32_t)(blk * 32 + pass * EC);
+        if constexpr (EC == 4) {
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(r[blk][0]), "=r"(r[blk][1]), "=r"(r[blk][2]), "=r"(r[blk][3])
+                       : "r"(ta)
+                       : "memory");
+        } else {
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                       : "=r"(r[blk][0]), "=r"(r[blk][1])
+                       : "r"(ta)
+                       : "memory");
+        }
+      }
+      tmem_wait_ld();
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float x0 = v[0][c], x1 = v[1][c], x2 = v[2][c], x3 = v[3][c];
+      for (int c = 0; c < EC; ++c) {
+        const float x0 = __uint_as_float(r[0][c]), x1 = __uint_as_float(r[1][c]);
+        const float x2 = __uint_as_float(r[2][c]), x3 = __uint_as_float(r[3][c]);
         const float s01 = x0 + x1, d01 = x0 - x1, s23 = x2 + x3, d23 = x2 - x3;
-        v[0][c] = s01 + s23;
-        v[1][c] = d01 + d23;
-        v[2][c] = s01 - s23;
-        v[3][c] = d01 - d23;
+        r[0][c] = __float_as_uint(s01 + s23);
+        r[1][c] = __float_as_uint(d01 + d23);
+        r[2][c] = __float_as_uint(s01 - s23);
+        r[3][c] = __float_as_uint(d01 - d23);
       }
 #pragma unroll
-      for (int blk = 0; blk < 4; ++blk)
-        *reinterpret_cast<float4*>(T + (size_t)(blk * 128 + b) * kTStride + cgrp * 8 + half * 4) =
-            make_float4(v[blk][0], v[blk][1], v[blk][2], v[blk][3]);
+      for (int blk = 0; blk < 4; ++blk) {
+        float* dst = trow + (size_t)blk * 128 * kTStride + pass * EC;
+        if constexpr (EC == 4)
+          *reinterpret_cast<uint4*>(dst) = make_uint4(r[blk][0], r[blk][1], r[blk][2], r[blk][3]);
+        else
+          *reinterpret_cast<uint2*>(dst) = make_uint2(r[blk][0], r[blk][1]);
+      }
     }
   };
   // Gather of chunk tile `t` (block i, chunk a) from T.
@@ -272,9 +288,8 @@ __global__ void __launch_bounds__(kNT, 1)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int u = 4 * u4 + q;
-        const float tv = tcol[oo[q]];
-        const uint32_t sb = (gmask[u >> 5] << (31 - (u & 31))) & 0x80000000u;
-        acc[u] += __int_as_float(__float_as_int(tv) ^ (int)sb);
+        const uint32_t tv = __float_as_uint(tcol[oo[q]]);
+        acc[u] += __uint_as_float(tv ^ ((gmask[u >> 5] << (31 - (u & 31))) & 0x80000000u));
       }
     }
   };
@@ -282,93 +297,106 @@ __global__ void __launch_bounds__(kNT, 1)
   TileIt cur = tile_at(t_begin), prev = cur;
   uint32_t mma_issued = 0;  // MMA batches committed (thread 0)
   bool failed = false;
-  for (int64_t k = 0; k < ntiles; ++k) {
+  // Only thread 0 waits on the mbarriers (chunk k + 1 landed, MMA k done);
+  // the CTA barrier that follows releases the others, so 511 threads do not
+  // poll.  Its result rides on __syncthreads_or.
+  {
+    const bool ok0 = tid != 0 || ntiles == 0 || mbar_wait_bounded(&full[0], 0u, kTcWait);
+    if (__syncthreads_or(!ok0)) failed = true;
+  }
+  for (int64_t k = 0; k < ntiles && !failed; ++k) {
     const int s = (int)(k & 1);
     const int64_t rows_i = min(g.rb, g.n - (int64_t)cur.i * g.rb);
     const int nvalid = (int)min((int64_t)kR2, rows_i - (int64_t)cur.a * kR2);
-    bool ok = mbar_wait_bounded(&full[s], (uint32_t)((k >> 1) & 1), kTcWait);
-    if (k >= 1) ok = ok && mbar_wait_bounded(&mmad[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), kTcWait);
-    // D^(i) signs and transpose into the K-major B operand: item = (4
-    // columns, 8 consecutive rows); lanes 8-15 / 24-31 walk their rows in a
-    // rotated order so a half-warp's two rows sit in different bank halves.
+    const bool ok = true;  // chunk k landed and MMA k - 1 finished (checked by thread 0 below)
+    // D^(i) signs and transpose into the K-major B operand with
+    // ldmatrix.trans: warp w takes 8-row groups q = 4w .. 4w + 3; one x4 load
+    // covers the group's four 8 x 8 tiles (columns 8i .. 8i + 7), and lane t
+    // then holds rows 8q + 2(t % 4), +1 of column 8i + t / 4 as one 32-bit
+    // word, which is that column's K-pair in the operand.
     if (ok) {
-      const unsigned char* X = Xs + (size_t)s * kXBytes;
+      const uint32_t X = smem_u32(Xs + (size_t)s * kXBytes);
       const uint64_t* dw = s_d + s * 8;
-      const int q4 = tid & 7;                  // columns 4 q4 .. 4 q4 + 3
-      const int g8 = (tid >> 3);               // rows 8 g8 .. 8 g8 + 7 (64 groups)
-      const int rot = (tid >> 3) & 1;
+      const int lane = tid & 31;
+      const uint32_t kp = (uint32_t)(2 * (lane & 3));  // row pair within the 8-row group
+      // Operand address of (column n0 = block * 32 + lane / 4, K-pair kp): the
+      // four tiles' columns n0 + 8i share the swizzle phase (n & 7), so they
+      // are 8 rows = 1024 bytes apart.
+      unsigned char* bt_lane = Bt + (size_t)(((rl >> 2) * kW + (lane >> 2)) * 128 + 2 * kp);
+      const bool full_chunk = nvalid >= kR2;
 #pragma unroll
-      for (int pair = 0; pair < 2; ++pair) {  // columns (4 q4, 4 q4 + 1), then (4 q4 + 2, 4 q4 + 3)
-        uint32_t w[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int jj = (j + rot) & 7;
-          const int row = 8 * g8 + jj;
-          uint32_t x = 0u;
-          if (row < nvalid) x = *reinterpret_cast<const uint32_t*>(X + (size_t)row * (kW * 2) + q4 * 8 + pair * 4);
-          w[jj] = x ^ (((dw[row >> 6] >> (row & 63)) & 1ull) ? 0x80008000u : 0u);
+      for (int gq = 0; gq < 4; ++gq) {
+        const int q = 4 * rl + gq;  // 8-row group 0..63
+        uint32_t r0, r1, r2, r3;
+        // The chunk is staged with the 64-byte swizzle: 16-byte unit u of row r
+        // sits at unit u ^ ((r >> 1) & 3), so the 8 rows of a tile hit 8 banks.
+        const int r8 = 8 * q + (lane & 7);
+        const uint32_t addr = X + (uint32_t)(r8 * (kW * 2) + (((lane >> 3) ^ ((r8 >> 1) & 3)) << 4));
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                     : "r"(addr)
+                     : "memory");
+        const uint32_t db = (uint32_t)(dw[q >> 3] >> ((q & 7) * 8 + kp));  // bit 0: row kp, bit 1: row kp + 1
+        uint32_t flip = ((db & 1u) << 15) | ((db & 2u) << 30);
+        if (!full_chunk) {  // rows past the block's end read as zero
+          const int row = 8 * q + (int)kp;
+          const uint32_t keep = row >= nvalid ? 0u : (row + 1 >= nvalid ? 0x0000FFFFu : 0xFFFFFFFFu);
+          r0 &= keep;
+          r1 &= keep;
+          r2 &= keep;
+          r3 &= keep;
+          flip &= keep;
         }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t sel = h ? 0x7632u : 0x5410u;  // high or low halves of two words
-          uint4 o;
-          o.x = __byte_perm(w[0], w[1], sel);
-          o.y = __byte_perm(w[2], w[3], sel);
-          o.z = __byte_perm(w[4], w[5], sel);
-          o.w = __byte_perm(w[6], w[7], sel);
-          const uint32_t n = (uint32_t)(4 * q4 + 2 * pair + h);
-          *reinterpret_cast<uint4*>(Bt + sw128_off(n, (uint32_t)(8 * g8), kW)) = o;
-        }
+        uint32_t* dst = reinterpret_cast<uint32_t*>(bt_lane + ((q >> 3) & 1) * 16384 +
+                                                    ((((uint32_t)q & 7u) ^ (uint32_t)(lane >> 2)) << 4));
+        dst[0] = r0 ^ flip;
+        dst[256] = r1 ^ flip;  // + 1024 bytes: column + 8
+        dst[512] = r2 ^ flip;
+        dst[768] = r3 ^ flip;
       }
     }
     fence_proxy_async_smem();
     tc::tc_fence_before();
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
+    __syncthreads();
     tc::tc_fence_after();
     if (tid == 0) {
-      // MMAs of chunk k into accumulator buffer s: 4 blocks x 8 K-steps.
+      // MMAs of chunk k into accumulator buffer s: 8 K-steps of 16, all four
+      // blocks at once (N = 128).
       const uint32_t hb = smem_u32(Hs), bb = smem_u32(Bt);
+      const uint32_t d = tmem + (uint32_t)(s * 128);
 #pragma unroll
-      for (int blk = 0; blk < 4; ++blk) {
-        const uint32_t d = tmem + (uint32_t)(s * 128 + blk * 32);
-#pragma unroll
-        for (int ks = 0; ks < 8; ++ks) {
-          const uint32_t koff = (uint32_t)(ks & 3) * 32u;
-          const uint64_t ad = tc::desc_sw128(hb + (uint32_t)(ks >> 2) * (128u * 128u) + koff);
-          const uint64_t bd = tc::desc_sw128(bb + (uint32_t)(2 * blk + (ks >> 2)) * (kW * 128u) + koff);
-          mma_f16(d, ad, bd, idesc, ks > 0 ? 1u : 0u);
-        }
+      for (int ks = 0; ks < 8; ++ks) {
+        const uint32_t koff = (uint32_t)(ks & 3) * 32u + (uint32_t)(ks >> 2) * (128u * 128u);
+        mma_f16(d, tc::desc_sw128(hb + koff), tc::desc_sw128(bb + koff), idesc, ks > 0 ? 1u : 0u);
       }
       tc::mma_commit(&mmad[s]);
       ++mma_issued;
       if (issued < ntiles) issue_next();  // stage s was consumed by the transpose above
     }
     TileIt nx = cur;
-    nx.next(g.nch, g.p);
+    nx.next(g.nch, g.p, pstep);
     if (k + 1 < ntiles) d_words((int)((k + 1) & 1), nx);
     if (k >= 1) epilogue((int)((k - 1) & 1));
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     if (k >= 1) gather(prev);
+    bool ok0 = true;
+    if (tid == 0) {
+      if (k + 1 < ntiles) ok0 = mbar_wait_bounded(&full[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1), kTcWait);
+      ok0 = ok0 && mbar_wait_bounded(&mmad[s], (uint32_t)((k >> 1) & 1), kTcWait);
+    }
+    tc::tc_fence_before();
+    if (__syncthreads_or(!ok0)) failed = true;
+    tc::tc_fence_after();
     prev = cur;
     cur = nx;
   }
-  if (!failed && ntiles > 0) {
-    const int64_t k = ntiles - 1;
-    const bool ok = mbar_wait_bounded(&mmad[k & 1], (uint32_t)((k >> 1) & 1), kTcWait);
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-    } else {
-      tc::tc_fence_after();
-      epilogue((int)(k & 1));
-      tc::tc_fence_before();
-      __syncthreads();
-      gather(prev);
-    }
+  if (!failed && ntiles > 0) {  // MMA of the last chunk: waited at the end of the loop
+    epilogue((int)((ntiles - 1) & 1));
+    tc::tc_fence_before();
+    __syncthreads();
+    gather(prev);
   }
   if (failed) {
     if (tid == 0) {
@@ -398,7 +426,8 @@ int launch_tc(const SketchPlan& plan, const SketchArgs& a, int* err, void* out, 
   CUtensorMap map;
   const CUtensorMapDataType dt =
       std::is_same<Tin, __nv_bfloat16>::value ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  if (!make_tensor_map_2d(&map, a.A, dt, 2, (uint64_t)a.n, (uint64_t)a.m, (uint64_t)a.lda, kW, 256))
+  if (!make_tensor_map_2d(&map, a.A, dt, 2, (uint64_t)a.n, (uint64_t)a.m, (uint64_t)a.lda, kW, 256,
+                          CU_TENSOR_MAP_SWIZZLE_64B))
     return BSRHT_EUNSUP;
   BSRHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<plan.G, kNT, smem, stream>>>(map, a, err);

@@ -104,30 +104,34 @@ __global__ void __launch_bounds__(NT, 1)
   const int cg = tid % W;  // == lane
   const int rl = tid / W;  // == warp
   const int jn = (int)g.jn;
-  const int64_t t_begin = (int64_t)blockIdx.x * g.T / g.G;
-  const int64_t t_end = (int64_t)(blockIdx.x + 1) * g.T / g.G;
-  const int64_t ntiles = t_end - t_begin;
+  TileSched sched;
+  sched.init(g, (int)blockIdx.x);
+  const int64_t t_begin = sched.begin;
+  const int64_t ntiles = sched.end - sched.begin;
 
   // Tile t = (panel pc, block i, chunk a) in panel-major order; iterators
   // advance without divisions.
   struct TileIt {
     int64_t pc, i, a;
+    int step;
     __device__ void next(int64_t nch, int p) {
       if (++a == nch) {
         a = 0;
         if (++i == p) {
           i = 0;
-          ++pc;
+          pc += step;
         }
       }
     }
   };
-  auto tile_at = [&](int64_t t) {
+  auto tile_at = [&](int64_t t) {  // unit t of the schedule
     TileIt it;
-    it.pc = t / g.C;
-    const int64_t c = t - it.pc * g.C;
+    const int64_t u = t / g.C;
+    const int64_t c = t - u * g.C;
+    it.pc = u * sched.step + sched.half;
     it.i = c / g.nch;
     it.a = c - it.i * g.nch;
+    it.step = sched.step;
     return it;
   };
   TileIt iss = tile_at(t_begin);  // next tile to issue (thread 0 only)
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(NT, 1)
   int64_t cur_pc = -1;
   float* part = static_cast<float*>(g.part);
   auto flush = [&](int64_t pc) {
-    float* dst = part + ((int64_t)blockIdx.x + pc) * (int64_t)jn * W + cg;
+    float* dst = part + sched.slot(pc) * (int64_t)jn * W + cg;
 #pragma unroll
     for (int u = 0; u < JM; ++u) {
       const int jl = rl + NRL * u;
