@@ -5,7 +5,10 @@
 // chunk of a W-column panel, D^(i) signs, the R2-point Walsh-Hadamard
 // transform (tensor form of H, Sec. 2) and the sampled rows with the outer
 // Kronecker-factor and Dt^(i) signs, accumulated over the chunks a CTA owns
-// (eq. 2.4 block sum), partials reduced in a fixed order.  Here one thread
+// (eq. 2.4 block sum), partials reduced in a fixed order.  The register
+// phase (high five row bits) gives each thread one column of 32 rows; the
+// exchange phase (low four bits) and the gather give it two adjacent columns
+// and use 64-bit shared-memory accesses.  Here one thread
 // streams the chunks with cp.async.bulk.tensor into a STAGES-deep ring
 // guarded by mbarriers, so HBM reads of later chunks overlap the butterflies
 // and the gather of the current one.  FP32 inputs are transformed in place
@@ -35,10 +38,8 @@ template <typename Tin, int W, int NT, int R2, int JM, int STAGES>
 struct TmaShape {
   static constexpr int NRL = NT / W;
   static constexpr int E = R2 / NRL;
-  static constexpr int Q = E / NRL;
   static constexpr int LOG_R2 = ilog2c(R2);
   static constexpr int JG = JM * NRL;
-  static constexpr int DW = R2 / 64;
   static constexpr bool kInPlace = sizeof(Tin) == 4;
   static constexpr int BOXR = R2 < 256 ? R2 : 256;
   static constexpr size_t stage_bytes = sizeof(Tin) * (size_t)R2 * W;
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(NT, 1)
     k_sketch_tma(const __grid_constant__ CUtensorMap tmap, SketchArgs g, const uint32_t* __restrict__ dmtab,
                  const uint64_t* __restrict__ dttab, int64_t tw, int* __restrict__ err) {
   using S = TmaShape<Tin, W, NT, R2, JM, STAGES>;
-  constexpr int NRL = S::NRL, E = S::E, Q = S::Q, JG = S::JG, BOXR = S::BOXR;
+  constexpr int NRL = S::NRL, E = S::E, JG = S::JG, BOXR = S::BOXR;
   static_assert(W == 32 && NRL == 16 && E == 32 && R2 == 512, "sign masks assume 16 row lanes x 32 rows");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128 - (reinterpret_cast<uintptr_t>(smem_raw) & 127)) & 127);
@@ -160,37 +161,41 @@ __global__ void __launch_bounds__(NT, 1)
       off = (uint32_t)(sv & (R2 - 1)) * W;
       hi = (uint32_t)(sv >> S::LOG_R2);
     }
-    s_off[(jl % NRL) * JM + jl / NRL] = off;  // [row lane][u]: jl = rl + NRL * u
+    s_off[(jl % 32) * (JM / 2) + jl / 32] = off;  // [row lane rg][u]: jl = rg + 32 u
     s_hi[jl] = hi;
   }
   __syncthreads();
   if (tid == 0)
     for (int64_t k = 0; k < STAGES && k < ntiles; ++k) issue_next();
 
-  // Lane cg of row lane rl evaluates the outer-factor sign of sketch row
-  // jl = rl + NRL * (32 h + cg); its s_hi never changes, its Dt^(i) word only
-  // with the block.
-  uint32_t my_hi[JM / 32];
-  uint64_t my_dt[JM / 32];
+  // Exchange phase and gather: thread = (row lane rg = tid / 16, column
+  // pair cp = tid % 16); sketch rows jl = rg + 32 u, u < JM / 2, two columns
+  // each.  The 16 lanes of a row lane share its sketch rows: lane cp
+  // evaluates the outer-factor x Dt^(i) sign of u = 16 h + cp and a warp
+  // ballot hands each lane its row lane's 16 bits.  s_hi never changes; the
+  // Dt word only with the block.
+  constexpr int JU = JM / 2, NH = JU / 16;
+  const int cp = tid & 15, rg = tid >> 4;
+  uint32_t my_hi[NH];
+  uint64_t my_dt[NH];
   int64_t dt_block = -1;
 #pragma unroll
-  for (int h = 0; h < JM / 32; ++h) {
-    const int jl = rl + NRL * (32 * h + cg);
-    my_hi[h] = s_hi[jl];
+  for (int h = 0; h < NH; ++h) {
+    my_hi[h] = s_hi[rg + 32 * (16 * h + cp)];
     my_dt[h] = 0;
   }
 
-  float acc[JM];
+  float acc[JU][2];
 #pragma unroll
-  for (int u = 0; u < JM; ++u) acc[u] = 0.f;
+  for (int u = 0; u < JU; ++u) acc[u][0] = acc[u][1] = 0.f;
   int64_t cur_pc = -1;
   float* part = static_cast<float*>(g.part);
   auto flush = [&](int64_t pc) {
-    float* dst = part + sched.slot(pc) * (int64_t)jn * W + cg;
+    float* dst = part + sched.slot(pc) * (int64_t)jn * W + 2 * cp;
 #pragma unroll
-    for (int u = 0; u < JM; ++u) {
-      const int jl = rl + NRL * u;
-      if (jl < jn) dst[(int64_t)jl * W] = acc[u];
+    for (int u = 0; u < JU; ++u) {
+      const int jl = rg + 32 * u;
+      if (jl < jn) *reinterpret_cast<float2*>(dst + (int64_t)jl * W) = make_float2(acc[u][0], acc[u][1]);
     }
   };
 
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(NT, 1)
     if (pc != cur_pc) {
       if (cur_pc >= 0) flush(cur_pc);
 #pragma unroll
-      for (int u = 0; u < JM; ++u) acc[u] = 0.f;
+      for (int u = 0; u < JU; ++u) acc[u][0] = acc[u][1] = 0.f;
       cur_pc = pc;
     }
     const int64_t rows_i = min(g.rb, g.n - i * g.rb);
@@ -219,18 +224,18 @@ __global__ void __launch_bounds__(NT, 1)
     }
     if (i != dt_block) {
 #pragma unroll
-      for (int h = 0; h < JM / 32; ++h) {
-        const int jl = rl + NRL * (32 * h + cg);
+      for (int h = 0; h < NH; ++h) {
+        const int jl = rg + 32 * (16 * h + cp);
         my_dt[h] = jl < jn ? __ldg(dttab + i * tw + (jl >> 6)) : 0ull;
       }
       dt_block = i;
     }
-    uint32_t gmask[JM / 32];
+    uint32_t gmask[NH];
 #pragma unroll
-    for (int h = 0; h < JM / 32; ++h) {
-      const int jl = rl + NRL * (32 * h + cg);
+    for (int h = 0; h < NH; ++h) {
+      const int jl = rg + 32 * (16 * h + cp);
       const uint32_t sg = (uint32_t)((__popc(my_hi[h] & (uint32_t)a) + (int)((my_dt[h] >> (jl & 63)) & 1ull)) & 1);
-      gmask[h] = __ballot_sync(0xffffffffu, jl < jn ? sg : 0u);
+      gmask[h] = (__ballot_sync(0xffffffffu, jl < jn ? sg : 0u) >> (16 * ((tid >> 4) & 1))) & 0xFFFFu;
     }
     const bool ok = mbar_wait_bounded(&bar[s], parity, kWaitLimit);
 
@@ -275,31 +280,38 @@ __global__ void __launch_bounds__(NT, 1)
         issue_next();
       }
     }
-    // Exchange phase: rows NRL*h + b, low log2(NRL) bits.
+    // Exchange phase: rows 16 rg + b (low four bits), columns 2 cp, 2 cp + 1.
+    {
+      float w0[NRL], w1[NRL];
+      float* tp = tile + (NRL * rg) * W + 2 * cp;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      float w2[NRL];
-      const int h = rl * Q + q;
+      for (int b = 0; b < NRL; ++b) {
+        const float2 t2 = *reinterpret_cast<const float2*>(tp + b * W);
+        w0[b] = t2.x;
+        w1[b] = t2.y;
+      }
+      fwht_regs<float, NRL>(w0);
+      fwht_regs<float, NRL>(w1);
 #pragma unroll
-      for (int b = 0; b < NRL; ++b) w2[b] = tile[(NRL * h + b) * W + cg];
-      fwht_regs<float, NRL>(w2);
-#pragma unroll
-      for (int b = 0; b < NRL; ++b) tile[(NRL * h + b) * W + cg] = w2[b];
+      for (int b = 0; b < NRL; ++b) *reinterpret_cast<float2*>(tp + b * W) = make_float2(w0[b], w1[b]);
     }
     __syncthreads();
-    // Sampled rows (offsets s_lo * W) with the signs of gmask.
-    const uint4* offv = reinterpret_cast<const uint4*>(s_off + rl * JM);
-    const float* tcol = tile + cg;
+    // Sampled rows (offsets s_lo * W) with the signs of gmask, two columns per load.
+    const uint4* offv = reinterpret_cast<const uint4*>(s_off + rg * JU);
+    const float* tq = tile + 2 * cp;
 #pragma unroll
-    for (int u4 = 0; u4 < JM / 4; ++u4) {
+    for (int u4 = 0; u4 < JU / 4; ++u4) {
       const uint4 o = offv[u4];
       const uint32_t oo[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int u = 4 * u4 + q;
-        const float tv = tcol[oo[q]];
-        const uint32_t sb = (gmask[u >> 5] << (31 - (u & 31))) & 0x80000000u;
-        acc[u] += __int_as_float(__float_as_int(tv) ^ (int)sb);
+        const float2 tv = *reinterpret_cast<const float2*>(tq + oo[q]);
+        // +-1.0f from the sign bit: the product is exact, so the FMA adds
+        // exactly +-tv, one instruction per column.
+        const float sg = __uint_as_float(((gmask[u >> 4] << (31 - (u & 15))) & 0x80000000u) | 0x3f800000u);
+        acc[u][0] = fmaf(tv.x, sg, acc[u][0]);
+        acc[u][1] = fmaf(tv.y, sg, acc[u][1]);
       }
     }
     if constexpr (!S::kInPlace) {

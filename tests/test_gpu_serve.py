@@ -72,22 +72,26 @@ def test_mix_equals_alone(lib):
     alone_r = [tuple(x.clone() for x in t) for t in alone_r]
     alone_n = tuple(x.clone() for x in alone_n)
 
-    with lib.Server(hbm_budget=2 << 30, executors=4, max_group=16) as srv:
+    # Two executors: the RSVD / Nystrom requests, submitted first, keep them
+    # busy while the sketches queue up, so the sketches must be packed into
+    # grouped launches when an executor frees up.
+    with lib.Server(hbm_budget=2 << 30, executors=2, max_group=16) as srv:
         tickets, outs = [], []
-        for (n, m, p, l, dt, seed), a in sk:
-            out = torch.empty(l, m, device="cuda", dtype=lib.sketch_out_dtype(dt))
-            tickets.append(srv.submit_sketch(a, p, l, seed, out))
-            outs.append(out)
         r_outs = []
         for a in (a_r, a_r32):
             o = (torch.empty(a.shape[0], 20, device="cuda", dtype=torch.float64),
                  torch.empty(20, device="cuda", dtype=torch.float64),
                  torch.empty(a.shape[1], 20, device="cuda", dtype=torch.float64))
-            tickets.append(srv.submit_rsvd(a, 20, 64, 4, 3, o))
             r_outs.append(o)
         n_out = (torch.empty(3000, 30, device="cuda", dtype=torch.float64),
                  torch.empty(30, device="cuda", dtype=torch.float64))
-        tickets.append(srv.submit_nystrom(a_n, 30, 60, 4, 2, n_out))
+        sk_outs = [torch.empty(l, m, device="cuda", dtype=lib.sketch_out_dtype(dt)) for (n, m, p, l, dt, seed), a in sk]
+        r_tickets = [srv.submit_rsvd(a, 20, 64, 4, 3, o) for a, o in zip((a_r, a_r32), r_outs)]
+        n_ticket = srv.submit_nystrom(a_n, 30, 60, 4, 2, n_out)
+        for ((n, m, p, l, dt, seed), a), out in zip(sk, sk_outs):
+            tickets.append(srv.submit_sketch(a, p, l, seed, out))
+            outs.append(out)
+        tickets += r_tickets + [n_ticket]
         for t in tickets:
             assert srv.wait(t, 600.0) == 0
         st = srv.stats()
