@@ -275,7 +275,7 @@ SKETCH_TRAFFIC_F32_N2E20_M4096 = 4 * 4.2956e9 + 0.0119e9
 
 
 def sketch_traffic(args, mode):
-    if (args.dtype, args.n, args.m, args.p, args.l) == ("f32", 1 << 20, 4096, 4, 512):
+    if (args.dtype, args.n, args.m, args.p, args.l, args.variant) == ("f32", 1 << 20, 4096, 4, 512, "auto"):
         return SKETCH_TRAFFIC_F32_N2E20_M4096
     return None
 

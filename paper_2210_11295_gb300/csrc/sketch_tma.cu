@@ -8,7 +8,9 @@
 // (eq. 2.4 block sum), partials reduced in a fixed order.  The register
 // phase (high five row bits) gives each thread one column of 32 rows; the
 // exchange phase (low four bits) and the gather give it two adjacent columns
-// and use 64-bit shared-memory accesses.  Here one thread
+// and use 64-bit shared-memory accesses.  For l > 512 a 256-thread form
+// (k_sketch_tma256) holds 2 x 32 rows in the register phase and 4 columns in
+// the exchange phase and gather.  Here one thread
 // streams the chunks with cp.async.bulk.tensor into a STAGES-deep ring
 // guarded by mbarriers, so HBM reads of later chunks overlap the butterflies
 // and the gather of the current one.  FP32 inputs are transformed in place
@@ -49,6 +51,24 @@ struct TmaShape {
   static_assert(NT % W == 0 && E >= NRL && E % NRL == 0, "thread layout");
   static_assert(R2 >= 64 && R2 % BOXR == 0, "chunk rows");
   static_assert(JG % 64 == 0, "sketch-row groups on 64-bit words");
+};
+
+// Chunk geometry: R2 = 512 rows x W = 32 columns, 256 threads (so each may
+// hold 64 values in registers).  Register phase (row bits 4-8): 16 row
+// lanes x 16 column pairs, rows rl + 16 e; exchange phase (bits 0-3) and
+// gather: 32 row groups x 8 column quads.  JU sketch rows per thread (32 JU
+// per launch).
+template <typename Tin, int JU, int STAGES>
+struct TmaShape256 {
+  static constexpr int W = 32, NT = 256, R2 = 512;
+  static constexpr int JG = 32 * JU;
+  static constexpr bool kInPlace = sizeof(Tin) == 4;
+  static constexpr int BOXR = 256;
+  static constexpr size_t stage_bytes = sizeof(Tin) * (size_t)R2 * W;
+  static constexpr size_t tile_bytes = kInPlace ? 0 : sizeof(float) * (size_t)R2 * W;
+  static constexpr size_t meta_bytes = 2 * sizeof(uint32_t) * JG + sizeof(uint64_t) * STAGES;
+  static constexpr size_t smem_bytes() { return STAGES * stage_bytes + tile_bytes + meta_bytes + 128; }
+  static_assert(JG % 64 == 0 && JU % 8 == 0, "sketch-row groups on 64-bit words");
 };
 
 template <typename Tin>
@@ -329,6 +349,256 @@ __global__ void __launch_bounds__(NT, 1)
   if (cur_pc >= 0) flush(cur_pc);
 }
 
+template <typename Tin, int JU, int STAGES>
+__global__ void __launch_bounds__(256, 1)
+    k_sketch_tma256(const __grid_constant__ CUtensorMap tmap, SketchArgs g, const uint32_t* __restrict__ dmtab,
+                 const uint64_t* __restrict__ dttab, int64_t tw, int* __restrict__ err) {
+  using S = TmaShape256<Tin, JU, STAGES>;
+  constexpr int W = S::W, NT = S::NT, R2 = S::R2, JG = S::JG, BOXR = S::BOXR;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((128 - (reinterpret_cast<uintptr_t>(smem_raw) & 127)) & 127);
+  Tin* stage = reinterpret_cast<Tin*>(base);                                   // [STAGES][R2][W]
+  float* tile_sep = reinterpret_cast<float*>(base + STAGES * S::stage_bytes);  // [R2][W] (16-bit inputs)
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(base + STAGES * S::stage_bytes + S::tile_bytes);  // s_lo * W
+  uint32_t* s_hi = s_off + JG;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_hi + JG);
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int rl = tid >> 4, cp = tid & 15;  // register phase: row lane, column pair
+  const int rg = tid >> 3, c4 = tid & 7;   // exchange phase and gather: row group, column quad
+  const int jn = (int)g.jn;
+  TileSched sched;
+  sched.init(g, (int)blockIdx.x);
+  const int64_t t_begin = sched.begin;
+  const int64_t ntiles = sched.end - sched.begin;
+
+  // Tile t = (panel pc, block i, chunk a) in panel-major order; iterators
+  // advance without divisions.
+  struct TileIt {
+    int64_t pc, i, a;
+    int step;
+    __device__ void next(int64_t nch, int p) {
+      if (++a == nch) {
+        a = 0;
+        if (++i == p) {
+          i = 0;
+          pc += step;
+        }
+      }
+    }
+  };
+  auto tile_at = [&](int64_t t) {  // unit t of the schedule
+    TileIt it;
+    const int64_t u = t / g.C;
+    const int64_t c = t - u * g.C;
+    it.pc = u * sched.step + sched.half;
+    it.i = c / g.nch;
+    it.a = c - it.i * g.nch;
+    it.step = sched.step;
+    return it;
+  };
+  TileIt iss = tile_at(t_begin);  // next tile to issue (thread 0 only)
+  int64_t issued = 0;
+  auto issue_next = [&]() {  // TMA for the CTA's next tile into stage issued % STAGES
+    const int s = (int)(issued % STAGES);
+    Tin* dst = stage + (size_t)s * R2 * W;
+    mbar_arrive_expect_tx(&bar[s], (uint32_t)S::stage_bytes);
+    const int32_t x = (int32_t)(iss.pc * W);
+    const int64_t y0 = iss.i * g.rb + iss.a * R2;
+#pragma unroll
+    for (int h = 0; h < R2 / BOXR; ++h)
+      tma_load_2d(dst + (size_t)h * BOXR * W, &tmap, &bar[s], x, (int32_t)(y0 + h * BOXR));
+    iss.next(g.nch, g.p);
+    ++issued;
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  for (int jl = tid; jl < JG; jl += NT) {
+    uint32_t off = 0, hi = 0;
+    if (jl < jn) {
+      const uint64_t sv = sample_word(g.seed, (uint64_t)(g.j0 + jl)) & (uint64_t)(g.r - 1);
+      off = (uint32_t)(sv & (R2 - 1)) * W;
+      hi = (uint32_t)(sv >> 9);  // R2 = 512
+    }
+    s_off[(jl % 32) * JU + jl / 32] = off;  // [row group rg][u]: jl = rg + 32 u
+    s_hi[jl] = hi;
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int64_t k = 0; k < STAGES && k < ntiles; ++k) issue_next();
+
+  // Gather: sketch rows jl = rg + 32 u, u < JU, four columns each.  The 8
+  // lanes of a row group share its sketch rows: lane c4 evaluates the
+  // outer-factor x Dt^(i) sign of u = 8 h + c4 and a warp ballot hands each
+  // lane its row group's byte.  s_hi never changes; the Dt word only with
+  // the block.
+  constexpr int NH = JU / 8;
+  uint32_t my_hi[NH];
+  uint64_t my_dt[NH];
+  int64_t dt_block = -1;
+#pragma unroll
+  for (int h = 0; h < NH; ++h) {
+    my_hi[h] = s_hi[rg + 32 * (8 * h + c4)];
+    my_dt[h] = 0;
+  }
+
+  float acc[JU][4];
+#pragma unroll
+  for (int u = 0; u < JU; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
+  int64_t cur_pc = -1;
+  float* part = static_cast<float*>(g.part);
+  auto flush = [&](int64_t pc) {
+    float* dst = part + sched.slot(pc) * (int64_t)jn * W + 4 * c4;
+#pragma unroll
+    for (int u = 0; u < JU; ++u) {
+      const int jl = rg + 32 * u;
+      if (jl < jn)
+        *reinterpret_cast<float4*>(dst + (int64_t)jl * W) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+    }
+  };
+
+  TileIt cur = tile_at(t_begin);
+  uint32_t dmask_next = ntiles > 0 ? __ldg(dmtab + (cur.i * g.nch + cur.a) * 16 + rl) : 0u;  // rows rl + 16 e
+  int s = 0;
+  uint32_t parity = 0;
+  for (int64_t k = 0; k < ntiles; ++k, cur.next(g.nch, g.p)) {
+    const int64_t pc = cur.pc, i = cur.i, a = cur.a;
+    if (pc != cur_pc) {
+      if (cur_pc >= 0) flush(cur_pc);
+#pragma unroll
+      for (int u = 0; u < JU; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
+      cur_pc = pc;
+    }
+    const int64_t rows_i = min(g.rb, g.n - i * g.rb);
+    const int64_t row0 = a * R2;
+    const int nvalid = (int)min((int64_t)R2, rows_i - row0);
+    // This thread's 32 D^(i) signs (rows rl + 16e) and, by a warp ballot, the
+    // outer-factor x Dt^(i) signs of its row lane's sketch rows jl = rl + 16u.
+    const uint32_t dmask = dmask_next;
+    {  // prefetch the next chunk's D mask
+      TileIt nx = cur;
+      nx.next(g.nch, g.p);
+      if (k + 1 < ntiles) dmask_next = __ldg(dmtab + (nx.i * g.nch + nx.a) * 16 + rl);
+    }
+    if (i != dt_block) {
+#pragma unroll
+      for (int h = 0; h < NH; ++h) {
+        const int jl = rg + 32 * (8 * h + c4);
+        my_dt[h] = jl < jn ? __ldg(dttab + i * tw + (jl >> 6)) : 0ull;
+      }
+      dt_block = i;
+    }
+    uint32_t gmask[NH];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      const int jl = rg + 32 * (8 * h + c4);
+      const uint32_t sg = (uint32_t)((__popc(my_hi[h] & (uint32_t)a) + (int)((my_dt[h] >> (jl & 63)) & 1ull)) & 1);
+      gmask[h] = (__ballot_sync(0xffffffffu, jl < jn ? sg : 0u) >> (8 * (lane >> 3))) & 0xFFu;
+    }
+    const bool ok = mbar_wait_bounded(&bar[s], parity, kWaitLimit);
+
+    Tin* st = stage + (size_t)s * R2 * W;
+    float* tile = S::kInPlace ? reinterpret_cast<float*>(st) : tile_sep;
+    // Register phase: rows rl + 16 e (high five row bits), columns 2 cp,
+    // 2 cp + 1, D^(i) signs (one per row for both columns).
+    {
+      float v0[32], v1[32];
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        const int rr = rl + 16 * e;
+        float x0 = 0.f, x1 = 0.f;
+        if (nvalid == R2 || rr < nvalid) {
+          if constexpr (sizeof(Tin) == 4) {
+            const float2 t2 = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st) + rr * W + 2 * cp);
+            x0 = t2.x;
+            x1 = t2.y;
+          } else {
+            const uint32_t raw = *reinterpret_cast<const uint32_t*>(st + rr * W + 2 * cp);
+            const Tin* h2 = reinterpret_cast<const Tin*>(&raw);
+            x0 = widen<Tin>(h2[0]);
+            x1 = widen<Tin>(h2[1]);
+          }
+        }
+        const uint32_t sb = (dmask << (31 - e)) & 0x80000000u;
+        v0[e] = __uint_as_float(__float_as_uint(x0) ^ sb);
+        v1[e] = __uint_as_float(__float_as_uint(x1) ^ sb);
+      }
+      fwht_regs<float, 32>(v0);
+      fwht_regs<float, 32>(v1);
+      if constexpr (!S::kInPlace) __syncthreads();  // the previous chunk's gather is done with the tile
+#pragma unroll
+      for (int e = 0; e < 32; ++e)
+        *reinterpret_cast<float2*>(tile + (rl + 16 * e) * W + 2 * cp) = make_float2(v0[e], v1[e]);
+    }
+    // One barrier both publishes the register phase and makes a failed
+    // (bounded) wait CTA-uniform: data read after a failed wait is garbage
+    // but nothing reaches global memory before this check.
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(err, 1);
+        for (int64_t kk = (issued - STAGES < k ? k : issued - STAGES); kk < issued; ++kk)
+          mbar_wait_bounded(&bar[kk % STAGES], (uint32_t)((kk / STAGES) & 1), kWaitLimit);
+      }
+      __syncthreads();
+      return;
+    }
+    // Every thread has finished the previous chunk's gather (FP32: its stage,
+    // which is its tile, is free) or this chunk's widening (16-bit: this
+    // stage is free): refill it.
+    if (tid == 0 && issued < ntiles && (!S::kInPlace || k >= 1)) {
+      fence_proxy_async_smem();
+      issue_next();
+    }
+    // Exchange phase: rows 16 rg + b (low four bits), columns 4 c4 .. 4 c4 + 3.
+    {
+      float w[4][16];
+      float* tp = tile + (16 * rg) * W + 4 * c4;
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        const float4 t4 = *reinterpret_cast<const float4*>(tp + b * W);
+        w[0][b] = t4.x;
+        w[1][b] = t4.y;
+        w[2][b] = t4.z;
+        w[3][b] = t4.w;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) fwht_regs<float, 16>(w[c]);
+#pragma unroll
+      for (int b = 0; b < 16; ++b)
+        *reinterpret_cast<float4*>(tp + b * W) = make_float4(w[0][b], w[1][b], w[2][b], w[3][b]);
+    }
+    __syncthreads();
+    // Sampled rows (offsets s_lo * W) with the signs of gmask, four columns
+    // per load; +-1.0f from the sign bit makes the FMA add exactly +-t.
+    const uint4* offv = reinterpret_cast<const uint4*>(s_off + rg * JU);
+    const float* tq = tile + 4 * c4;
+#pragma unroll
+    for (int u4 = 0; u4 < JU / 4; ++u4) {
+      const uint4 o = offv[u4];
+      const uint32_t oo[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int u = 4 * u4 + q;
+        const float4 tv = *reinterpret_cast<const float4*>(tq + oo[q]);
+        const float sg = __uint_as_float(((gmask[u >> 3] << (31 - (u & 7))) & 0x80000000u) | 0x3f800000u);
+        acc[u][0] = fmaf(tv.x, sg, acc[u][0]);
+        acc[u][1] = fmaf(tv.y, sg, acc[u][1]);
+        acc[u][2] = fmaf(tv.z, sg, acc[u][2]);
+        acc[u][3] = fmaf(tv.w, sg, acc[u][3]);
+      }
+    }
+    if (++s == STAGES) {
+      s = 0;
+      parity ^= 1u;
+    }
+  }
+  if (cur_pc >= 0) flush(cur_pc);
+}
+
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -348,13 +618,35 @@ EncodeFn encode_fn() {
   return fn;
 }
 
+// l <= 512 (JM = 32): 512 threads of 32 values (more warps hide the
+// shared-memory latency); l > 512 (JM = 64): 256 threads of 64 values, whose
+// 255-register budget holds the 128 accumulators without spilling much.
+template <typename Tin, int JM>
+struct TmaKernel {
+  static constexpr int STAGES = stages_for<Tin>();
+  static constexpr bool k256 = JM == 64;
+  static constexpr int NT = k256 ? 256 : 512;
+  static size_t smem() {
+    if constexpr (k256)
+      return TmaShape256<Tin, JM / 2, STAGES>::smem_bytes();
+    else
+      return TmaShape<Tin, 32, 512, 512, JM, STAGES>::smem_bytes();
+  }
+  static auto fn() {
+    if constexpr (k256)
+      return k_sketch_tma256<Tin, JM / 2, STAGES>;
+    else
+      return k_sketch_tma<Tin, 32, 512, 512, JM, STAGES>;
+  }
+};
+
 template <typename Tin, int JM>
 int launch_tma(const SketchPlan& plan, const SketchArgs& a, const CUtensorMap& map, int* err, uint64_t* dtab,
                uint64_t* dttab, void* out, int64_t ldo, cudaStream_t stream) {
-  constexpr int W = 32, NT = 512, R2 = 512, STAGES = stages_for<Tin>();
-  using S = TmaShape<Tin, W, NT, R2, JM, STAGES>;
-  auto kern = k_sketch_tma<Tin, W, NT, R2, JM, STAGES>;
-  const size_t smem = S::smem_bytes();
+  constexpr int W = 32;
+  constexpr int NT = TmaKernel<Tin, JM>::NT;
+  auto kern = TmaKernel<Tin, JM>::fn();
+  const size_t smem = TmaKernel<Tin, JM>::smem();
   BSRHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t tw = (a.jn + 63) / 64;
   const int64_t tot = (int64_t)plan.p * (plan.nch * 16 + tw);
@@ -375,10 +667,9 @@ int launch_tma(const SketchPlan& plan, const SketchArgs& a, const CUtensorMap& m
 
 template <typename Tin, int JM>
 int occ_tma() {
-  constexpr int W = 32, NT = 512, R2 = 512, STAGES = stages_for<Tin>();
-  using S = TmaShape<Tin, W, NT, R2, JM, STAGES>;
-  auto kern = k_sketch_tma<Tin, W, NT, R2, JM, STAGES>;
-  const size_t smem = S::smem_bytes();
+  constexpr int NT = TmaKernel<Tin, JM>::NT;
+  auto kern = TmaKernel<Tin, JM>::fn();
+  const size_t smem = TmaKernel<Tin, JM>::smem();
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess) return 0;
