@@ -291,9 +291,13 @@ __device__ __forceinline__ T warp_sum(T v) {
 // most tiny_rel ||M||_F, *fnorm = ||M||_F) are left alone: rounding keeps
 // their directions random and rotating them would never converge.
 // `status` (may be null) gets kStatusNoConv if max_sweeps ran out.
+// Column norms: nrm[c] = |M_c|^2 is formed exactly at the start of every
+// sweep and then carried through the rotations as alpha - t gamma and
+// beta + t gamma (what the rotation makes of them in exact arithmetic), so a
+// pair needs one inner product instead of three.
 template <typename T, int JR>
-__global__ void k_jacobi(T* __restrict__ M, T* __restrict__ V, int l, int lp, double tol, double tol_stop,
-                         const double* __restrict__ fnorm, double tiny_rel, int max_sweeps,
+__global__ void k_jacobi(T* __restrict__ M, T* __restrict__ V, T* __restrict__ nrm, int l, int lp, double tol,
+                         double tol_stop, const double* __restrict__ fnorm, double tiny_rel, int max_sweeps,
                          int* __restrict__ rot_counts, int* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
   const int lane = threadIdx.x & 31;
@@ -304,6 +308,18 @@ __global__ void k_jacobi(T* __restrict__ M, T* __restrict__ V, int l, int lp, do
   const T tiny2 = (T)(tiny * tiny);
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
+    for (int c = warp; c < l; c += nwarps) {
+      const T* __restrict__ col = M + (int64_t)c * l;
+      T sq = 0;
+#pragma unroll
+      for (int e = 0; e < JR; ++e) {
+        const int r = lane + 32 * e;
+        if (r < l) sq = fma(col[r], col[r], sq);
+      }
+      sq = warp_sum(sq);
+      if (lane == 0) nrm[c] = sq;
+    }
+    grid.sync();
     for (int round = 0; round < lp - 1; ++round) {
       for (int k = warp; k < lp / 2; k += nwarps) {
         int p = rr_player(k, round, lp), q = rr_player(lp - 1 - k, round, lp);
@@ -327,14 +343,10 @@ __global__ void k_jacobi(T* __restrict__ M, T* __restrict__ V, int l, int lp, do
           vx[e] = in ? va[r] : (T)0;
           vy[e] = in ? vb[r] : (T)0;
         }
-        T al = 0, be = 0, ga = 0;
+        T ga = 0;
 #pragma unroll
-        for (int e = 0; e < JR; ++e) {
-          al = fma(x[e], x[e], al);
-          be = fma(y[e], y[e], be);
-          ga = fma(x[e], y[e], ga);
-        }
-        const T alpha = warp_sum(al), beta = warp_sum(be), gamma = warp_sum(ga);
+        for (int e = 0; e < JR; ++e) ga = fma(x[e], y[e], ga);
+        const T alpha = nrm[p], beta = nrm[q], gamma = warp_sum(ga);
         if (alpha <= tiny2 && beta <= tiny2) continue;
         const T gnorm = sqrt(alpha * beta);
         if (gamma == (T)0 || !(fabs(gamma) > ttol * gnorm)) continue;
@@ -352,7 +364,11 @@ __global__ void k_jacobi(T* __restrict__ M, T* __restrict__ V, int l, int lp, do
             vb[r] = s * vx[e] + c * vy[e];
           }
         }
-        if (lane == 0 && significant) atomicAdd(&rot_counts[sweep], 1);
+        if (lane == 0) {
+          nrm[p] = alpha - t * gamma;
+          nrm[q] = beta + t * gamma;
+          if (significant) atomicAdd(&rot_counts[sweep], 1);
+        }
       }
       grid.sync();
     }
@@ -422,14 +438,14 @@ __global__ void k_ns_coeff(double* __restrict__ G, int64_t l) {
 namespace {
 
 template <typename T>
-int launch_jacobi(const Dla& d, T* cols, T* Vc, int64_t l, double tol, double tol_stop, const double* fnorm,
+int launch_jacobi(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, double tol, double tol_stop, const double* fnorm,
                   double tiny_rel, int max_sweeps, int* rot, int* status) {
   int li = (int)l, lp = (int)(l + (l & 1)), msw = max_sweeps;
   // One column pair per warp, two warps per block: spreads the l/2 pairs of a
   // round over as many SMs as possible (FP64 throughput is per SM).
   const int threads = 64;
   const int pairs = lp / 2;
-  void* args[] = {&cols, &Vc, &li, &lp, &tol, &tol_stop, &fnorm, &tiny_rel, &msw, &rot, &status};
+  void* args[] = {&cols, &Vc, &nrm, &li, &lp, &tol, &tol_stop, &fnorm, &tiny_rel, &msw, &rot, &status};
   auto launch = [&](auto kern) -> int {
     int occ = 0;
     BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0));
@@ -462,6 +478,8 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
   int* perm = static_cast<int*>(ar.take(sizeof(int) * l));
   int* rot = static_cast<int*>(ar.take(sizeof(int) * 2 * max_sweeps));
   double* fnorm = static_cast<double*>(ar.take(sizeof(double)));
+  double* nrm64 = static_cast<double*>(ar.take(sizeof(double) * l));
+  float* nrm32 = static_cast<float*>(ar.take(sizeof(float) * l));
   float *M32 = nullptr, *V32 = nullptr;
   double *S2 = nullptr, *G = nullptr, *Y = nullptr;
   if (mixed) {
@@ -502,8 +520,8 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
     k_init_identity_cols<float><<<blocks_for(l * l, 256), 256, 0, d.s>>>(V32, l);
     DLA_LAUNCH_CHECK();
     const double tol32 = 16.0 * std::sqrt((double)l) * 0x1.0p-24;
-    TRY_DLA(launch_jacobi<float>(d, M32, V32, l, tol32, tol32, fnorm, (double)l * 0x1.0p-24, 20, rot + max_sweeps,
-                                 nullptr));
+    TRY_DLA(launch_jacobi<float>(d, M32, V32, nrm32, l, tol32, tol32, fnorm, (double)l * 0x1.0p-24, 20,
+                                 rot + max_sweeps, nullptr));
     // 2. Make it orthogonal in FP64: with S = V0^T (the column storage),
     //    two Newton-Schulz steps S <- 1.5 S - 0.5 S (S^T S) take the
     //    orthogonality error from ~1e-6 to rounding level.
@@ -526,8 +544,8 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
     DLA_LAUNCH_CHECK();
   }
   // 4. FP64 one-sided Jacobi (from V0 it converges in a few sweeps).
-  TRY_DLA(launch_jacobi<double>(d, cols, Vc, l, tol, 16.0 * tol, fnorm, (double)l * 0x1.0p-53, max_sweeps, rot,
-                                d.status));
+  TRY_DLA(launch_jacobi<double>(d, cols, Vc, nrm64, l, tol, 16.0 * tol, fnorm, (double)l * 0x1.0p-53, max_sweeps,
+                                rot, d.status));
   k_col_norms<<<blocks_for(l, 8), 256, 0, d.s>>>(cols, sig, l);
   DLA_LAUNCH_CHECK();
   k_rank_desc<<<blocks_for(l, 256), 256, 0, d.s>>>(sig, perm, l);

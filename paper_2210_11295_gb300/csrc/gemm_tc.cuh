@@ -3,8 +3,9 @@
 //
 // A (M x K) and Bt = B^T (N x K) are FP32 with K contiguous (K-major) and
 // are read by TMA with the 128-byte swizzle.  Each tile is split in shared
-// memory into a TF32-exact hi part (low 13 mantissa bits cleared) and lo =
-// x - hi, and the product is accumulated in TMEM as
+// memory into a TF32-exact hi part (low 13 mantissa bits cleared; the TF32
+// MMA reads the staged x as exactly that) and lo = x - hi, and the product
+// is accumulated in TMEM as
 //   A_hi B_hi + A_hi B_lo + A_lo B_hi
 // (three TF32 MMAs; the dropped A_lo B_lo term and the TF32 truncation of the
 // lo parts leave a relative error of about 2^-21 per product, FP32 level).
@@ -117,20 +118,17 @@ __host__ __device__ __forceinline__ bool tile_below_diagonal(int64_t bm, int64_t
   return bm * BM >= (bn + 1) * BN;
 }
 
-// In-place split of n16 16-byte groups: hi keeps the TF32 bits, lo = x - hi.
-__device__ __forceinline__ void split_tf32(uint4* __restrict__ hi, uint4* __restrict__ lo, int t, int n16) {
+// Split of n16 16-byte groups: lo = x - hi with hi = x with the low 13
+// mantissa bits cleared.  The staged x itself serves as the hi operand: the
+// TF32 MMA reads only the top 19 bits of each 32-bit operand, which is hi.
+__device__ __forceinline__ void split_tf32(const uint4* __restrict__ hi, uint4* __restrict__ lo, int t, int n16) {
   for (int idx = t; idx < n16; idx += 128) {
     const uint4 x = hi[idx];
-    uint4 h, l;
-    h.x = x.x & 0xFFFFE000u;
-    h.y = x.y & 0xFFFFE000u;
-    h.z = x.z & 0xFFFFE000u;
-    h.w = x.w & 0xFFFFE000u;
-    l.x = __float_as_uint(__uint_as_float(x.x) - __uint_as_float(h.x));
-    l.y = __float_as_uint(__uint_as_float(x.y) - __uint_as_float(h.y));
-    l.z = __float_as_uint(__uint_as_float(x.z) - __uint_as_float(h.z));
-    l.w = __float_as_uint(__uint_as_float(x.w) - __uint_as_float(h.w));
-    hi[idx] = h;
+    uint4 l;
+    l.x = __float_as_uint(__uint_as_float(x.x) - __uint_as_float(x.x & 0xFFFFE000u));
+    l.y = __float_as_uint(__uint_as_float(x.y) - __uint_as_float(x.y & 0xFFFFE000u));
+    l.z = __float_as_uint(__uint_as_float(x.z) - __uint_as_float(x.z & 0xFFFFE000u));
+    l.w = __float_as_uint(__uint_as_float(x.w) - __uint_as_float(x.w & 0xFFFFE000u));
     lo[idx] = l;
   }
 }
