@@ -6,6 +6,7 @@
 
 #include "common.cuh"
 #include "dla.cuh"
+#include "trace.cuh"
 #include "gemm.cuh"
 #include "sketch.cuh"
 
@@ -522,6 +523,7 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
     const double tol32 = 16.0 * std::sqrt((double)l) * 0x1.0p-24;
     TRY_DLA(launch_jacobi<float>(d, M32, V32, nrm32, l, tol32, tol32, fnorm, (double)l * 0x1.0p-24, 20,
                                  rot + max_sweeps, nullptr));
+    trace_mark(d.s, "svd_jacobi_fp32");
     // 2. Make it orthogonal in FP64: with S = V0^T (the column storage),
     //    two Newton-Schulz steps S <- 1.5 S - 0.5 S (S^T S) take the
     //    orthogonality error from ~1e-6 to rounding level.
@@ -539,6 +541,7 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
     //    rotations compose onto V0 and M V = U Sigma holds for the result.
     TRY_DLA(gemm64(Vc, false, colsM, Y, false));
     cols = Y;
+    trace_mark(d.s, "svd_orthogonalize");
   } else {
     k_init_identity_cols<double><<<blocks_for(l * l, 256), 256, 0, d.s>>>(Vc, l);
     DLA_LAUNCH_CHECK();

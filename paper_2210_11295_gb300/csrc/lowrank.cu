@@ -162,9 +162,16 @@ OrthBufs take_orth_bufs(Arena& ar, int64_t l, size_t cs) {
 // Buffers: X (input), Y and Z (rows x l scratch). On return *Qout points to
 // the buffer holding Q; X is left intact when keep_x (then Q is not formed
 // on the fast path unless need_q).
+// With Rinv_out != nullptr the fast path may return Q in factored form,
+// Q = Q1 R2^{-1}: then *Qout holds the first-pass basis Q1 and *Rinv_out the
+// upper-triangular FP64 R2^{-1} (l x l), and the caller applies R2^{-1} to its
+// small right-hand factor instead of forming Q (one rows x l x l product
+// less).  *Rinv_out is nullptr when Q is explicit.
 int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void* Z, int64_t rows, int64_t l,
-                uint64_t seed, const OrthBufs& b, double* R, bool need_q, bool keep_x, void** Qout) {
+                uint64_t seed, const OrthBufs& b, double* R, bool need_q, bool keep_x, void** Qout,
+                const double** Rinv_out = nullptr) {
   const void* RinvB = (tc == DT::F32) ? b.Rinv_c : (const void*)b.Rinv;
+  if (Rinv_out) *Rinv_out = nullptr;
   // ---- fast path: CholeskyQR2 (Z serves as scratch for the transposed Grams)
   bool fast = true;
   TRY(tall_gram(d, ar, dry, tc, X, rows, l, Z, b.G));
@@ -199,7 +206,12 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
         if (tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
       }
       void* dst = keep_x ? Z : X;
-      if (need_q || !keep_x) TRY(tall_gemm(d, ar, tc, tc, tc, rows, l, l, Y, l, b.Rinv, RinvB, l, dst, l, true));
+      if (Rinv_out) {
+        *Rinv_out = b.Rinv;
+        dst = Y;
+      } else if (need_q || !keep_x) {
+        TRY(tall_gemm(d, ar, tc, tc, tc, rows, l, l, Y, l, b.Rinv, RinvB, l, dst, l, true));
+      }
       if (R) TRY(gemm64(d, ar, l, l, l, b.LT2, l, false, b.LT1, l, R, l, true, false));
       *Qout = dst;
       if (!dry) return BSRHT_OK;
@@ -293,6 +305,7 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
   double* Us = static_cast<double*>(ar.take(8 * l * l));
   double* Vs = static_cast<double*>(ar.take(8 * l * l));
   double* sig = static_cast<double*>(ar.take(8 * l));
+  double* Vp = static_cast<double*>(ar.take(8 * l * k));
   void* Vs_c = ar.take(cs * l * l);
   const OrthBufs ob = take_orth_bufs(ar, l, cs);
   if (!ar.ok()) return BSRHT_ENOMEM;
@@ -316,9 +329,11 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
   // Step 3: the paper's Z = Q^T A_paper, i.e. Z^T = A Q (n x l): second pass over A.
   TRY(tall_gemm(d, ar, ta, tc, tc, n, l, m, A, lda, Q, Qa, l, W1, l, false));
   if (!dry) trace_mark(d.s, "second_pass");
-  // Step 4: Z^T = P R (CholeskyQR2, rank-robust).
+  // Step 4: Z^T = P R (CholeskyQR2, rank-robust).  On the CholeskyQR2 path P
+  // stays factored, P = P1 R2^{-1} (Rinv2 != nullptr).
   void* Pv = nullptr;
-  TRY(orth_robust(d, ar, dry, tc, W1, W2, W3, n, l, seed ^ 0x52ull, ob, R, true, false, &Pv));
+  const double* Rinv2 = nullptr;
+  TRY(orth_robust(d, ar, dry, tc, W1, W2, W3, n, l, seed ^ 0x52ull, ob, R, true, false, &Pv, &Rinv2));
   if (!dry) trace_mark(d.s, "tall_qr");
   // Step 5: SVD of R^T; the columns of R^T are the rows of R.
   {
@@ -327,13 +342,21 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
     ar.release(mk);
   }
   if (!dry) trace_mark(d.s, "small_svd");
-  // Step 6: U = P V~_k, V = Q U~_k, S = Sigma~_k.
-  const void* Vk = Vs;
+  // Step 6: U = P V~_k, V = Q U~_k, S = Sigma~_k.  With P factored, U =
+  // P1 (R2^{-1} V~_k): the l x k factor is formed in FP64 first.
+  const double* Vk64 = Vs;
+  int64_t ldv = l;
+  if (Rinv2) {
+    TRY(gemm64(d, ar, l, k, l, Rinv2, l, false, Vs, l, Vp, k));
+    Vk64 = Vp;
+    ldv = k;
+  }
+  const void* Vk = Vk64;
   if (tc == DT::F32) {
-    if (!dry) TRY(cast_copy(d, DT::F64, Vs, DT::F32, Vs_c, l * l));
+    if (!dry) TRY(cast_copy(d, DT::F64, Vk64, DT::F32, Vs_c, ldv == l ? l * l : l * k));
     Vk = Vs_c;
   }
-  TRY(tall_gemm(d, ar, tc, tc, DT::F64, n, k, l, Pv, l, Vs, Vk, l, U, k, false));
+  TRY(tall_gemm(d, ar, tc, tc, DT::F64, n, k, l, Pv, l, Vk64, Vk, ldv, U, k, false));
   TRY(gemm64(d, ar, m, k, l, Q, l, false, Us, l, V, k));
   if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(S, sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, d.s));
   {
