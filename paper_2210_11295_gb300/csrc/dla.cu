@@ -282,54 +282,87 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // One-sided (Hestenes) Jacobi on the columns of M with round-robin pairs;
-// one warp per column pair, a grid-wide barrier between rounds.  A warp loads
-// its two columns of M and of V into registers (JR values per lane), forms
-// the three inner products, rotates in registers and stores once, so each
-// round costs one round trip to L2 instead of one per element.  A pair is
-// rotated while |x.y| > tol sqrt(x.x y.y); the sweeps stop after one in
-// which no rotation exceeded tol_stop (>= tol), i.e. once only rounding-level
-// rotations are left.  Two columns that are both numerically zero (norm at
-// most tiny_rel ||M||_F, *fnorm = ||M||_F) are left alone: rounding keeps
-// their directions random and rotating them would never converge.
+// one block of WP warps per column pair, a grid-wide barrier between rounds.
+// Warp w of the block holds rows w*32*JR .. (w+1)*32*JR-1 of the two columns
+// of M and of V in registers (JR values per lane), the block sums the
+// partial inner products in shared memory, every warp derives the rotation
+// from the sum and rotates its rows in registers, so each round costs one
+// round trip to L2 and one block barrier.  A pair is rotated while
+// |x.y| > tol sqrt(x.x y.y); the sweeps stop after one in which no rotation
+// exceeded tol_stop (>= tol), i.e. once only rounding-level rotations are
+// left.  Two columns that are both numerically zero (norm at most
+// tiny_rel ||M||_F, *fnorm = ||M||_F) are left alone: rounding keeps their
+// directions random and rotating them would never converge.
 // `status` (may be null) gets kStatusNoConv if max_sweeps ran out.
 // Column norms: nrm[c] = |M_c|^2 is formed exactly at the start of every
 // sweep and then carried through the rotations as alpha - t gamma and
 // beta + t gamma (what the rotation makes of them in exact arithmetic), so a
 // pair needs one inner product instead of three.
-template <typename T, int JR>
-__global__ void k_jacobi(T* __restrict__ M, T* __restrict__ V, T* __restrict__ nrm, int l, int lp, double tol,
-                         double tol_stop, const double* __restrict__ fnorm, double tiny_rel, int max_sweeps,
-                         int* __restrict__ rot_counts, int* __restrict__ status) {
+// Rotation: t = tan(theta) is the smaller root of gamma t^2 + (beta - alpha)
+// t - gamma = 0; c = 1/sqrt(1 + t^2), s = c t.  The rotation is orthogonal
+// for any t, and a relative error delta in t leaves a cosine of about delta
+// times the old one, so in FP64 t comes from an FP32 evaluation of the root
+// (the FP64 units of this GPU run at 1/64 of the FP32 rate) while c and s
+// are formed in FP64 from that t.
+__device__ __forceinline__ double jac_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float jac_rsqrt(float x) { return rsqrtf(x); }
+
+// tan(theta) for the pair (alpha, beta, gamma), gamma != 0, with
+// zeta = (beta - alpha) / (2 gamma).  For |zeta| > 2^60 the root is
+// 1 / (2 zeta) to relative 2^-122, which also keeps zeta^2 in FP32 range.
+__device__ __forceinline__ float jac_tangent(float alpha, float beta, float gamma) {
+  const float zeta = (beta - alpha) / (2.0f * gamma);
+  if (fabsf(zeta) > 0x1.0p60f) return 0.5f / zeta;
+  return (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+}
+__device__ __forceinline__ double jac_tangent(double alpha, double beta, double gamma) {
+  const double d = beta - alpha, g2 = 2.0 * gamma;
+  if (fabs(d) > 0x1.0p60 * fabs(g2)) return gamma / d;  // 1 / (2 zeta), in FP64
+  // |zeta| <= 2^60: scale d and 2 gamma by the same power of two so that
+  // 2 gamma lands in [1, 2); zeta is unchanged and both values are in FP32
+  // range.  Subnormal gamma (biased exponent 0) is scaled as if its
+  // exponent were -1022; its FP32 value is then below 1 but not zero.
+  int e = (int)((__double_as_longlong(g2) >> 52) & 0x7FF) - 1023;
+  e = e < -1022 ? -1022 : e;
+  const double sc = __longlong_as_double((long long)(1023 - e) << 52);  // 2^-e, e in [-1022, 1023]
+  const float zeta = __double2float_rn(d * sc) / __double2float_rn(g2 * sc);
+  return (double)((zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta)));
+}
+
+template <typename T, int JR, int WP>
+__global__ void __launch_bounds__(32 * WP) k_jacobi(T* __restrict__ M, T* __restrict__ V, T* __restrict__ nrm,
+                                                    int l, int lp, double tol, double tol_stop,
+                                                    const double* __restrict__ fnorm, double tiny_rel,
+                                                    int max_sweeps, int* __restrict__ rot_counts,
+                                                    int* __restrict__ status) {
   cg::grid_group grid = cg::this_grid();
-  const int lane = threadIdx.x & 31;
-  const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  const int nwarps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+  __shared__ T part[2][WP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int gwarp = blockIdx.x * WP + w, nwarps = gridDim.x * WP;
+  const T ttol2 = (T)(tol * tol), tstop2 = (T)(tol_stop * tol_stop);
   const T ttol = (T)tol, tstop = (T)tol_stop;
   const double tiny = tiny_rel * fnorm[0];
   const T tiny2 = (T)(tiny * tiny);
-  int sweep = 0;
+  const int row0 = w * 32 * JR + lane;
+  int sweep = 0, it = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    for (int c = warp; c < l; c += nwarps) {
+    for (int c = gwarp; c < l; c += nwarps) {
       const T* __restrict__ col = M + (int64_t)c * l;
       T sq = 0;
-#pragma unroll
-      for (int e = 0; e < JR; ++e) {
-        const int r = lane + 32 * e;
-        if (r < l) sq = fma(col[r], col[r], sq);
-      }
+      for (int r = lane; r < l; r += 32) sq = fma(col[r], col[r], sq);
       sq = warp_sum(sq);
       if (lane == 0) nrm[c] = sq;
     }
     grid.sync();
     for (int round = 0; round < lp - 1; ++round) {
-      for (int k = warp; k < lp / 2; k += nwarps) {
+      for (int k = blockIdx.x; k < lp / 2; k += gridDim.x) {
         int p = rr_player(k, round, lp), q = rr_player(lp - 1 - k, round, lp);
         if (p > q) {
           const int t = p;
           p = q;
           q = t;
         }
-        if (q >= l) continue;  // padding column
+        if (q >= l) continue;  // padding column (block-uniform)
         T* __restrict__ a = M + (int64_t)p * l;
         T* __restrict__ b = M + (int64_t)q * l;
         T* __restrict__ va = V + (int64_t)p * l;
@@ -337,7 +370,7 @@ __global__ void k_jacobi(T* __restrict__ M, T* __restrict__ V, T* __restrict__ n
         T x[JR], y[JR], vx[JR], vy[JR];
 #pragma unroll
         for (int e = 0; e < JR; ++e) {
-          const int r = lane + 32 * e;
+          const int r = row0 + 32 * e;
           const bool in = r < l;
           x[e] = in ? a[r] : (T)0;
           y[e] = in ? b[r] : (T)0;
@@ -347,17 +380,37 @@ __global__ void k_jacobi(T* __restrict__ M, T* __restrict__ V, T* __restrict__ n
         T ga = 0;
 #pragma unroll
         for (int e = 0; e < JR; ++e) ga = fma(x[e], y[e], ga);
-        const T alpha = nrm[p], beta = nrm[q], gamma = warp_sum(ga);
+        ga = warp_sum(ga);
+        const T alpha = nrm[p], beta = nrm[q];  // read before thread 0 updates them
+        if (WP > 1) {
+          // Double-buffered: a warp can be one pair ahead, never two (the
+          // barrier of the next pair waits for the slowest warp).
+          if (lane == 0) part[it & 1][w] = ga;
+          __syncthreads();
+          ga = 0;
+#pragma unroll
+          for (int u = 0; u < WP; ++u) ga += part[it & 1][u];
+          ++it;
+        }
+        const T gamma = ga;
         if (alpha <= tiny2 && beta <= tiny2) continue;
-        const T gnorm = sqrt(alpha * beta);
-        if (gamma == (T)0 || !(fabs(gamma) > ttol * gnorm)) continue;
-        const bool significant = fabs(gamma) > tstop * gnorm;
-        const T zeta = (beta - alpha) / ((T)2 * gamma);
-        const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-        const T c = (T)1 / sqrt((T)1 + t * t), s = c * t;
+        if (gamma == (T)0) continue;
+        bool rotate, significant;
+        if constexpr (sizeof(T) == 8) {
+          const T g2 = gamma * gamma, ab = alpha * beta;
+          rotate = g2 > ttol2 * ab;
+          significant = g2 > tstop2 * ab;
+        } else {
+          const T gnorm = sqrt(alpha) * sqrt(beta);  // alpha * beta may overflow FP32
+          rotate = fabs(gamma) > ttol * gnorm;
+          significant = fabs(gamma) > tstop * gnorm;
+        }
+        if (!rotate) continue;
+        const T t = jac_tangent(alpha, beta, gamma);
+        const T c = jac_rsqrt((T)1 + t * t), s = c * t;
 #pragma unroll
         for (int e = 0; e < JR; ++e) {
-          const int r = lane + 32 * e;
+          const int r = row0 + 32 * e;
           if (r < l) {
             a[r] = c * x[e] - s * y[e];
             b[r] = s * x[e] + c * y[e];
@@ -365,7 +418,7 @@ __global__ void k_jacobi(T* __restrict__ M, T* __restrict__ V, T* __restrict__ n
             vb[r] = s * vx[e] + c * vy[e];
           }
         }
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
           nrm[p] = alpha - t * gamma;
           nrm[q] = beta + t * gamma;
           if (significant) atomicAdd(&rot_counts[sweep], 1);
@@ -438,41 +491,61 @@ __global__ void k_ns_coeff(double* __restrict__ G, int64_t l) {
 
 namespace {
 
-template <typename T>
-int launch_jacobi(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, double tol, double tol_stop, const double* fnorm,
-                  double tiny_rel, int max_sweeps, int* rot, int* status) {
+// WP warps per column pair (measured on GB300 at l = 128 .. 1024): two for
+// FP64, where the rotations load the FP64 units and every warp of a pair
+// repeats the scalar work (four above l = 1024, to stay within 16 values per
+// lane); four for FP32 at l >= 512 and two below, where a round is
+// latency-bound and shorter per-warp chains help.
+template <typename T, int WP>
+int launch_jacobi_wp(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, double tol, double tol_stop,
+                     const double* fnorm, double tiny_rel, int max_sweeps, int* rot, int* status) {
   int li = (int)l, lp = (int)(l + (l & 1)), msw = max_sweeps;
-  // One column pair per warp, two warps per block: spreads the l/2 pairs of a
-  // round over as many SMs as possible (FP64 throughput is per SM).
-  const int threads = 64;
+  const int threads = 32 * WP;
   const int pairs = lp / 2;
   void* args[] = {&cols, &Vc, &nrm, &li, &lp, &tol, &tol_stop, &fnorm, &tiny_rel, &msw, &rot, &status};
   auto launch = [&](auto kern) -> int {
     int occ = 0;
     BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0));
-    const int blocks =
-        std::max(1, std::min((pairs + threads / 32 - 1) / (threads / 32), num_sms() * std::max(occ, 1)));
+    const int blocks = std::max(1, std::min(pairs, num_sms() * std::max(occ, 1)));
     BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(threads), args, 0, d.s));
     note_launches(1);
     return BSRHT_OK;
   };
   if (l <= 1) return BSRHT_OK;
-  if (l <= 128) return launch(k_jacobi<T, 4>);
-  if (l <= 256) return launch(k_jacobi<T, 8>);
-  if (l <= 512) return launch(k_jacobi<T, 16>);
-  if (l <= 1024) return launch(k_jacobi<T, 32>);
-  if (l <= 2048) return launch(k_jacobi<T, 64>);
+  const int64_t per = (l + 32 * WP - 1) / (32 * WP);  // values per lane and column
+  if (per <= 1) return launch(k_jacobi<T, 1, WP>);
+  if (per <= 2) return launch(k_jacobi<T, 2, WP>);
+  if (per <= 4) return launch(k_jacobi<T, 4, WP>);
+  if (per <= 8) return launch(k_jacobi<T, 8, WP>);
+  if (per <= 16) return launch(k_jacobi<T, 16, WP>);
+  if constexpr (sizeof(T) == 4) {
+    if (per <= 32) return launch(k_jacobi<T, 32, WP>);
+  }
   return BSRHT_EUNSUP;
+}
+
+template <typename T>
+int launch_jacobi(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, double tol, double tol_stop, const double* fnorm,
+                  double tiny_rel, int max_sweeps, int* rot, int* status) {
+  if constexpr (sizeof(T) == 8) {
+    if (l <= 1024)
+      return launch_jacobi_wp<T, 2>(d, cols, Vc, nrm, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot, status);
+    return launch_jacobi_wp<T, 4>(d, cols, Vc, nrm, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot, status);
+  } else if (l >= 512)
+    return launch_jacobi_wp<T, 4>(d, cols, Vc, nrm, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot, status);
+  else
+    return launch_jacobi_wp<T, 2>(d, cols, Vc, nrm, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot, status);
 }
 
 }  // namespace
 
-int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout) {
+int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout,
+               double polish_tol) {
   if (l > 2048) return BSRHT_EUNSUP;
   const int max_sweeps = 40;
   // Rotate only while the cosine of the pair exceeds sqrt(l) eps (the usual
   // one-sided Jacobi threshold); a tighter one keeps rotating at noise level.
-  const double tol = std::max(1e-15, std::sqrt((double)l) * 0x1.0p-52);
+  const double tol = polish_tol > 0.0 ? polish_tol : std::max(1e-15, std::sqrt((double)l) * 0x1.0p-52);
   const bool mixed = l > kJacobiMixedMin;
   double* Vc = static_cast<double*>(ar.take(sizeof(double) * l * l));
   double* sig = static_cast<double*>(ar.take(sizeof(double) * l));

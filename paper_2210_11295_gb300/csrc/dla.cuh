@@ -66,7 +66,11 @@ int tri_inverse(const Dla& d, const double* L, double* LT, double* Rinv, int64_t
 // colsM[c*l + i] = M[i][c].  On return colsM holds U Sigma (columns),
 // colsV[c*l + i] = V[i][c]; sigma[c] = ||U Sigma e_c||.  Columns are sorted
 // by descending sigma into U (l x l row-major, U[i][c]) and Vout (row-major).
-int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout);
+// polish_tol > 0 replaces the FP64 rotation threshold sqrt(l) 2^-52 on the
+// cosine of a pair: Vout (accumulated rotations) stays orthogonal to FP64
+// rounding whatever the threshold, the columns of U to about polish_tol.
+int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout,
+               double polish_tol = 0.0);
 
 // Tensor-core (tcgen05) GEMM in FP32 accuracy (three TF32 products):
 // C (M x N, FP32 or FP64 in tc_out, ldc) = A (M x K, FP32, lda) * B, with B

@@ -281,6 +281,12 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
   return BSRHT_OK;
 }
 
+// Cosine threshold of the FP64 Jacobi polish for FP32 data: 16 sqrt(l) 2^-40
+// (sweeps stop once none exceeds 16 times that), about 3.3e-10 at l = 512:
+// far below the FP32 accuracy of the tall factors it is combined with, and
+// reached in one rotating sweep from the FP32 Jacobi's 16 sqrt(l) 2^-24.
+double polish_tol_fp32(int64_t l) { return 16.0 * std::sqrt((double)l) * 0x1.0p-40; }
+
 // ---------------------------------------------------------------- RSVD
 int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, int64_t l, int p, uint64_t seed,
               double* U, double* S, double* V, Arena& ar, bool dry) {
@@ -306,6 +312,7 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
   double* Vs = static_cast<double*>(ar.take(8 * l * l));
   double* sig = static_cast<double*>(ar.take(8 * l));
   double* Vp = static_cast<double*>(ar.take(8 * l * k));
+  double* RT = static_cast<double*>(ar.take(8 * l * l));
   void* Vs_c = ar.take(cs * l * l);
   const OrthBufs ob = take_orth_bufs(ar, l, cs);
   if (!ar.ok()) return BSRHT_ENOMEM;
@@ -335,10 +342,20 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
   const double* Rinv2 = nullptr;
   TRY(orth_robust(d, ar, dry, tc, W1, W2, W3, n, l, seed ^ 0x52ull, ob, R, true, false, &Pv, &Rinv2));
   if (!dry) trace_mark(d.s, "tall_qr");
-  // Step 5: SVD of R^T; the columns of R^T are the rows of R.
+  // Step 5: SVD of R^T = U~ Sigma~ V~^T.  FP64 data: Jacobi on the columns
+  // of R^T (the rows of R) to FP64 tolerance.  FP32 data: Jacobi on the
+  // columns of R (R = V~ Sigma~ U~^T), so that the accumulated rotations,
+  // orthogonal to FP64 rounding, give U~ (multiplied by the FP64 Q below),
+  // and the polish stops at cosines of polish_tol_fp32(l): the other factor
+  // V~ meets P, itself orthogonal only to FP32 accuracy.
   {
     const size_t mk = ar.mark();
-    TRY(jacobi_svd(d, ar, R, l, Us, sig, Vs));
+    if (tc == DT::F32) {
+      if (!dry) TRY(transpose_lower_to_upper(d, R, RT, l));
+      TRY(jacobi_svd(d, ar, RT, l, Vs, sig, Us, polish_tol_fp32(l)));
+    } else {
+      TRY(jacobi_svd(d, ar, R, l, Us, sig, Vs));
+    }
     ar.release(mk);
   }
   if (!dry) trace_mark(d.s, "small_svd");
@@ -606,7 +623,7 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
   }
   {
     const size_t mk = ar.mark();
-    TRY(jacobi_svd(d, ar, RT, lr, Us, sig, Vs));
+    TRY(jacobi_svd(d, ar, RT, lr, Us, sig, Vs, tc == DT::F32 ? polish_tol_fp32(lr) : 0.0));
     ar.release(mk);
   }
   if (!dry) trace_mark(d.s, "small_svd");
