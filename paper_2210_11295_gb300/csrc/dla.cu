@@ -268,6 +268,246 @@ int tri_inverse(const Dla& d, const double* L, double* LT, double* Rinv, int64_t
   return BSRHT_OK;
 }
 
+// ------------------------------------------- fused Cholesky and inverse
+// One cooperative kernel: right-looking blocked Cholesky G = L L^T with
+// 32 x 32 blocks, and the same block eliminations applied to an identity
+// matrix T, which turns T into L^-1.  Step kb:
+//   (a) L_kk = chol(A_kk) and X_kk = L_kk^-1 (one CTA, shared memory);
+//   (b) panel L_ik = A_ik X_kk^T (one warp per row i > kb) and the final
+//       block row X_kb,c = X_kk T_kb,c of L^-1 (c < kb);
+//   (c) trailing update A_ij -= L_ik L_jk^T (kb < j <= i) and
+//       T_ic -= L_ik X_kb,c (c <= kb < i), one 32 x 32 tile per CTA; the CTA
+//       holding tile (kb+1, kb+1) then factors it, which is (a) of the next
+//       step.
+// Two grid barriers per block step.  Outputs: L in the lower triangle of g
+// (upper zeroed), LT = L^T and Rinv = L^-T (row-major, upper triangular).
+// T and X are l x l scratch.  A pivot <= 0 sets kStatusNotPD (and is
+// replaced by 1 so the kernel runs to the end).
+constexpr int kCB = 32;
+
+struct CholInvArgs {
+  double* g;
+  double* LT;
+  double* Rinv;
+  double* T;
+  double* X;
+  int l;
+  int nblk;
+  int* status;
+};
+
+// 1/sqrt(p) and sqrt(p) for a pivot p > 0: FP32 seed on p scaled by an even
+// power of two into [1, 4), then two Newton steps y <- y (3/2 - p y^2 / 2)
+// (relative error 2^-23 -> 2^-45 -> rounding); a dependent chain of about
+// ten FP64 operations instead of a square root and a division.
+__device__ __forceinline__ void ci_pivot(double p, double& r, double& y) {
+  if (p > 0x1.0p-1000 && p < 0x1.0p1000) {
+    const long long bits = __double_as_longlong(p);
+    const int e = (int)((bits >> 52) & 0x7FF) - 1023;  // p = f 2^e, f in [1, 2)
+    const int k = e >> 1;                               // floor(e / 2)
+    const double m = __longlong_as_double(bits - ((long long)(2 * k) << 52));  // p 2^-2k in [1, 4)
+    const double hm = -0.5 * m;
+    double y0 = (double)rsqrtf((float)m);
+    y0 = y0 * fma(hm * y0, y0, 1.5);
+    y0 = y0 * fma(hm * y0, y0, 1.5);
+    y = y0 * __longlong_as_double((long long)(1023 - k) << 52);  // times 2^-k
+    r = p * y;
+  } else {
+    r = sqrt(p);
+    y = 1.0 / r;
+  }
+}
+
+// (a): factor the diagonal block kb (already updated) and invert it.  The
+// block lives on one SM, whose FP64 rate bounds this step, so the trailing
+// update of a column enumerates only the lower-triangle entries (no idle
+// lanes on masked-out entries).
+__device__ void ci_factor_diag(const CholInvArgs& a, int kb, double (*s)[kCB + 1], double (*xi)[kCB + 1],
+                               double* dinv, double* rdiag, double (*red)[kCB]) {
+  const int tid = threadIdx.x, l = a.l, k0 = kb * kCB;
+  const int nb = min(kCB, l - k0);
+  for (int e = tid; e < kCB * kCB; e += blockDim.x) {
+    const int i = e / kCB, j = e % kCB;
+    double v = (i == j) ? 1.0 : 0.0;
+    if (i < nb && j < nb && j <= i) v = a.g[(int64_t)(k0 + i) * l + k0 + j];
+    s[i][j] = v;
+  }
+  for (int j = 0; j < kCB; ++j) {
+    __syncthreads();
+    if (tid == 0) {
+      double p = s[j][j];
+      if (!(p > 0.0)) {
+        atomicOr(a.status, kStatusNotPD);
+        p = 1.0;
+      }
+      double r, y;
+      ci_pivot(p, r, y);
+      s[j][j] = r;
+      rdiag[j] = r;
+      dinv[j] = y;
+    }
+    __syncthreads();
+    if (tid > j && tid < kCB) s[tid][j] *= dinv[j];
+    __syncthreads();
+    // Entries (i, c) with j < c <= i: item e -> row offset u with
+    // u (u + 1) / 2 <= e < (u + 1) (u + 2) / 2.
+    const int rem = kCB - 1 - j;
+    const int items = rem * (rem + 1) / 2;
+    for (int e = tid; e < items; e += blockDim.x) {
+      int u = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((u + 1) * (u + 2) / 2 <= e) ++u;
+      while (u * (u + 1) / 2 > e) --u;
+      const int i = j + 1 + u, c = j + 1 + (e - u * (u + 1) / 2);
+      s[i][c] -= s[i][j] * s[c][j];
+    }
+  }
+  __syncthreads();
+  // X_kk = L_kk^-1 row by row: X[i][c] = (delta_ic - sum_{c<=k<i} L[i][k] X[k][c]) / L[i][i];
+  // lane = column c, the eight warps split the sum over k.
+  const int lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = 0; i < kCB; ++i) {
+    double part = 0.0;
+    for (int k = lane + w; k < i; k += nw)  // k >= c = lane
+      part = fma(s[i][k], xi[k][lane], part);
+    red[w][lane] = part;
+    __syncthreads();
+    if (w == 0) {
+      double sum = 0.0;
+      for (int u = 0; u < nw; ++u) sum += red[u][lane];
+      xi[i][lane] = (lane <= i) ? ((i == lane ? 1.0 : 0.0) - sum) * dinv[i] : 0.0;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    a.g[(int64_t)(k0 + i) * l + k0 + j] = (j <= i) ? s[i][j] : 0.0;
+    a.X[(int64_t)(k0 + i) * l + k0 + j] = xi[i][j];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_chol_inv(CholInvArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double s0[kCB][kCB + 1];
+  __shared__ double s1[kCB][kCB + 1];
+  __shared__ double dinv[kCB];
+  __shared__ double rdiag[kCB];
+  __shared__ double red[8][kCB];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int l = a.l, nblk = a.nblk;
+  const int64_t ll = (int64_t)l * l;
+  // T = I (only its lower block triangle is ever read).
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + tid; e < ll; e += (int64_t)gridDim.x * blockDim.x)
+    a.T[e] = (e / l == e % l) ? 1.0 : 0.0;
+  if (blockIdx.x == 0) ci_factor_diag(a, 0, s0, s1, dinv, rdiag, red);
+  grid.sync();
+  const int gw = blockIdx.x * (blockDim.x >> 5) + w, nwg = gridDim.x * (blockDim.x >> 5);
+  for (int kb = 0; kb < nblk; ++kb) {
+    const int k0 = kb * kCB, nb = min(kCB, l - k0);
+    const int rows_below = l - k0 - nb;
+    // (b) X_kk into shared memory (every CTA), then panel rows and X row block.
+    for (int e = tid; e < kCB * kCB; e += blockDim.x) {
+      const int i = e / kCB, j = e % kCB;
+      s1[i][j] = (i < nb && j < nb) ? a.X[(int64_t)(k0 + i) * l + k0 + j] : 0.0;
+    }
+    __syncthreads();
+    const int xrow_items = kb * kCB;  // rows r < 32 of block kb times column blocks c < kb
+    for (int it = gw; it < rows_below + xrow_items; it += nwg) {
+      if (it < rows_below) {
+        const int64_t i = k0 + nb + it;
+        const double v = lane < nb ? a.g[i * l + k0 + lane] : 0.0;
+        double out = 0.0;
+        for (int e = 0; e < kCB; ++e) out = fma(__shfl_sync(0xffffffffu, v, e), s1[lane][e], out);
+        if (lane < nb) a.g[i * l + k0 + lane] = out;
+      } else {
+        const int q = it - rows_below, r = q / kb, c = q % kb;
+        if (r < nb) {
+          // X[k0+r][c*32+lane] = sum_{e<=r} X_kk[r][e] T[k0+e][c*32+lane]
+          double out = 0.0;
+          for (int e = 0; e <= r; ++e) out = fma(s1[r][e], a.T[(int64_t)(k0 + e) * l + c * kCB + lane], out);
+          a.X[(int64_t)(k0 + r) * l + c * kCB + lane] = out;
+        }
+      }
+    }
+    grid.sync();
+    if (kb + 1 == nblk) break;
+    // (c) trailing tiles (bi >= bj > kb) and T tiles (bi > kb >= c).
+    const int rem = nblk - kb - 1;
+    const int n_trail = rem * (rem + 1) / 2, n_t = rem * (kb + 1);
+    const int tx = tid & 31, ty = tid >> 5;
+    for (int item = blockIdx.x; item < n_trail + n_t; item += gridDim.x) {
+      int bi, bj;
+      bool trail = item < n_trail;
+      if (trail) {
+        // item 0 is the diagonal tile (kb+1, kb+1); then the rest row by row.
+        int q = item, row = 0;
+        while (q > row) {
+          q -= row + 1;
+          ++row;
+        }
+        bi = kb + 1 + row;
+        bj = kb + 1 + q;
+      } else {
+        const int q = item - n_trail;
+        bi = kb + 1 + q / (kb + 1);
+        bj = q % (kb + 1);
+      }
+      __syncthreads();
+      // s0 = L rows of block bi (panel of block kb); s1 = L rows of block bj or X row block kb.
+      for (int r = ty; r < kCB; r += 8) {
+        const int64_t ri = (int64_t)bi * kCB + r;
+        s0[r][tx] = (ri < l && tx < nb) ? a.g[ri * l + k0 + tx] : 0.0;
+        if (trail) {
+          const int64_t rj = (int64_t)bj * kCB + r;
+          s1[r][tx] = (rj < l && tx < nb) ? a.g[rj * l + k0 + tx] : 0.0;
+        } else {
+          s1[r][tx] = (r < nb) ? a.X[(int64_t)(k0 + r) * l + bj * kCB + tx] : 0.0;
+        }
+      }
+      __syncthreads();
+      const int64_t col = (int64_t)bj * kCB + tx;
+      for (int r = ty; r < kCB; r += 8) {
+        const int64_t row = (int64_t)bi * kCB + r;
+        if (row >= l || col >= l) continue;
+        double acc = 0.0;
+        if (trail) {
+#pragma unroll 8
+          for (int e = 0; e < kCB; ++e) acc = fma(s0[r][e], s1[tx][e], acc);
+          a.g[row * l + col] -= acc;
+        } else {
+#pragma unroll 8
+          for (int e = 0; e < kCB; ++e) acc = fma(s0[r][e], s1[e][tx], acc);
+          a.T[row * l + col] -= acc;
+        }
+      }
+      if (item == 0) {
+        __syncthreads();
+        ci_factor_diag(a, kb + 1, s0, s1, dinv, rdiag, red);
+      }
+    }
+    grid.sync();
+  }
+  // Outputs: zero the upper triangle of g, LT = L^T, Rinv = X^T.
+  grid.sync();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + tid; e < ll; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / l, j = e % l;  // element (i, j) of the outputs
+    if (j > i) a.g[e] = 0.0;
+    a.LT[e] = (j >= i) ? a.g[j * l + i] : 0.0;
+    a.Rinv[e] = (j >= i) ? a.X[j * l + i] : 0.0;
+  }
+}
+
+int chol_inv(const Dla& d, double* g, double* LT, double* Rinv, double* T, double* X, int64_t l) {
+  if (l <= 0) return BSRHT_OK;
+  CholInvArgs a{g, LT, Rinv, T, X, (int)l, (int)((l + kCB - 1) / kCB), d.status};
+  int occ = 0;
+  BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chol_inv, 256, 0));
+  const int blocks = num_sms() * std::max(1, std::min(occ, 1));
+  void* args[] = {&a};
+  BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_chol_inv, dim3(blocks), dim3(256), args, 0, d.s));
+  note_launches(1);
+  return BSRHT_OK;
+}
+
 // ------------------------------------------------------- Jacobi SVD
 __device__ __forceinline__ int rr_player(int pos, int round, int lp) {
   if (pos == 0) return 0;

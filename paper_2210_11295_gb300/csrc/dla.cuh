@@ -62,6 +62,12 @@ int cholesky(const Dla& d, double* g, int64_t l);
 // L; LT receives L^T (the upper Cholesky factor R = L^T).
 int tri_inverse(const Dla& d, const double* L, double* LT, double* Rinv, int64_t l);
 
+// cholesky followed by tri_inverse in one cooperative kernel: L in the lower
+// triangle of g (upper zeroed), LT = L^T, Rinv = L^-T; T and X are l x l
+// FP64 scratch.  Sets *status |= kStatusNotPD on a non-positive pivot (the
+// outputs are then meaningless).
+int chol_inv(const Dla& d, double* g, double* LT, double* Rinv, double* T, double* X, int64_t l);
+
 // One-sided Jacobi SVD of the l x l FP64 matrix given by its COLUMNS:
 // colsM[c*l + i] = M[i][c].  On return colsM holds U Sigma (columns),
 // colsV[c*l + i] = V[i][c]; sigma[c] = ||U Sigma e_c||.  Columns are sorted
@@ -82,7 +88,8 @@ int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const floa
             const void* B, int64_t ldb, bool b_kmajor, DT tc_out, void* C, int64_t ldc, bool gram);
 bool gemm_tc_eligible(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda);
 // Bt (N x ldk, FP32) = B^T for B K x N (FP32 or FP64, ldb); Bt[:, K:ldk] = 0.
-int transpose_to_f32(const Dla& d, DT tb, const void* B, int64_t K, int64_t N, int64_t ldb, float* Bt, int64_t ldk);
+int transpose_to_f32(const Dla& d, DT tb, const void* B, int64_t K, int64_t N, int64_t ldb, float* Bt, int64_t ldk,
+                     float* Blo = nullptr);
 
 // Householder QR of the tall FP64 X (rows x l, rows >= l), X overwritten by
 // the reflectors; Q (rows x l, orthonormal columns) is formed explicitly.

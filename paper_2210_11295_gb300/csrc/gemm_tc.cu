@@ -16,10 +16,12 @@ namespace bsrht {
 namespace {
 
 // Bt[n][k] = B[k][n] in FP32 (B is K x N, FP32 or FP64, leading dimension
-// ldb); columns k in [K, ldk) are zero.
+// ldb); columns k in [K, ldk) are zero.  With Blo != nullptr also
+// Blo[n][k] = Bt[n][k] - (Bt[n][k] with the low 13 mantissa bits cleared),
+// the lo part of the TF32 split.
 template <typename TB>
 __global__ void k_transpose_f32(const TB* __restrict__ B, int64_t K, int64_t N, int64_t ldb, float* __restrict__ Bt,
-                                int64_t ldk) {
+                                int64_t ldk, float* __restrict__ Blo) {
   __shared__ float tile[32][33];
   const int64_t k0 = (int64_t)blockIdx.x * 32, nb = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
@@ -30,7 +32,11 @@ __global__ void k_transpose_f32(const TB* __restrict__ B, int64_t K, int64_t N, 
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
     const int64_t n = nb + r, k = k0 + tx;
-    if (n < N && k < ldk) Bt[n * ldk + k] = tile[tx][r];
+    if (n < N && k < ldk) {
+      const float x = tile[tx][r];
+      Bt[n * ldk + k] = x;
+      if (Blo) Blo[n * ldk + k] = x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+    }
   }
 }
 
@@ -52,11 +58,13 @@ __global__ void k_tc_reduce(const float* __restrict__ P, TC* __restrict__ C, int
   C[i * ldc + j] = (TC)s;
 }
 
-template <typename TC>
-int launch_tc(const Dla& d, const CUtensorMap& ma, const CUtensorMap& mb, tc::GemmTcArgs g, dim3 grid) {
+template <typename TC, bool PRE>
+int launch_tc(const Dla& d, const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mblo, tc::GemmTcArgs g,
+              dim3 grid) {
   const size_t smem = tc::smem_bytes();
-  BSRHT_CUDA_TRY(cudaFuncSetAttribute(tc::k_gemm_tf32x3<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  tc::k_gemm_tf32x3<TC><<<grid, tc::THREADS, smem, d.s>>>(ma, mb, g);
+  BSRHT_CUDA_TRY(
+      cudaFuncSetAttribute(tc::k_gemm_tf32x3<TC, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  tc::k_gemm_tf32x3<TC, PRE><<<grid, tc::THREADS, smem, d.s>>>(ma, mb, mblo, g);
   BSRHT_CUDA_TRY(cudaGetLastError());
   return BSRHT_OK;
 }
@@ -67,12 +75,13 @@ bool gemm_tc_eligible(int64_t M, int64_t N, int64_t K, const void* A, int64_t ld
   return M >= 1 && N >= 1 && K >= 8 && (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0;
 }
 
-int transpose_to_f32(const Dla& d, DT tb, const void* B, int64_t K, int64_t N, int64_t ldb, float* Bt, int64_t ldk) {
+int transpose_to_f32(const Dla& d, DT tb, const void* B, int64_t K, int64_t N, int64_t ldb, float* Bt, int64_t ldk,
+                     float* Blo) {
   dim3 g((unsigned)((ldk + 31) / 32), (unsigned)((N + 31) / 32));
   if (tb == DT::F32)
-    k_transpose_f32<float><<<g, 256, 0, d.s>>>(static_cast<const float*>(B), K, N, ldb, Bt, ldk);
+    k_transpose_f32<float><<<g, 256, 0, d.s>>>(static_cast<const float*>(B), K, N, ldb, Bt, ldk, Blo);
   else if (tb == DT::F64)
-    k_transpose_f32<double><<<g, 256, 0, d.s>>>(static_cast<const double*>(B), K, N, ldb, Bt, ldk);
+    k_transpose_f32<double><<<g, 256, 0, d.s>>>(static_cast<const double*>(B), K, N, ldb, Bt, ldk, Blo);
   else
     return BSRHT_EUNSUP;
   BSRHT_CUDA_TRY(cudaGetLastError());
@@ -85,13 +94,16 @@ int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const floa
   if (M <= 0 || N <= 0) return BSRHT_OK;
   if (tc_out != DT::F32 && tc_out != DT::F64) return BSRHT_EUNSUP;
   const float* Bt = static_cast<const float*>(B);
+  const float* Btlo = nullptr;
   int64_t ldk = ldb;
   if (!b_kmajor) {
     ldk = (K + 3) / 4 * 4;
     float* bt = static_cast<float*>(ar.take(sizeof(float) * (size_t)N * ldk));
+    float* btlo = static_cast<float*>(ar.take(sizeof(float) * (size_t)N * ldk));
     if (!ar.ok()) return BSRHT_ENOMEM;
-    if (!ar.measure) TRY_TC(transpose_to_f32(d, tb, B, K, N, ldb, bt, ldk));
+    if (!ar.measure) TRY_TC(transpose_to_f32(d, tb, B, K, N, ldb, bt, ldk, btlo));
     Bt = bt;
+    Btlo = btlo;
   } else if (tb != DT::F32 || (ldk % 4) != 0) {
     return BSRHT_EUNSUP;
   }
@@ -116,17 +128,26 @@ int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const floa
   int* err = static_cast<int*>(ar.take(256));
   if (!ar.ok()) return BSRHT_ENOMEM;
   if (ar.measure) return BSRHT_OK;
-  CUtensorMap ma, mb;
+  CUtensorMap ma, mb, mblo;
   if (!make_tensor_map_2d(&ma, A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)M, (uint64_t)K, (uint64_t)lda, tc::BK,
                           tc::BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
       !make_tensor_map_2d(&mb, Bt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)N, (uint64_t)K, (uint64_t)ldk, tc::BK,
                           tc::BN, CU_TENSOR_MAP_SWIZZLE_128B))
     return BSRHT_EUNSUP;
+  const bool pre = Btlo != nullptr;
+  mblo = mb;
+  if (pre && !make_tensor_map_2d(&mblo, Btlo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)N, (uint64_t)K,
+                                 (uint64_t)ldk, tc::BK, tc::BN, CU_TENSOR_MAP_SWIZZLE_128B))
+    return BSRHT_EUNSUP;
   BSRHT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), d.s));
   if (tm * tn > 0x7FFFFFFF) return BSRHT_EUNSUP;
   dim3 grid((unsigned)(tm * tn), 1u, (unsigned)splits);
   tc::GemmTcArgs g{M, N, K, splits > 1 ? (void*)P : C, ldc, gram ? 1 : 0, err};
-  int st = (tc_out == DT::F32 || splits > 1) ? launch_tc<float>(d, ma, mb, g, grid) : launch_tc<double>(d, ma, mb, g, grid);
+  const bool f32_out = tc_out == DT::F32 || splits > 1;
+  int st = pre ? (f32_out ? launch_tc<float, true>(d, ma, mb, mblo, g, grid)
+                          : launch_tc<double, true>(d, ma, mb, mblo, g, grid))
+               : (f32_out ? launch_tc<float, false>(d, ma, mb, mblo, g, grid)
+                          : launch_tc<double, false>(d, ma, mb, mblo, g, grid));
   if (st != BSRHT_OK) return st;
   int launches = 1;
   if (splits > 1) {

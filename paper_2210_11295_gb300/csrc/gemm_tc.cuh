@@ -17,6 +17,12 @@
 // fresh TMEM buffer (two buffers, ping-pong) and the epilogue warps add it
 // into an FP32 running sum held in registers, rounding to nearest.
 //
+// The small right-hand operand of a tall product (B given K x N) is split
+// once in global memory while it is transposed, and both halves come in by
+// TMA; only the Gram product, whose B is the tall matrix itself, splits B
+// in shared memory too.  (Shared-memory bandwidth, shared by the split and
+// the MMA operand reads, is what bounds this kernel.)
+//
 // CTA: 256 threads.  Warp 0 allocates TMEM and issues the TMA loads (one
 // thread), warp 1 issues the MMAs (one thread), warps 4-7 split the tiles,
 // fold the finished K blocks (tcgen05.ld of their 32 TMEM lanes) and store
@@ -133,9 +139,13 @@ __device__ __forceinline__ void split_tf32(const uint4* __restrict__ hi, uint4* 
   }
 }
 
-template <typename TC>
+// PRE: B arrives already split (mapB its FP32 values, mapBlo the lo parts,
+// both by TMA), and the epilogue warps split only the A tile; without PRE
+// they split both tiles in shared memory.
+template <typename TC, bool PRE>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_gemm_tf32x3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, GemmTcArgs g) {
+    k_gemm_tf32x3(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  const __grid_constant__ CUtensorMap mapBlo, GemmTcArgs g) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(smem_raw) & 1023)) & 1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
@@ -186,10 +196,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         unsigned char* st = base + (size_t)s * STAGE_BYTES;
-        mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
+        mbar_arrive_expect_tx(&full[s], A_BYTES + (PRE ? 2 : 1) * B_BYTES);
         const int32_t kx = (kb0 + kb) * BK;
         tma_load_2d(st, &mapA, &full[s], kx, (int32_t)m0);
         tma_load_2d(st + 2 * A_BYTES, &mapB, &full[s], kx, (int32_t)n0);
+        if (PRE) tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mapBlo, &full[s], kx, (int32_t)n0);
         issued = kb + 1;
       }
       if (failed) {
@@ -269,8 +280,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       unsigned char* st = base + (size_t)s * STAGE_BYTES;
       split_tf32(reinterpret_cast<uint4*>(st), reinterpret_cast<uint4*>(st + A_BYTES), t, (int)(A_BYTES / 16));
-      split_tf32(reinterpret_cast<uint4*>(st + 2 * A_BYTES), reinterpret_cast<uint4*>(st + 2 * A_BYTES + B_BYTES), t,
-                 (int)(B_BYTES / 16));
+      if (!PRE)
+        split_tf32(reinterpret_cast<uint4*>(st + 2 * A_BYTES), reinterpret_cast<uint4*>(st + 2 * A_BYTES + B_BYTES),
+                   t, (int)(B_BYTES / 16));
       fence_proxy_async_smem();
       mbar_arrive(&ready[s]);
       if (kb > 0 && !fold(kb - 1)) failed = true;

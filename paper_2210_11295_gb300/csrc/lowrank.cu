@@ -174,9 +174,10 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
   if (Rinv_out) *Rinv_out = nullptr;
   // ---- fast path: CholeskyQR2 (Z serves as scratch for the transposed Grams)
   bool fast = true;
+  // (b.Ug and b.Vg, used only by the fallback, are the scratch of chol_inv.)
   TRY(tall_gram(d, ar, dry, tc, X, rows, l, Z, b.G));
   if (!dry) {
-    TRY(cholesky(d, b.G, l));
+    TRY(chol_inv(d, b.G, b.LT1, b.Rinv, b.Ug, b.Vg, l));
     int hs = 0;
     TRY(read_status(d, &hs));
     if (hs) {
@@ -185,14 +186,11 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
     }
   }
   if (fast || dry) {
-    if (!dry) {
-      TRY(tri_inverse(d, b.G, b.LT1, b.Rinv, l));
-      if (tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
-    }
+    if (!dry && tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
     TRY(tall_gemm(d, ar, tc, tc, tc, rows, l, l, X, l, b.Rinv, RinvB, l, Y, l, true));
     TRY(tall_gram(d, ar, dry, tc, Y, rows, l, Z, b.G));
     if (!dry) {
-      TRY(cholesky(d, b.G, l));
+      TRY(chol_inv(d, b.G, b.LT2, b.Rinv, b.Ug, b.Vg, l));
       int hs = 0;
       TRY(read_status(d, &hs));
       if (hs) {
@@ -201,10 +199,7 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
       }
     }
     if (fast || dry) {
-      if (!dry) {
-        TRY(tri_inverse(d, b.G, b.LT2, b.Rinv, l));
-        if (tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
-      }
+      if (!dry && tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
       void* dst = keep_x ? Z : X;
       if (Rinv_out) {
         *Rinv_out = b.Rinv;
@@ -267,11 +262,10 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
     void* dst = pass == 0 ? Z : Y;
     TRY(gemm_c(d, ar, tc, tc, DT::F64, l, l, rows, src, l, true, src, l, b.G, l, false, true));
     if (!dry) {
-      TRY(cholesky(d, b.G, l));
+      TRY(chol_inv(d, b.G, b.LT1, b.Rinv, b.Ug, b.Vg, l));
       int hs = 0;
       TRY(read_status(d, &hs));
       if (hs) return BSRHT_ENOTPD;
-      TRY(tri_inverse(d, b.G, b.LT1, b.Rinv, l));
       if (tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
     }
     TRY(gemm_c(d, ar, tc, tc, tc, rows, l, l, src, l, false, RinvB, l, dst, l, true, false));
@@ -550,7 +544,7 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
     TRY(sketch_run(sp_y, Y64, seed, R, l, sk_ws, d.s));
     k_symmetrize<double><<<(unsigned)((l * l + 255) / 256), 256, 0, d.s>>>(R, G, l);
     BSRHT_CUDA_TRY(cudaGetLastError());
-    TRY(cholesky(d, G, l));
+    TRY(chol_inv(d, G, LT1, Cinv, ob.Ug, ob.Vg, l));  // C^-1 = L^-T, used unless the eig path is taken
     k_pivot_ratio<<<1, 256, 0, d.s>>>(G, l, pr);
     BSRHT_CUDA_TRY(cudaGetLastError());
     note_launches(3);
@@ -570,10 +564,7 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
   if (tc == DT::F32) Ynu = B;
   void* Z = Y;
   if (!use_eig || dry) {
-    if (!dry) {
-      TRY(tri_inverse(d, G, LT1, Cinv, l));
-      if (tc == DT::F32) TRY(cast_copy(d, DT::F64, Cinv, DT::F32, Cinv_c, l * l));
-    }
+    if (!dry && tc == DT::F32) TRY(cast_copy(d, DT::F64, Cinv, DT::F32, Cinv_c, l * l));
     TRY(tall_gemm(d, ar, tc, tc, tc, n, l, l, Ynu, l, Cinv, tc == DT::F32 ? Cinv_c : (const void*)Cinv, l, Z, l,
                   true));
   }
