@@ -296,34 +296,34 @@ struct CholInvArgs {
   int* status;
 };
 
-// 1/sqrt(p) and sqrt(p) for a pivot p > 0: FP32 seed on p scaled by an even
-// power of two into [1, 4), then two Newton steps y <- y (3/2 - p y^2 / 2)
-// (relative error 2^-23 -> 2^-45 -> rounding); a dependent chain of about
-// ten FP64 operations instead of a square root and a division.
-__device__ __forceinline__ void ci_pivot(double p, double& r, double& y) {
-  if (p > 0x1.0p-1000 && p < 0x1.0p1000) {
-    const long long bits = __double_as_longlong(p);
-    const int e = (int)((bits >> 52) & 0x7FF) - 1023;  // p = f 2^e, f in [1, 2)
-    const int k = e >> 1;                               // floor(e / 2)
-    const double m = __longlong_as_double(bits - ((long long)(2 * k) << 52));  // p 2^-2k in [1, 4)
-    const double hm = -0.5 * m;
-    double y0 = (double)rsqrtf((float)m);
-    y0 = y0 * fma(hm * y0, y0, 1.5);
-    y0 = y0 * fma(hm * y0, y0, 1.5);
-    y = y0 * __longlong_as_double((long long)(1023 - k) << 52);  // times 2^-k
-    r = p * y;
-  } else {
-    r = sqrt(p);
-    y = 1.0 / r;
+// 1/d for a pivot d > 0: FP32 seed on d scaled by a power of two into
+// [1, 2), then two Newton steps y <- y + y (1 - d y) (relative error 2^-23 ->
+// 2^-46 -> rounding).  A dependent FP64 operation costs about 60 cycles on
+// this GPU (measured), so this chain of six is what one column of the
+// diagonal factorisation waits for.
+__device__ __forceinline__ double ci_rcp(double d) {
+  if (d > 0x1.0p-1000 && d < 0x1.0p1000) {
+    const long long bits = __double_as_longlong(d);
+    const int e = (int)((bits >> 52) & 0x7FF) - 1023;                       // d = f 2^e, f in [1, 2)
+    const double f = __longlong_as_double(bits - ((long long)e << 52));     // f in [1, 2)
+    double y = (double)__frcp_rn((float)f);
+    y = fma(y, fma(-f, y, 1.0), y);
+    y = fma(y, fma(-f, y, 1.0), y);
+    return y * __longlong_as_double((long long)(1023 - e) << 52);          // times 2^-e
   }
+  return 1.0 / d;
 }
 
-// (a): factor the diagonal block kb (already updated) and invert it.  The
-// block lives on one SM, whose FP64 rate bounds this step, so the trailing
-// update of a column enumerates only the lower-triangle entries (no idle
-// lanes on masked-out entries).
-__device__ void ci_factor_diag(const CholInvArgs& a, int kb, double (*s)[kCB + 1], double (*xi)[kCB + 1],
-                               double* dinv, double* rdiag, double (*red)[kCB]) {
+// (a): factor the diagonal block kb (already updated), G_kk = L D L^T with
+// unit lower L, and form its inverse alongside: the eliminations of column j
+// (row i -= l_ij row j, l_ij = s_ij / d_j) are applied to the trailing part
+// of s and to an identity block t, which ends as L^-1.  Thread 0 applies
+// column j's elimination to the next pivot first and forms its reciprocal
+// while threads 1..255 apply the rest, so one barrier per column; the
+// square roots come at the end, all at once: L_kk = L D^1/2 and
+// X_kk = L_kk^-1 = D^-1/2 L^-1.
+__device__ void ci_factor_diag(const CholInvArgs& a, int kb, double (*s)[kCB + 1], double (*t)[kCB + 1],
+                               double* dinv, double* dd) {
   const int tid = threadIdx.x, l = a.l, k0 = kb * kCB;
   const int nb = min(kCB, l - k0);
   for (int e = tid; e < kCB * kCB; e += blockDim.x) {
@@ -331,57 +331,67 @@ __device__ void ci_factor_diag(const CholInvArgs& a, int kb, double (*s)[kCB + 1
     double v = (i == j) ? 1.0 : 0.0;
     if (i < nb && j < nb && j <= i) v = a.g[(int64_t)(k0 + i) * l + k0 + j];
     s[i][j] = v;
-  }
-  for (int j = 0; j < kCB; ++j) {
-    __syncthreads();
-    if (tid == 0) {
-      double p = s[j][j];
-      if (!(p > 0.0)) {
-        atomicOr(a.status, kStatusNotPD);
-        p = 1.0;
-      }
-      double r, y;
-      ci_pivot(p, r, y);
-      s[j][j] = r;
-      rdiag[j] = r;
-      dinv[j] = y;
-    }
-    __syncthreads();
-    if (tid > j && tid < kCB) s[tid][j] *= dinv[j];
-    __syncthreads();
-    // Entries (i, c) with j < c <= i: item e -> row offset u with
-    // u (u + 1) / 2 <= e < (u + 1) (u + 2) / 2.
-    const int rem = kCB - 1 - j;
-    const int items = rem * (rem + 1) / 2;
-    for (int e = tid; e < items; e += blockDim.x) {
-      int u = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-      while ((u + 1) * (u + 2) / 2 <= e) ++u;
-      while (u * (u + 1) / 2 > e) --u;
-      const int i = j + 1 + u, c = j + 1 + (e - u * (u + 1) / 2);
-      s[i][c] -= s[i][j] * s[c][j];
-    }
+    t[i][j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  // X_kk = L_kk^-1 row by row: X[i][c] = (delta_ic - sum_{c<=k<i} L[i][k] X[k][c]) / L[i][i];
-  // lane = column c, the eight warps split the sum over k.
-  const int lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-  for (int i = 0; i < kCB; ++i) {
-    double part = 0.0;
-    for (int k = lane + w; k < i; k += nw)  // k >= c = lane
-      part = fma(s[i][k], xi[k][lane], part);
-    red[w][lane] = part;
-    __syncthreads();
-    if (w == 0) {
-      double sum = 0.0;
-      for (int u = 0; u < nw; ++u) sum += red[u][lane];
-      xi[i][lane] = (lane <= i) ? ((i == lane ? 1.0 : 0.0) - sum) * dinv[i] : 0.0;
+  if (tid == 0) {
+    double p = s[0][0];
+    if (!(p > 0.0)) {
+      atomicOr(a.status, kStatusNotPD);
+      p = 1.0;
+    }
+    dd[0] = p;
+    dinv[0] = ci_rcp(p);
+  }
+  __syncthreads();
+  for (int j = 0; j < kCB; ++j) {
+    const double ij = dinv[j];
+    if (tid == 0) {
+      if (j + 1 < kCB) {
+        const double x = s[j + 1][j];
+        double p = fma(-x * ij, x, s[j + 1][j + 1]);
+        if (!(p > 0.0)) {
+          atomicOr(a.status, kStatusNotPD);
+          p = 1.0;
+        }
+        dd[j + 1] = p;
+        dinv[j + 1] = ci_rcp(p);
+      }
+    } else {
+      // Trailing entries (i, c), j < c <= i, except the next pivot; item e ->
+      // row offset u with u (u + 1) / 2 <= e < (u + 1) (u + 2) / 2.  Then the
+      // entries (i, c), i > j, c <= j of t.
+      const int rem = kCB - 1 - j;
+      const int n_tr = rem * (rem + 1) / 2;
+      const int n_items = n_tr + rem * (j + 1);
+      for (int e = tid - 1; e < n_items; e += blockDim.x - 1) {
+        if (e < n_tr) {
+          if (e == 0) continue;  // (j+1, j+1): thread 0
+          int u = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+          while ((u + 1) * (u + 2) / 2 <= e) ++u;
+          while (u * (u + 1) / 2 > e) --u;
+          const int i = j + 1 + u, c = j + 1 + (e - u * (u + 1) / 2);
+          s[i][c] = fma(-s[i][j] * ij, s[c][j], s[i][c]);
+        } else {
+          const int q = e - n_tr, i = j + 1 + q / (j + 1), c = q % (j + 1);
+          t[i][c] = fma(-s[i][j] * ij, t[j][c], t[i][c]);
+        }
+      }
     }
     __syncthreads();
   }
+  // D^1/2: sqrt(d_j) and 1/sqrt(d_j), all columns at once.
+  if (tid < kCB) {
+    const double r = sqrt(dd[tid]);
+    dd[tid] = r;
+    dinv[tid] = 1.0 / r;
+  }
+  __syncthreads();
   for (int e = tid; e < nb * nb; e += blockDim.x) {
     const int i = e / nb, j = e % nb;
-    a.g[(int64_t)(k0 + i) * l + k0 + j] = (j <= i) ? s[i][j] : 0.0;
-    a.X[(int64_t)(k0 + i) * l + k0 + j] = xi[i][j];
+    // L_kk[i][j] = (s_ij / d_j) sqrt(d_j) = s_ij / sqrt(d_j);  X_kk[i][j] = t_ij / sqrt(d_i).
+    a.g[(int64_t)(k0 + i) * l + k0 + j] = (j < i) ? s[i][j] * dinv[j] : (i == j ? dd[j] : 0.0);
+    a.X[(int64_t)(k0 + i) * l + k0 + j] = (j <= i) ? t[i][j] * dinv[i] : 0.0;
   }
 }
 
@@ -390,15 +400,14 @@ __global__ void __launch_bounds__(256) k_chol_inv(CholInvArgs a) {
   __shared__ double s0[kCB][kCB + 1];
   __shared__ double s1[kCB][kCB + 1];
   __shared__ double dinv[kCB];
-  __shared__ double rdiag[kCB];
-  __shared__ double red[8][kCB];
+  __shared__ double dd[kCB];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int l = a.l, nblk = a.nblk;
   const int64_t ll = (int64_t)l * l;
   // T = I (only its lower block triangle is ever read).
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + tid; e < ll; e += (int64_t)gridDim.x * blockDim.x)
     a.T[e] = (e / l == e % l) ? 1.0 : 0.0;
-  if (blockIdx.x == 0) ci_factor_diag(a, 0, s0, s1, dinv, rdiag, red);
+  if (blockIdx.x == 0) ci_factor_diag(a, 0, s0, s1, dinv, dd);
   grid.sync();
   const int gw = blockIdx.x * (blockDim.x >> 5) + w, nwg = gridDim.x * (blockDim.x >> 5);
   for (int kb = 0; kb < nblk; ++kb) {
@@ -481,7 +490,7 @@ __global__ void __launch_bounds__(256) k_chol_inv(CholInvArgs a) {
       }
       if (item == 0) {
         __syncthreads();
-        ci_factor_diag(a, kb + 1, s0, s1, dinv, rdiag, red);
+        ci_factor_diag(a, kb + 1, s0, s1, dinv, dd);
       }
     }
     grid.sync();
