@@ -786,6 +786,214 @@ int launch_jacobi(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, double tol, d
     return launch_jacobi_wp<T, 2>(d, cols, Vc, nrm, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot, status);
 }
 
+// Block one-sided Jacobi (FP32 phase of the mixed SVD).  The columns are cut
+// into nblk blocks of B (the last ones padded with absent columns); CTA c
+// holds the block pair of round-robin position c in shared memory (M and V
+// columns), so a grid barrier is needed only between block rounds.  In the
+// first block round of a sweep the pairs inside each of the two blocks are
+// treated (B - 1 rounds of round-robin), in every block round the B x B cross
+// pairs (B rounds, warp w pairs column w of the first block with column
+// (w + r) mod B of the second): over a sweep every pair of columns is
+// rotated exactly once, as in the scalar kernel, with the same rotation and
+// stopping rules.  Column norms are formed exactly when a block pair is
+// loaded and carried through the rotations in between.
+template <int B, int JR>
+__global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, float* __restrict__ V, int l, int nblk,
+                                                       double tol, double tol_stop, const double* __restrict__ fnorm,
+                                                       double tiny_rel, int max_sweeps,
+                                                       int* __restrict__ rot_counts) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ float jsm[];
+  float* Ms = jsm;
+  float* Vs = jsm + (size_t)2 * B * l;
+  float* nrm = Vs + (size_t)2 * B * l;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float ttol = (float)tol, tstop = (float)tol_stop;
+  const double tiny = tiny_rel * fnorm[0];
+  const float tiny2 = (float)(tiny * tiny);
+  auto gcol = [&](int P, int Q, int j) { return j < B ? P * B + j : Q * B + (j - B); };
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int R = 0; R < nblk - 1; ++R) {
+      const int P = rr_player(blockIdx.x, R, nblk), Q = rr_player(nblk - 1 - blockIdx.x, R, nblk);
+      // The B columns of a block are one contiguous run of B l floats (16-byte
+      // aligned: B is a multiple of 4); copy both runs with float4 accesses,
+      // all in flight at once.  Absent columns (>= l) read as zero.
+      for (int h = 0; h < 2; ++h) {
+        const int blk = h ? Q : P;
+        const int64_t valid = (int64_t)max(0, min(B, l - blk * B)) * l;  // floats present
+        const float4* gm = reinterpret_cast<const float4*>(M + (int64_t)blk * B * l);
+        const float4* gv = reinterpret_cast<const float4*>(V + (int64_t)blk * B * l);
+        float4* sm4 = reinterpret_cast<float4*>(Ms + (size_t)h * B * l);
+        float4* sv4 = reinterpret_cast<float4*>(Vs + (size_t)h * B * l);
+        const int n4 = B * l / 4;
+#pragma unroll 4
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+          float4 xm = make_float4(0.f, 0.f, 0.f, 0.f), xv = xm;
+          if (4 * (int64_t)i + 3 < valid) {
+            xm = gm[i];
+            xv = gv[i];
+          } else if (4 * (int64_t)i < valid) {
+            const float* m1 = reinterpret_cast<const float*>(gm + i);
+            const float* v1 = reinterpret_cast<const float*>(gv + i);
+            const int64_t left = valid - 4 * (int64_t)i;
+            xm.x = m1[0]; xv.x = v1[0];
+            if (left > 1) { xm.y = m1[1]; xv.y = v1[1]; }
+            if (left > 2) { xm.z = m1[2]; xv.z = v1[2]; }
+          }
+          sm4[i] = xm;
+          sv4[i] = xv;
+        }
+      }
+      __syncthreads();
+      for (int j = w; j < 2 * B; j += B) {
+        const float* col = Ms + (size_t)j * l;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int r = lane;
+        for (; r + 96 < l; r += 128) {
+          s0 = fmaf(col[r], col[r], s0);
+          s1 = fmaf(col[r + 32], col[r + 32], s1);
+          s2 = fmaf(col[r + 64], col[r + 64], s2);
+          s3 = fmaf(col[r + 96], col[r + 96], s3);
+        }
+        for (; r < l; r += 32) s0 = fmaf(col[r], col[r], s0);
+        const float sq = warp_sum((s0 + s1) + (s2 + s3));
+        if (lane == 0) nrm[j] = sq;
+      }
+      __syncthreads();
+      const int nr = (R == 0 ? B - 1 : 0) + B;
+      for (int ir = 0; ir < nr; ++ir) {
+        int p, q;
+        if (R == 0 && ir < B - 1) {  // inside block 0 (warps 0..B/2-1) or block 1
+          const int half = w / (B / 2), k = w % (B / 2);
+          p = half * B + rr_player(k, ir, B);
+          q = half * B + rr_player(B - 1 - k, ir, B);
+        } else {
+          const int cr = ir - (R == 0 ? B - 1 : 0);
+          p = w;
+          q = B + (w + cr) % B;
+        }
+        const int gp = gcol(P, Q, p), gq = gcol(P, Q, q);
+        float* a = Ms + (size_t)p * l;
+        float* b = Ms + (size_t)q * l;
+        float* va = Vs + (size_t)p * l;
+        float* vb = Vs + (size_t)q * l;
+        const float alpha = nrm[p], beta = nrm[q];
+        bool skip = gp >= l || gq >= l || (alpha <= tiny2 && beta <= tiny2);
+        if (!skip) {
+          // The warp's two columns of M and of V in registers (JR values per
+          // lane; rows lane + 32 e), loaded back to back.
+          float x[JR], y[JR], vx[JR], vy[JR];
+#pragma unroll
+          for (int e = 0; e < JR; ++e) {
+            const int r = lane + 32 * e;
+            const bool in = r < l;
+            x[e] = in ? a[r] : 0.f;
+            y[e] = in ? b[r] : 0.f;
+            vx[e] = in ? va[r] : 0.f;
+            vy[e] = in ? vb[r] : 0.f;
+          }
+          float g4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int e = 0; e < JR; ++e) g4[e & 3] = fmaf(x[e], y[e], g4[e & 3]);
+          const float gamma = warp_sum((g4[0] + g4[1]) + (g4[2] + g4[3]));
+          const float gnorm = sqrtf(alpha) * sqrtf(beta);
+          if (gamma != 0.f && fabsf(gamma) > ttol * gnorm) {
+            const float t = jac_tangent(alpha, beta, gamma);
+            const float c = rsqrtf(1.f + t * t), s = c * t;
+#pragma unroll
+            for (int e = 0; e < JR; ++e) {
+              const int r = lane + 32 * e;
+              if (r < l) {
+                a[r] = c * x[e] - s * y[e];
+                b[r] = s * x[e] + c * y[e];
+                va[r] = c * vx[e] - s * vy[e];
+                vb[r] = s * vx[e] + c * vy[e];
+              }
+            }
+            if (lane == 0) {
+              nrm[p] = alpha - t * gamma;
+              nrm[q] = beta + t * gamma;
+              if (fabsf(gamma) > tstop * gnorm) atomicAdd(&rot_counts[sweep], 1);
+            }
+          }
+        }
+        __syncthreads();
+      }
+      for (int h = 0; h < 2; ++h) {
+        const int blk = h ? Q : P;
+        const int64_t valid = (int64_t)max(0, min(B, l - blk * B)) * l;
+        float4* gm = reinterpret_cast<float4*>(M + (int64_t)blk * B * l);
+        float4* gv = reinterpret_cast<float4*>(V + (int64_t)blk * B * l);
+        const float4* sm4 = reinterpret_cast<const float4*>(Ms + (size_t)h * B * l);
+        const float4* sv4 = reinterpret_cast<const float4*>(Vs + (size_t)h * B * l);
+        const int n4 = B * l / 4;
+#pragma unroll 4
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+          if (4 * (int64_t)i + 3 < valid) {
+            gm[i] = sm4[i];
+            gv[i] = sv4[i];
+          } else if (4 * (int64_t)i < valid) {
+            float* m1 = reinterpret_cast<float*>(gm + i);
+            float* v1 = reinterpret_cast<float*>(gv + i);
+            const float4 xm = sm4[i], xv = sv4[i];
+            const int64_t left = valid - 4 * (int64_t)i;
+            m1[0] = xm.x; v1[0] = xv.x;
+            if (left > 1) { m1[1] = xm.y; v1[1] = xv.y; }
+            if (left > 2) { m1[2] = xm.z; v1[2] = xv.z; }
+          }
+        }
+      }
+      grid.sync();
+    }
+    if (*((volatile int*)&rot_counts[sweep]) == 0) break;
+  }
+}
+
+template <int B, int JR>
+int launch_jacobi_blk_b(const Dla& d, float* M, float* V, int64_t l, double tol, double tol_stop,
+                        const double* fnorm, double tiny_rel, int max_sweeps, int* rot) {
+  int li = (int)l, nblk = (int)((l + B - 1) / B), msw = max_sweeps;
+  nblk += nblk & 1;
+  const size_t smem = sizeof(float) * ((size_t)4 * B * l + 2 * B);
+  BSRHT_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_blk<B, JR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_blk<B, JR>, 32 * B, smem));
+  if ((int64_t)(nblk / 2) > (int64_t)occ * num_sms()) return BSRHT_EUNSUP;  // not co-resident: caller falls back
+  void* args[] = {&M, &V, &li, &nblk, &tol, &tol_stop, &fnorm, &tiny_rel, &msw, &rot};
+  BSRHT_CUDA_TRY(
+      cudaLaunchCooperativeKernel((void*)k_jacobi_blk<B, JR>, dim3(nblk / 2), dim3(32 * B), args, smem, d.s));
+  note_launches(1);
+  return BSRHT_OK;
+}
+
+template <int B>
+int launch_jacobi_blk_jr(const Dla& d, float* M, float* V, int64_t l, double tol, double tol_stop,
+                         const double* fnorm, double tiny_rel, int max_sweeps, int* rot) {
+  if (l <= 128) return launch_jacobi_blk_b<B, 4>(d, M, V, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot);
+  if (l <= 256) return launch_jacobi_blk_b<B, 8>(d, M, V, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot);
+  if (l <= 512) return launch_jacobi_blk_b<B, 16>(d, M, V, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot);
+  if constexpr (B <= 8) {
+    if (l <= 1024) return launch_jacobi_blk_b<B, 32>(d, M, V, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot);
+  }
+  return BSRHT_EUNSUP;
+}
+
+// Blocks of 8 columns, for l <= 512 only.  Only l / 16 CTAs work, and a
+// block round is bound by their instruction issue (ncu at l = 512, B = 16:
+// 43 % issue-active, about 460 warp instructions per warp and inner round),
+// so the block form wins only while the grid barriers it saves outweigh the
+// SMs it leaves idle: measured on GB300, FP32 phase at l = 512 10.9 ms
+// (B = 8) against 13.3 (B = 16) and 15.2 (scalar kernel), at l = 128 1.2
+// against 2.7 ms; at l = 600 and 1024 the scalar kernel is as fast or
+// faster.  BSRHT_EUNSUP sends the caller to the scalar kernel (also when the
+// block pairs cannot all be resident at once).
+int launch_jacobi_blk(const Dla& d, float* M, float* V, int64_t l, double tol, double tol_stop, const double* fnorm,
+                      double tiny_rel, int max_sweeps, int* rot) {
+  if (l <= 1 || l > 512) return BSRHT_EUNSUP;
+  return launch_jacobi_blk_jr<8>(d, M, V, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot);
+}
+
 }  // namespace
 
 int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout,
@@ -838,13 +1046,18 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
   double* cols = colsM;
   if (mixed) {
     // 1. FP32 one-sided Jacobi on a copy of M: V32 ~ the right singular
-    //    vectors to FP32 accuracy, at 64x the FP64 rate of this GPU.
+    //    vectors to FP32 accuracy, at 64x the FP64 rate of this GPU (block
+    //    Jacobi in shared memory: one grid barrier per block round).
     TRY_DLA(cast_copy(d, DT::F64, colsM, DT::F32, M32, l * l));
     k_init_identity_cols<float><<<blocks_for(l * l, 256), 256, 0, d.s>>>(V32, l);
     DLA_LAUNCH_CHECK();
     const double tol32 = 16.0 * std::sqrt((double)l) * 0x1.0p-24;
-    TRY_DLA(launch_jacobi<float>(d, M32, V32, nrm32, l, tol32, tol32, fnorm, (double)l * 0x1.0p-24, 20,
-                                 rot + max_sweeps, nullptr));
+    const int bst = launch_jacobi_blk(d, M32, V32, l, tol32, tol32, fnorm, (double)l * 0x1.0p-24, 20, rot + max_sweeps);
+    if (bst == BSRHT_EUNSUP)
+      TRY_DLA(launch_jacobi<float>(d, M32, V32, nrm32, l, tol32, tol32, fnorm, (double)l * 0x1.0p-24, 20,
+                                   rot + max_sweeps, nullptr));
+    else if (bst != BSRHT_OK)
+      return bst;
     trace_mark(d.s, "svd_jacobi_fp32");
     // 2. Make it orthogonal in FP64: with S = V0^T (the column storage),
     //    two Newton-Schulz steps S <- 1.5 S - 0.5 S (S^T S) take the
