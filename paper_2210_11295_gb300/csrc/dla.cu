@@ -626,10 +626,12 @@ __global__ void __launch_bounds__(32 * WP) k_jacobi(T* __restrict__ M, T* __rest
           vx[e] = in ? va[r] : (T)0;
           vy[e] = in ? vb[r] : (T)0;
         }
-        T ga = 0;
+        // Four independent partial sums: a dependent FP64 FMA costs about 60
+        // cycles on this GPU.
+        T g4[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int e = 0; e < JR; ++e) ga = fma(x[e], y[e], ga);
-        ga = warp_sum(ga);
+        for (int e = 0; e < JR; ++e) g4[e & 3] = fma(x[e], y[e], g4[e & 3]);
+        T ga = warp_sum((g4[0] + g4[1]) + (g4[2] + g4[3]));
         const T alpha = nrm[p], beta = nrm[q];  // read before thread 0 updates them
         if (WP > 1) {
           // Double-buffered: a warp can be one pair ahead, never two (the
