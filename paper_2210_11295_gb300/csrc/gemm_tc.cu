@@ -90,7 +90,7 @@ int transpose_to_f32(const Dla& d, DT tb, const void* B, int64_t K, int64_t N, i
 }
 
 int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, DT tb,
-            const void* B, int64_t ldb, bool b_kmajor, DT tc_out, void* C, int64_t ldc, bool gram) {
+            const void* B, int64_t ldb, bool b_kmajor, DT tc_out, void* C, int64_t ldc, bool gram, bool b_upper) {
   if (M <= 0 || N <= 0) return BSRHT_OK;
   if (tc_out != DT::F32 && tc_out != DT::F64) return BSRHT_EUNSUP;
   const float* Bt = static_cast<const float*>(B);
@@ -142,7 +142,7 @@ int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const floa
   BSRHT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), d.s));
   if (tm * tn > 0x7FFFFFFF) return BSRHT_EUNSUP;
   dim3 grid((unsigned)(tm * tn), 1u, (unsigned)splits);
-  tc::GemmTcArgs g{M, N, K, splits > 1 ? (void*)P : C, ldc, gram ? 1 : 0, err};
+  tc::GemmTcArgs g{M, N, K, splits > 1 ? (void*)P : C, ldc, gram ? 1 : 0, err, (b_upper && !gram) ? 1 : 0};
   const bool f32_out = tc_out == DT::F32 || splits > 1;
   int st = pre ? (f32_out ? launch_tc<float, true>(d, ma, mb, mblo, g, grid)
                           : launch_tc<double, true>(d, ma, mb, mblo, g, grid))

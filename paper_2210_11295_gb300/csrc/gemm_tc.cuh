@@ -118,6 +118,7 @@ struct GemmTcArgs {
   int64_t ldc;
   int gram;
   int* err;
+  int b_upper;  // B[k][n] = 0 for k > n: the N tile at n0 stops at K = n0 + BN
 };
 
 __host__ __device__ __forceinline__ bool tile_below_diagonal(int64_t bm, int64_t bn) {
@@ -162,7 +163,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int64_t bm = (int64_t)blockIdx.x / tn, bn = (int64_t)blockIdx.x - bm * tn;
   const int64_t m0 = bm * BM, n0 = bn * BN;
   if (g.gram && tile_below_diagonal(bm, bn)) return;  // uniform: before any barrier
-  const int nkb_all = (int)((g.K + BK - 1) / BK);
+  const int64_t kmax = g.b_upper ? (g.K < n0 + BN ? g.K : n0 + BN) : g.K;
+  const int nkb_all = (int)((kmax + BK - 1) / BK);
   const int kb0 = (int)((int64_t)nkb_all * blockIdx.z / gridDim.z);
   const int kb1 = (int)((int64_t)nkb_all * (blockIdx.z + 1) / gridDim.z);
   const int nkb = kb1 - kb0;

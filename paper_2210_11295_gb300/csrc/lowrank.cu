@@ -66,7 +66,7 @@ int tall_gemm(const Dla& d, Arena& ar, DT ta, DT tc, DT tout, int64_t M, int64_t
   if (ta == DT::F32 && use_tc(tc, M, N, K, A, lda) && B64 != nullptr) {
     const size_t mk = ar.mark();
     const int st = gemm_tc(d, ar, M, N, K, static_cast<const float*>(A), lda, DT::F64, B64, ldb, false, tout, C, ldc,
-                           false);
+                           false, tri_b);
     ar.release(mk);
     return st;
   }
