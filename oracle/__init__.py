@@ -14,10 +14,12 @@ Hadamard transform for low-rank approximation on distributed architectures"):
 * ``lowrank`` - randomized SVD (Algorithm 1), randomized Nystrom
                 (Algorithm 2 with Remark 3.1's shift) and the Eckart-Young
                 optimum (Sec. 3), on numpy/LAPACK.
+* ``gaussian``- the Gaussian embedding the paper compares against (Sec. 4),
+                N(0, 1/l) entries from Philox and Box-Muller, and its sketch.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it. It shares no code with the CUDA library and never
 imports it; the product path never calls into this package.
 """
 
-from . import philox, bsrht, lowrank  # noqa: F401
+from . import philox, bsrht, lowrank, gaussian  # noqa: F401

@@ -36,6 +36,7 @@ import numpy as np
 import scipy.linalg as sla
 
 from .bsrht import dense_omega, sketch_dense
+from .gaussian import gaussian_sketch
 
 EPS64 = 2.0 ** -52
 
@@ -71,11 +72,16 @@ def truncated_svd(a: np.ndarray, k: int):
     return uk, s[:k], vk
 
 
-def rsvd(a: np.ndarray, k: int, l: int, p: int, seed: int):
-    """Algorithm 1 for the tall n x m matrix ``a``; returns (U n x k, S k, V m x k)."""
+def rsvd(a: np.ndarray, k: int, l: int, p: int, seed: int, sketch: str = "bsrht"):
+    """Algorithm 1 for the tall n x m matrix ``a``; returns (U n x k, S k, V m x k).
+    ``sketch="gaussian"`` takes Omega from ``oracle.gaussian`` (the comparator
+    of Sec. 4; p is then unused)."""
     a = np.asarray(a, dtype=np.float64)
     # Step 1: Y = A_paper Omega^T = (Omega A)^T, m x l.
-    y = sketch_dense(a, p, l, seed).T
+    if sketch == "gaussian":
+        y = gaussian_sketch(a, l, seed).T
+    else:
+        y = sketch_dense(a, p, l, seed).T
     # Step 2: orthonormal basis Q of range(Y).
     q, _ = np.linalg.qr(y)
     # Step 3: Z = Q^T A_paper = (A Q)^T; step 4 needs Z^T = A Q = P R.
