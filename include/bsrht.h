@@ -71,8 +71,25 @@ typedef enum bsrht_dtype {
 typedef enum bsrht_variant {
   BSRHT_VARIANT_AUTO = 0,     /* library choice                             */
   BSRHT_VARIANT_CUDACORE = 1, /* radix-2 butterflies on CUDA cores (K1)     */
-  BSRHT_VARIANT_TENSOR = 2    /* Kronecker H16 factors on tensor cores (K2)  */
+  BSRHT_VARIANT_TENSOR = 2,   /* Kronecker H16 factors on tensor cores (K2)  */
+  BSRHT_VARIANT_GAUSSIAN = 3  /* not a block SRHT: the Gaussian embedding the
+                                 paper compares against (Sec. 4), see below  */
 } bsrht_variant;
+
+/*
+ * BSRHT_VARIANT_GAUSSIAN (bsrht_sketch, bsrht_rsvd; BSRHT_F32 only, n >= 8;
+ * bsrht_nystrom returns BSRHT_EUNSUP): Omega is replaced by Omega_G (l x n)
+ * with independent N(0, 1/l) entries -- the comparator of Sec. 4, where the
+ * paper reports the same approximation quality and a block SRHT up to 2.5x
+ * faster to apply.  p is validated but unused.  Entries: Philox4x64-10 with
+ * key (seed, 0) and counter (k>>1, j, 3, 0) for row j, column k (words 0, 1
+ * for even k, 2, 3 for odd k); a word w gives u = (2 (w >> 41) + 1) 2^-24 and
+ * the pair (u1, u2) gives z = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller,
+ * evaluated in FP32); the entry is z / sqrt(l).  B = Omega_G A is a dense
+ * product (2 l n m flops, tcgen05 tensor cores at FP32 accuracy); its
+ * scratch holds Omega_G and a transposed, TF32-split copy of A (about
+ * 4 l n + 8 n m bytes; the *_workspace queries report it).
+ */
 
 typedef struct bsrht_opts {
   int32_t dtype;          /* bsrht_dtype of A                                */

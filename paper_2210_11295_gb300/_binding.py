@@ -26,7 +26,7 @@ BSRHT_ENOCONV = -1002
 BSRHT_ECUDA = -1003
 
 F64, F32, BF16, F16 = 0, 1, 2, 3
-VARIANT_AUTO, VARIANT_CUDACORE, VARIANT_TENSOR = 0, 1, 2
+VARIANT_AUTO, VARIANT_CUDACORE, VARIANT_TENSOR, VARIANT_GAUSSIAN = 0, 1, 2, 3
 
 _DTYPES = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 

@@ -653,6 +653,9 @@ int validate_rsvd(const bsrht_opts& o, int64_t n, int64_t m, int k, int64_t l, i
 
 int validate_nystrom(const bsrht_opts& o, int64_t n, int k, int64_t l, int p) {
   if (o.dtype < BSRHT_F64 || o.dtype > BSRHT_F16) return BSRHT_EINVAL;
+  // The shift of Remark 3.1 adds nu Omega^T entry by entry from the block
+  // SRHT definition; the Gaussian comparator is a sketch / rSVD option only.
+  if (o.variant == BSRHT_VARIANT_GAUSSIAN) return BSRHT_EUNSUP;
   if (n < 1 || k < 1 || l < k || l > n || p < 1 || p > n) return BSRHT_EINVAL;
   if (o.lda != 0 && o.lda < n) return BSRHT_EINVAL;
   return BSRHT_OK;

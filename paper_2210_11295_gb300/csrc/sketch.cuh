@@ -14,7 +14,7 @@ struct SketchPlan {
   int dtype = 0;      // bsrht_dtype of A
   int variant = 1;    // 1 = CUDA-core butterflies (K1), 2 = tensor cores (K2)
   int path = 0;       // 0 = chunked FWHT kernel, 1 = small-r direct kernel, 2 = TMA-fed chunked kernel,
-                      // 3 = tensor-core kernel (K2, 16-bit inputs)
+                      // 3 = tensor-core kernel (K2, 16-bit inputs), 4 = Gaussian comparator (gaussian.cu)
   int inst = 0;       // kernel instance id within the dtype family
   int W = 0, NT = 0, R2 = 0, JM = 0, NRL = 0;
   int64_t n = 0, m = 0, lda = 0, l = 0;
@@ -46,6 +46,12 @@ int sketch_run(const SketchPlan& plan, const void* A, uint64_t seed, void* out, 
                void* work, cudaStream_t stream);
 
 int num_sms();
+
+// Gaussian-embedding comparator (gaussian.cu): plan (path 4; part_bytes =
+// the Omega_G scratch) and run.
+int gaussian_plan(SketchPlan& plan, int dtype, int64_t n, int64_t m, int64_t lda, int p, int64_t l);
+int gaussian_run(const SketchPlan& plan, const void* A, uint64_t seed, void* out, int64_t ldo, void* work,
+                 cudaStream_t stream);
 
 // Autotuner: times every candidate instance on A (scratch work, output out
 // of l x m) and records the fastest for the shape class; see

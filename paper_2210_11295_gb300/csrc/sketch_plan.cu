@@ -239,6 +239,8 @@ int sketch_make_plan(SketchPlan& pl, int dtype, int variant, int64_t n, int64_t 
   if (lda < m) return BSRHT_EINVAL;
   int64_t rb = (n + p - 1) / p, r = 1;
   while (r < rb) r <<= 1;
+  if (variant == BSRHT_VARIANT_GAUSSIAN) return gaussian_plan(pl, dtype, n, m, lda, p, l);
+  if (variant < BSRHT_VARIANT_AUTO || variant > BSRHT_VARIANT_GAUSSIAN) return BSRHT_EINVAL;
   if (variant == BSRHT_VARIANT_TENSOR) {
     // K2 only: 16-bit A, r >= 512, TMA-compatible rows.
     const int st = make_plan_choice(pl, dtype, n, m, lda, p, l, query_device, A, -3);
@@ -343,6 +345,7 @@ void sketch_autotune_reset() {
 int sketch_run(const SketchPlan& pl, const void* A, uint64_t seed, void* out, int64_t ldo, void* work,
                cudaStream_t stream) {
   if (pl.m == 0) return BSRHT_OK;
+  if (pl.path == 4) return gaussian_run(pl, A, seed, out, ldo, work, stream);
   if (pl.path != 1 && pl.work_bytes > 0 && work == nullptr) return BSRHT_ENOMEM;
   for (int64_t j0 = 0; j0 < pl.l; j0 += pl.jgroup) {
     SketchArgs a;
