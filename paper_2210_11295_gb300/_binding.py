@@ -218,10 +218,12 @@ def bsrht_sketch(a: torch.Tensor, p: int, l: int, seed: int, out: torch.Tensor |
     return out
 
 
-def bsrht_rsvd_workspace(n: int, m: int, k: int, l: int, p: int, dtype=torch.float32) -> int:
+def bsrht_rsvd_workspace(n: int, m: int, k: int, l: int, p: int, dtype=torch.float32,
+                         variant: int = VARIANT_AUTO) -> int:
     o = Opts()
     lib.bsrht_opts_init(ctypes.byref(o))
     o.dtype = _DTYPES[dtype]
+    o.variant = int(variant)
     out = ctypes.c_size_t(0)
     _check(lib.bsrht_rsvd_workspace(n, m, k, l, p, ctypes.byref(o), ctypes.byref(out)), "bsrht_rsvd_workspace")
     return int(out.value)
