@@ -202,11 +202,14 @@ int bsrht_nystrom_workspace(int64_t n, int32_t k, int64_t l, int32_t p,
  * The caller must make sure no call that uses the pool is still running. */
 int bsrht_release_pool(void);
 
-/* Stage tracing of bsrht_rsvd / bsrht_nystrom for the calling host thread:
- * when enabled, each call records CUDA events between its stages on its
- * stream (sketch, orthogonalisation of the sketch, second pass, tall QR,
- * small SVD, output factors; Nystrom: sketch, core, Z, tall QR, small SVD,
- * factors).  bsrht_profile_stages waits for those events and returns up to
+/* Stage tracing of bsrht_sketch / bsrht_rsvd / bsrht_nystrom for the calling
+ * host thread: when enabled, each call records CUDA events between its stages
+ * on its stream (sketch, orthogonalisation of the sketch, second pass, tall
+ * QR, small SVD, output factors; Nystrom: sketch, core, Z, tall QR, small
+ * SVD, factors; inside a sketch on the TMA / tensor-core kernels:
+ * sketch_tables, sketch_kernel, sketch_reduce, i.e. the sign tables, the
+ * transform kernel and the block-sum reduce, each timed on its own).
+ * bsrht_profile_stages waits for those events and returns up to
  * cap stage names (32 bytes each, NUL-terminated, in names) and durations in
  * milliseconds (ms); *count receives the number of stages of the last call. */
 int bsrht_profile_enable(int on);

@@ -5,6 +5,7 @@
 #include "capi_internal.cuh"
 #include "common.cuh"
 #include "sketch.cuh"
+#include "trace.cuh"
 
 namespace bsrht {
 
@@ -120,6 +121,9 @@ int bsrht_sketch(const void* A, int64_t n, int64_t m, int32_t p, int64_t l, uint
   void* work = nullptr;
   st = workspace_for(&o, pl.work_bytes, &work);
   if (st != BSRHT_OK) return st;
+  // With bsrht_profile_enable on, the TMA / tensor-core paths record events
+  // around their kernels (stages sketch_tables, sketch_kernel, sketch_reduce).
+  trace_begin(static_cast<cudaStream_t>(o.stream));
   return sketch_run(pl, A, seed, out, m, work, static_cast<cudaStream_t>(o.stream));
 }
 

@@ -317,25 +317,50 @@ __global__ void k_sketch_reduce_grouped(const __grid_constant__ SketchGroup grp)
 }
 
 // Fixed-order reduce of the TMA-fed kernels' partials; NaN output if any CTA
-// reported a failed wait.
+// reported a failed wait.  One thread per (sketch row, column panel): the
+// panel's slot range is worked out once (64-bit divisions), each slot is one
+// contiguous run of W floats, and the W sums stay in registers.  Launch with
+// jn * P threads; consecutive threads take consecutive rows of one panel, so
+// the slot loop is warp-uniform.
 template <int W>
 __global__ void k_sketch_reduce_checked(SketchArgs g, float* __restrict__ out, int64_t ldo, float scale,
                                         const int* __restrict__ err) {
+  static_assert(W % 4 == 0, "panel width");
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = g.jn * g.m;
-  if (idx >= total) return;
-  const int64_t jl = idx / g.m;
-  const int64_t col = idx - jl * g.m;
+  if (idx >= g.jn * g.P) return;
+  const int64_t pc = idx / g.jn;
+  const int64_t jl = idx - pc * g.jn;
+  const int64_t c0 = pc * W;
+  const int64_t left = g.m - c0;
+  const int nc = left < W ? (int)left : W;
+  float* o = out + (g.j0 + jl) * ldo + c0;
   if (*err) {
-    out[(g.j0 + jl) * ldo + col] = __int_as_float(0x7fc00000);
+    for (int cw = 0; cw < nc; ++cw) o[cw] = __int_as_float(0x7fc00000);
     return;
   }
-  const int64_t pc = col / W;
-  const int cw = (int)(col - pc * W);
+  float s[W];
+#pragma unroll
+  for (int cw = 0; cw < W; ++cw) s[cw] = 0.f;
   const float* part = static_cast<const float*>(g.part);
-  float s = 0.f;
-  for_panel_slots(g, pc, [&](int64_t slot) { s += part[(slot * g.jn + jl) * W + cw]; });
-  out[(g.j0 + jl) * ldo + col] = s * scale;
+  for_panel_slots(g, pc, [&](int64_t slot) {
+    const float4* v = reinterpret_cast<const float4*>(part + (slot * g.jn + jl) * W);
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+      const float4 x = v[q];
+      s[4 * q] += x.x;
+      s[4 * q + 1] += x.y;
+      s[4 * q + 2] += x.z;
+      s[4 * q + 3] += x.w;
+    }
+  });
+  if (nc == W) {
+#pragma unroll
+    for (int cw = 0; cw < W; ++cw) o[cw] = s[cw] * scale;
+  } else {
+#pragma unroll
+    for (int cw = 0; cw < W; ++cw)
+      if (cw < nc) o[cw] = s[cw] * scale;
+  }
 }
 
 // Direct kernel for tiny blocks (r below the smallest chunk): each thread

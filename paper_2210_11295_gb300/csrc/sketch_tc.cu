@@ -28,6 +28,7 @@
 #include "common.cuh"
 #include "gemm_tc.cuh"
 #include "sketch.cuh"
+#include "trace.cuh"
 #include "sketch_kernels.cuh"
 #include "tma.cuh"
 
@@ -432,7 +433,8 @@ int launch_tc(const SketchPlan& plan, const SketchArgs& a, int* err, void* out, 
   BSRHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<plan.G, kNT, smem, stream>>>(map, a, err);
   BSRHT_CUDA_TRY(cudaGetLastError());
-  const int64_t total = a.jn * a.m;
+  trace_mark(stream, "sketch_kernel");
+  const int64_t total = a.jn * a.P;  // one reduce thread per (sketch row, panel)
   const float scale = (float)(1.0 / sqrt((double)plan.l));
   k_sketch_reduce_checked<kW><<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(a, static_cast<float*>(out), ldo,
                                                                                    scale, err);

@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "sketch.cuh"
+#include "trace.cuh"
 #include "sketch_kernels.cuh"
 #include "tma.cuh"
 
@@ -654,13 +655,16 @@ int launch_tma(const SketchPlan& plan, const SketchArgs& a, const CUtensorMap& m
   k_sign_tables<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, stream>>>(a.seed, plan.p, plan.nch,
                                                                                           a.j0, tw, dmtab, dttab);
   BSRHT_CUDA_TRY(cudaGetLastError());
+  trace_mark(stream, "sketch_tables");
   kern<<<plan.G, NT, smem, stream>>>(map, a, dmtab, dttab, tw, err);
   BSRHT_CUDA_TRY(cudaGetLastError());
-  const int64_t total = a.jn * a.m;
+  trace_mark(stream, "sketch_kernel");
+  const int64_t total = a.jn * a.P;  // one reduce thread per (sketch row, panel)
   const float scale = (float)(1.0 / sqrt((double)plan.l));
   k_sketch_reduce_checked<W><<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(a, static_cast<float*>(out), ldo,
                                                                                   scale, err);
   BSRHT_CUDA_TRY(cudaGetLastError());
+  trace_mark(stream, "sketch_reduce");
   note_launches(3);
   return BSRHT_OK;
 }
