@@ -96,6 +96,49 @@ def rsvd(a: np.ndarray, k: int, l: int, p: int, seed: int, sketch: str = "bsrht"
     return u, st[:k].copy(), v
 
 
+def srsvd_seeds(seed: int):
+    """Seeds of Omega, Gamma, Phi, Psi in the single-view RSVD: seed + 0..3
+    (mod 2^64); one key per sketching matrix of the same generator."""
+    return tuple((seed + i) & ((1 << 64) - 1) for i in range(4))
+
+
+def srsvd(a: np.ndarray, k: int, l: int, s: int, p: int, seed: int):
+    """Single-view RSVD, Algorithm 3 of Sec. 3.3, for the tall n x m matrix
+    ``a`` (the paper's m x n matrix is a^T); returns (U n x k, S k, V m x k).
+
+    Sketching matrices, all block SRHTs (eq. 2.3): Omega (l x n, p blocks),
+    Gamma (l x m) and Phi (s x m) along the short side with one block, Psi
+    (s x n, p blocks); seeds from ``srsvd_seeds``.  In the paper's notation
+    (A_p = a^T): X = A_p^T Gamma^T, Y = A_p Omega^T, Z = Phi A_p Psi^T;
+    Q = orth(Y) (m x l), P = orth(X) (n x l); C = (Phi Q)^+ Z ((Psi P)^T)^+
+    (the reading of step 4: pseudo-inverses by least squares, the right one
+    applied to (Psi P)^T so that the product is defined); C = U~ S~ V~^T;
+    A_p ~ (Q U~_k) S~_k (P V~_k)^T, i.e. a ~ (P V~_k) S~_k (Q U~_k)^T.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    s_om, s_ga, s_ph, s_ps = srsvd_seeds(seed)
+    # Step 1: the three sketches (each a linear function of a alone).
+    y = sketch_dense(a, p, l, s_om).T              # m x l = A_p Omega^T
+    x = sketch_dense(a.T, 1, l, s_ga).T            # n x l = A_p^T Gamma^T
+    w = sketch_dense(a.T, 1, s, s_ph).T            # n x s = a Phi^T
+    z = sketch_dense(w, p, s, s_ps).T              # s x s = Phi A_p Psi^T
+    # Step 2: orthonormal bases.
+    q, _ = np.linalg.qr(y)
+    pm, _ = np.linalg.qr(x)
+    # Step 3: Phi Q (s x l) and Psi P (s x l).
+    phq = sketch_dense(q, 1, s, s_ph)
+    psp = sketch_dense(pm, p, s, s_ps)
+    # Step 4: C = (Phi Q)^+ Z ((Psi P)^T)^+ by least squares.
+    c1 = np.linalg.lstsq(phq, z, rcond=None)[0]    # l x s
+    c = np.linalg.lstsq(psp, c1.T, rcond=None)[0].T  # l x l
+    # Step 5: SVD of C; step 6: the factors.
+    uc, sc, vct = np.linalg.svd(c)
+    u = pm @ vct[:k].T
+    v = q @ uc[:, :k]
+    u, v = sign_normalize(u, v)
+    return u, sc[:k].copy(), v
+
+
 def nystrom_shift(y: np.ndarray) -> float:
     """nu = sqrt(n) * eps * ||Y||_F (reading of Remark 3.1)."""
     return math.sqrt(y.shape[0]) * EPS64 * float(np.linalg.norm(y))
