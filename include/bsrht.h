@@ -177,6 +177,33 @@ int bsrht_rsvd_workspace(int64_t n, int64_t m, int32_t k, int64_t l, int32_t p,
                          const bsrht_opts* opts, size_t* bytes);
 
 /*
+ * bsrht_srsvd - rank-k single-view randomized SVD, Algorithm 3 of Sec. 3.3:
+ * every sketch of A is a linear function of A alone (no second product with
+ * a basis, unlike Algorithm 1), so A could be streamed once.
+ *   A (n x m, BSRHT_F64 or BSRHT_F32, row stride opts->lda) ~ U diag(S) V^T,
+ *   U n x k, S k (descending), V m x k, all double, orthonormal columns.
+ *   Requires 1 <= k <= l <= s <= min(n, m), 1 <= p <= n; variant AUTO or
+ *   CUDACORE (BSRHT_EUNSUP otherwise and for 16-bit A).
+ * In the paper's orientation A_p = A^T (m x n).  Four block SRHTs (eq. 2.3,
+ * the same Philox rules as bsrht_sketch): Omega (l x n, p blocks, key
+ * seed), Gamma (l x m, one block, key seed+1), Phi (s x m, one block, key
+ * seed+2), Psi (s x n, p blocks, key seed+3).  Steps: Y = A_p Omega^T,
+ * X = A_p^T Gamma^T, Z = Phi A_p Psi^T (the m-side sketches run on an
+ * on-device transpose of A: scratch n m size(A) bytes); Q = orth(Y) (FP64),
+ * P = orth(X) (rank-robust CholeskyQR2); C = (Phi Q)^+ Z ((Psi P)^T)^+ by the
+ * normal equations of the well-conditioned Phi Q and Psi P; C = U~ S~ V~^T
+ * (FP64 Jacobi); U = P V~_k, S = S~_k, V = Q U~_k (signs as bsrht_rsvd).
+ * Synchronises opts->stream like bsrht_rsvd; BSRHT_ENOTPD if Phi Q or Psi P
+ * is numerically rank deficient.
+ */
+int bsrht_srsvd(const void* A, int64_t n, int64_t m, int32_t k, int64_t l,
+                int64_t s, int32_t p, uint64_t seed, double* U, double* S,
+                double* V, const bsrht_opts* opts);
+
+int bsrht_srsvd_workspace(int64_t n, int64_t m, int32_t k, int64_t l, int64_t s,
+                          int32_t p, const bsrht_opts* opts, size_t* bytes);
+
+/*
  * bsrht_nystrom - rank-k randomized Nystrom approximation, Algorithm 2 of
  * Sec. 3.2, of a symmetric positive semi-definite n x n matrix A (row stride
  * opts->lda >= n; symmetry is assumed, not checked).

@@ -116,6 +116,8 @@ def _load() -> ctypes.CDLL:
         "bsrht_sketch_workspace": (ctypes.c_int, [i64, i64, i32, i64, po, ctypes.POINTER(sz)]),
         "bsrht_rsvd": (ctypes.c_int, [vp, i64, i64, i32, i64, i32, u64, pd, pd, pd, po]),
         "bsrht_rsvd_workspace": (ctypes.c_int, [i64, i64, i32, i64, i32, po, ctypes.POINTER(sz)]),
+        "bsrht_srsvd": (ctypes.c_int, [vp, i64, i64, i32, i64, i64, i32, u64, pd, pd, pd, po]),
+        "bsrht_srsvd_workspace": (ctypes.c_int, [i64, i64, i32, i64, i64, i32, po, ctypes.POINTER(sz)]),
         "bsrht_nystrom": (ctypes.c_int, [vp, i64, i32, i64, i32, u64, pd, pd, po]),
         "bsrht_nystrom_workspace": (ctypes.c_int, [i64, i32, i64, i32, po, ctypes.POINTER(sz)]),
         "bsrht_release_pool": (ctypes.c_int, []),
@@ -244,6 +246,31 @@ def bsrht_rsvd(a: torch.Tensor, k: int, l: int, p: int, seed: int, variant: int 
     _check(lib.bsrht_rsvd(_dptr(a), n, m, k, l, p, seed & (2**64 - 1), _dbl(u), _dbl(s), _dbl(v),
                           ctypes.byref(o)), "bsrht_rsvd")
     return u, s, v
+
+
+def bsrht_srsvd_workspace(n: int, m: int, k: int, l: int, s: int, p: int, dtype=torch.float32) -> int:
+    o = Opts()
+    lib.bsrht_opts_init(ctypes.byref(o))
+    o.dtype = _DTYPES[dtype]
+    out = ctypes.c_size_t(0)
+    _check(lib.bsrht_srsvd_workspace(n, m, k, l, s, p, ctypes.byref(o), ctypes.byref(out)), "bsrht_srsvd_workspace")
+    return int(out.value)
+
+
+def bsrht_srsvd(a: torch.Tensor, k: int, l: int, s: int, p: int, seed: int,
+                workspace: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None, outs=None):
+    """Rank-k single-view randomized SVD (Algorithm 3): returns (U n x k, S k, V m x k) in float64."""
+    n, m = a.shape
+    if outs is None:
+        u = torch.empty(n, k, device=a.device, dtype=torch.float64)
+        sv = torch.empty(k, device=a.device, dtype=torch.float64)
+        v = torch.empty(m, k, device=a.device, dtype=torch.float64)
+    else:
+        u, sv, v = outs
+    o = make_opts(a, VARIANT_AUTO, workspace, stream)
+    _check(lib.bsrht_srsvd(_dptr(a), n, m, k, l, s, p, seed & (2**64 - 1), _dbl(u), _dbl(sv), _dbl(v),
+                           ctypes.byref(o)), "bsrht_srsvd")
+    return u, sv, v
 
 
 def bsrht_nystrom_workspace(n: int, k: int, l: int, p: int, dtype=torch.float32) -> int:

@@ -382,6 +382,153 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
   return status_to_code(hs);
 }
 
+// ------------------------------------------------------ single-view RSVD
+// Algorithm 3 (Sec. 3.3) for the tall n x m A (the paper's m x n matrix is
+// A^T = A_p).  Four block SRHTs (eq. 2.3): Omega (l x n, p blocks), Gamma
+// (l x m) and Phi (s x m) along the short side with one block, Psi (s x n,
+// p blocks), keys seed + 0..3.  Step 1 forms the three sketches, each a
+// linear function of A alone: Y = A_p Omega^T = (Omega A)^T, X = A_p^T
+// Gamma^T = (Gamma A^T)^T and Z = Phi A_p Psi^T = (Psi (A Phi^T))^T; the
+// short-side sketches run the same kernels on an on-device transpose of A.
+// Step 2: Q = orth(Y) (FP64, m x l), P = orth(X) (n x l).  Steps 3-4:
+// C = (Phi Q)^+ Z ((Psi P)^T)^+, by the normal equations
+// C = G1^-1 (Phi Q)^T Z (Psi P) G2^-1, G1 = (Phi Q)^T (Phi Q),
+// G2 = (Psi P)^T (Psi P): Phi and Psi embed range(Q) and range(P), so G1 and
+// G2 have condition numbers near 1 (Sec. 2, OSE property) and their fused
+// Cholesky inverses are accurate.  Steps 5-6: C = U~ S~ V~^T (Jacobi), and
+// A ~ (P V~_k) S~_k (Q U~_k)^T, i.e. U = P V~_k, V = Q U~_k.
+int srsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, int64_t l, int64_t s, int p,
+               uint64_t seed, double* U, double* S, double* V, Arena& ar, bool dry) {
+  const DT ta = dt_of(o.dtype);  // F32 or F64 (validated)
+  const DT tc = ta;
+  const size_t cs = dt_size(tc);
+  const int64_t lda = o.lda ? o.lda : m;
+  const uint64_t s_om = seed, s_ga = seed + 1, s_ph = seed + 2, s_ps = seed + 3;
+  Dla d{static_cast<cudaStream_t>(o.stream), nullptr};
+  d.status = static_cast<int*>(ar.take(sizeof(int)));
+  void* At = ar.take(cs * m * n);
+  void* Yb = ar.take(cs * l * m);
+  void* Xs = ar.take(cs * l * n);
+  void* Ws = ar.take(cs * s * n);
+  void* Wn = ar.take(cs * n * s);
+  void* Zs = ar.take(cs * s * s);
+  double* Zp = static_cast<double*>(ar.take(8 * s * s));
+  double* Y1 = static_cast<double*>(ar.take(8 * m * l));
+  double* Y2 = static_cast<double*>(ar.take(8 * m * l));
+  double* Y3 = static_cast<double*>(ar.take(8 * m * l));
+  void* X1 = ar.take(cs * n * l);
+  void* X2 = ar.take(cs * n * l);
+  void* X3 = ar.take(cs * n * l);
+  double* PhQ = static_cast<double*>(ar.take(8 * s * l));
+  void* PsPc = ar.take(cs * s * l);
+  double* PsP = static_cast<double*>(ar.take(8 * s * l));
+  double* G1 = static_cast<double*>(ar.take(8 * l * l));
+  double* G2 = static_cast<double*>(ar.take(8 * l * l));
+  double* LT = static_cast<double*>(ar.take(8 * l * l));
+  double* Ri1 = static_cast<double*>(ar.take(8 * l * l));
+  double* Ri2 = static_cast<double*>(ar.take(8 * l * l));
+  double* RiT = static_cast<double*>(ar.take(8 * l * l));
+  double* Gi1 = static_cast<double*>(ar.take(8 * l * l));
+  double* Gi2 = static_cast<double*>(ar.take(8 * l * l));
+  double* T1 = static_cast<double*>(ar.take(8 * l * s));
+  double* Mm = static_cast<double*>(ar.take(8 * l * l));
+  double* T2 = static_cast<double*>(ar.take(8 * l * l));
+  double* C = static_cast<double*>(ar.take(8 * l * l));
+  double* CT = static_cast<double*>(ar.take(8 * l * l));
+  double* Uc = static_cast<double*>(ar.take(8 * l * l));
+  double* Vc = static_cast<double*>(ar.take(8 * l * l));
+  double* sig = static_cast<double*>(ar.take(8 * l));
+  void* Vc_c = ar.take(cs * l * l);
+  const OrthBufs ob = take_orth_bufs(ar, l, 8);
+  // Sketch plans; the scratch is shared (the sketches run one after another).
+  SketchPlan sp_y, sp_x, sp_w, sp_z, sp_q, sp_p;
+  TRY(sketch_make_plan(sp_y, o.dtype, BSRHT_VARIANT_AUTO, n, m, lda, p, l, !dry, dry ? nullptr : A));
+  TRY(sketch_make_plan(sp_x, o.dtype, BSRHT_VARIANT_AUTO, m, n, n, 1, l, !dry, dry ? nullptr : At));
+  TRY(sketch_make_plan(sp_w, o.dtype, BSRHT_VARIANT_AUTO, m, n, n, 1, s, !dry, dry ? nullptr : At));
+  TRY(sketch_make_plan(sp_z, o.dtype, BSRHT_VARIANT_AUTO, n, s, s, p, s, !dry, dry ? nullptr : Wn));
+  TRY(sketch_make_plan(sp_q, BSRHT_F64, BSRHT_VARIANT_AUTO, m, l, l, 1, s, !dry, nullptr));
+  TRY(sketch_make_plan(sp_p, o.dtype, BSRHT_VARIANT_AUTO, n, l, l, p, s, !dry, nullptr));
+  const size_t skb = std::max({sp_y.work_bytes, sp_x.work_bytes, sp_w.work_bytes, sp_z.work_bytes,
+                               sp_q.work_bytes, sp_p.work_bytes});
+  void* sk_ws = ar.take(skb);
+  if (!ar.ok()) return BSRHT_ENOMEM;
+  if (!dry) BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
+
+  // Step 1: the three sketches.
+  if (!dry) {
+    trace_begin(d.s);
+    TRY(sketch_run(sp_y, A, s_om, Yb, m, sk_ws, d.s));                      // Omega A (l x m)
+    TRY(transpose_cast(d, ta, A, n, m, lda, ta, At, n));                   // A^T (m x n)
+    TRY(sketch_run(sp_x, At, s_ga, Xs, n, sk_ws, d.s));                    // Gamma A^T (l x n)
+    TRY(sketch_run(sp_w, At, s_ph, Ws, n, sk_ws, d.s));                    // Phi A^T (s x n)
+    TRY(transpose_cast(d, tc, Ws, s, n, n, tc, Wn, s));                    // A Phi^T (n x s)
+    TRY(sketch_run(sp_z, Wn, s_ps, Zs, s, sk_ws, d.s));                    // Psi A Phi^T = Z^T (s x s)
+    TRY(transpose_cast(d, tc, Zs, s, s, s, DT::F64, Zp, s));               // Z (s x s, FP64)
+    trace_mark(d.s, "sketches");
+    TRY(transpose_cast(d, tc, Yb, l, m, m, DT::F64, Y1, l));               // Y (m x l, FP64)
+    TRY(transpose_cast(d, tc, Xs, l, n, n, tc, X1, l));                    // X (n x l)
+  }
+  // Step 2: Q = orth(Y) in FP64, P = orth(X).
+  void* Qv = nullptr;
+  TRY(orth_robust(d, ar, dry, DT::F64, Y1, Y2, Y3, m, l, seed ^ 0x61ull, ob, nullptr, true, false, &Qv));
+  const double* Q = static_cast<const double*>(Qv);
+  void* Pv = nullptr;
+  TRY(orth_robust(d, ar, dry, tc, X1, X2, X3, n, l, seed ^ 0x62ull, ob, nullptr, true, false, &Pv));
+  if (!dry) trace_mark(d.s, "orth");
+  // Step 3: Phi Q and Psi P (s x l).
+  if (!dry) {
+    TRY(sketch_run(sp_q, Q, s_ph, PhQ, l, sk_ws, d.s));
+    TRY(sketch_run(sp_p, Pv, s_ps, PsPc, l, sk_ws, d.s));
+    if (tc == DT::F32)
+      TRY(cast_copy(d, DT::F32, PsPc, DT::F64, PsP, s * l));
+    else
+      BSRHT_CUDA_TRY(cudaMemcpyAsync(PsP, PsPc, 8 * s * l, cudaMemcpyDeviceToDevice, d.s));
+  }
+  // Step 4: C = G1^-1 (Phi Q)^T Z (Psi P) G2^-1.
+  TRY(gemm64(d, ar, l, l, s, PhQ, l, true, PhQ, l, G1, l, false, true));   // G1 = (Phi Q)^T (Phi Q)
+  TRY(gemm64(d, ar, l, l, s, PsP, l, true, PsP, l, G2, l, false, true));   // G2 = (Psi P)^T (Psi P)
+  if (!dry) {
+    TRY(chol_inv(d, G1, LT, Ri1, ob.Ug, ob.Vg, l));                         // Ri1 = L1^-T
+    TRY(chol_inv(d, G2, LT, Ri2, ob.Ug, ob.Vg, l));
+    TRY(transpose_lower_to_upper(d, Ri1, RiT, l));
+  }
+  TRY(gemm64(d, ar, l, l, l, RiT, l, true, RiT, l, Gi1, l));              // G1^-1 = Ri1 Ri1^T
+  if (!dry) TRY(transpose_lower_to_upper(d, Ri2, RiT, l));
+  TRY(gemm64(d, ar, l, l, l, RiT, l, true, RiT, l, Gi2, l));              // G2^-1
+  TRY(gemm64(d, ar, l, s, s, PhQ, l, true, Zp, s, T1, s));                // (Phi Q)^T Z
+  TRY(gemm64(d, ar, l, l, s, T1, s, false, PsP, l, Mm, l));               // ... (Psi P)
+  TRY(gemm64(d, ar, l, l, l, Gi1, l, false, Mm, l, T2, l));
+  TRY(gemm64(d, ar, l, l, l, T2, l, false, Gi2, l, C, l));
+  if (!dry) trace_mark(d.s, "core");
+  // Step 5: SVD of C (Jacobi on its columns, the rows of C^T).
+  if (!dry) TRY(transpose_lower_to_upper(d, C, CT, l));
+  {
+    const size_t mk = ar.mark();
+    TRY(jacobi_svd(d, ar, CT, l, Uc, sig, Vc));
+    ar.release(mk);
+  }
+  if (!dry) trace_mark(d.s, "small_svd");
+  // Step 6: U = P V~_k, V = Q U~_k, S = S~_k.
+  const void* Vk = Vc;
+  if (tc == DT::F32) {
+    if (!dry) TRY(cast_copy(d, DT::F64, Vc, DT::F32, Vc_c, l * l));
+    Vk = Vc_c;
+  }
+  TRY(tall_gemm(d, ar, tc, tc, DT::F64, n, k, l, Pv, l, Vc, Vk, l, U, k, false));
+  TRY(gemm64(d, ar, m, k, l, Q, l, false, Uc, l, V, k));
+  if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(S, sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, d.s));
+  {
+    const size_t mk = ar.mark();
+    TRY(sign_normalize(d, ar, U, n, k, V, m));
+    ar.release(mk);
+  }
+  if (!dry) trace_mark(d.s, "factors");
+  if (dry) return BSRHT_OK;
+  int hs = 0;
+  TRY(read_status(d, &hs));
+  return status_to_code(hs);
+}
+
 // ---------------------------------------------------------------- Nystrom
 struct OmegaTables {
   uint32_t* s;      // l samples s_j (mod r)
@@ -651,6 +798,15 @@ int validate_rsvd(const bsrht_opts& o, int64_t n, int64_t m, int k, int64_t l, i
   return BSRHT_OK;
 }
 
+int validate_srsvd(const bsrht_opts& o, int64_t n, int64_t m, int k, int64_t l, int64_t s, int p) {
+  if (o.dtype != BSRHT_F64 && o.dtype != BSRHT_F32) return o.dtype >= BSRHT_F64 && o.dtype <= BSRHT_F16
+                                                               ? BSRHT_EUNSUP : BSRHT_EINVAL;
+  if (o.variant != BSRHT_VARIANT_AUTO && o.variant != BSRHT_VARIANT_CUDACORE) return BSRHT_EUNSUP;
+  if (n < 1 || m < 1 || k < 1 || l < k || s < l || s > m || s > n || p < 1 || p > n) return BSRHT_EINVAL;
+  if (o.lda != 0 && o.lda < m) return BSRHT_EINVAL;
+  return BSRHT_OK;
+}
+
 int validate_nystrom(const bsrht_opts& o, int64_t n, int k, int64_t l, int p) {
   if (o.dtype < BSRHT_F64 || o.dtype > BSRHT_F16) return BSRHT_EINVAL;
   // The shift of Remark 3.1 adds nu Omega^T entry by entry from the block
@@ -693,6 +849,33 @@ int bsrht_rsvd(const void* A, int64_t n, int64_t m, int32_t k, int64_t l, int32_
   ar.base = static_cast<char*>(ws);
   ar.cap = need;
   return rsvd_impl(o, A, n, m, k, l, p, seed, U, S, V, ar, false);
+}
+
+int bsrht_srsvd_workspace(int64_t n, int64_t m, int32_t k, int64_t l, int64_t s, int32_t p, const bsrht_opts* opts,
+                          size_t* bytes) {
+  if (!bytes) return BSRHT_EINVAL;
+  const bsrht_opts o = opts_or_default(opts);
+  TRY(validate_srsvd(o, n, m, k, l, s, p));
+  Arena ar;
+  ar.measure = true;
+  TRY(srsvd_impl(o, nullptr, n, m, k, l, s, p, 0, nullptr, nullptr, nullptr, ar, true));
+  *bytes = ar.high + 256;
+  return BSRHT_OK;
+}
+
+int bsrht_srsvd(const void* A, int64_t n, int64_t m, int32_t k, int64_t l, int64_t s, int32_t p, uint64_t seed,
+                double* U, double* S, double* V, const bsrht_opts* opts) {
+  const bsrht_opts o = opts_or_default(opts);
+  TRY(validate_srsvd(o, n, m, k, l, s, p));
+  if (!A || !U || !S || !V) return BSRHT_EINVAL;
+  size_t need = 0;
+  TRY(bsrht_srsvd_workspace(n, m, k, l, s, p, &o, &need));
+  void* ws = nullptr;
+  TRY(workspace_for(&o, need, &ws));
+  Arena ar;
+  ar.base = static_cast<char*>(ws);
+  ar.cap = need;
+  return srsvd_impl(o, A, n, m, k, l, s, p, seed, U, S, V, ar, false);
 }
 
 int bsrht_nystrom_workspace(int64_t n, int32_t k, int64_t l, int32_t p, const bsrht_opts* opts, size_t* bytes) {
