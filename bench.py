@@ -330,6 +330,38 @@ def gaussian_comparator(args, lib, a, sketch_ms, step_ms, mode, stream):
     return res
 
 
+def single_view_rsvd(args, lib, a, stream):
+    """One bsrht_srsvd call (Algorithm 3, s = 2 l) on the benchmark's A after
+    a warm-up call: time (CUDA events) and stage times."""
+    import torch
+
+    n, m = a.shape
+    k, l, p = args.k, args.l, args.p
+    s = min(2 * l, m, n)
+    ws = torch.empty(max(lib.bsrht_srsvd_workspace(n, m, k, l, s, p, a.dtype), 1), dtype=torch.uint8, device=a.device)
+    outs = (torch.empty(n, k, device=a.device, dtype=torch.float64), torch.empty(k, device=a.device, dtype=torch.float64),
+            torch.empty(m, k, device=a.device, dtype=torch.float64))
+    lib.bsrht_srsvd(a, k, l, s, p, 0, workspace=ws, outs=outs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lib.bsrht_srsvd(a, k, l, s, p, 1, workspace=ws, outs=outs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lib.bsrht_profile_enable(True)
+    lib.bsrht_srsvd(a, k, l, s, p, 2, workspace=ws, outs=outs)
+    torch.cuda.synchronize()
+    stages = {}
+    for name, t in lib.bsrht_profile_stages():  # stage names repeat (several sketches): sum them
+        stages[name] = round(stages.get(name, 0.0) + t, 3)
+    lib.bsrht_profile_enable(False)
+    del ws, outs
+    torch.cuda.empty_cache()
+    return {"kind": "Algorithm 3 (single view): Omega, Gamma, Phi, Psi block SRHTs, s = 2 l", "s": s,
+            "ms": round(ms, 3), "stages_ms": stages}
+
+
 def run_ours(args):
     import torch
 
@@ -430,6 +462,10 @@ def run_ours(args):
     comparator = gaussian_comparator(args, lib, a, sketch_ms, step_ms, mode, stream) \
         if args.dtype == "f32" and args.variant == "auto" else None
 
+    # Algorithm 3 (single-view RSVD) on the same A, s = 2 l: one call, with
+    # its stages.
+    single_view = single_view_rsvd(args, lib, a, stream) if mode == "full" and args.variant == "auto" else None
+
     # End to end through the C ABI from pinned host buffers.
     a_host = a.cpu().pin_memory()
     e2e_ms = None
@@ -505,6 +541,8 @@ def run_ours(args):
         line["stages_ms"] = stages
     if comparator:
         line["gaussian_comparator"] = comparator
+    if single_view:
+        line["single_view_rsvd"] = single_view
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
