@@ -358,7 +358,7 @@ def single_view_rsvd(args, lib, a, stream):
     lib.bsrht_profile_enable(False)
     del ws, outs
     torch.cuda.empty_cache()
-    return {"kind": "Algorithm 3 (single view): Omega, Gamma, Phi, Psi block SRHTs, s = 2 l", "s": s,
+    return {"kind": "Algorithm 3 (single view): Omega, Phi, Psi block SRHTs, Gamma Gaussian, s = 2 l", "s": s,
             "ms": round(ms, 3), "stages_ms": stages}
 
 

@@ -184,12 +184,15 @@ int bsrht_rsvd_workspace(int64_t n, int64_t m, int32_t k, int64_t l, int32_t p,
  *   U n x k, S k (descending), V m x k, all double, orthonormal columns.
  *   Requires 1 <= k <= l <= s <= min(n, m), 1 <= p <= n; variant AUTO or
  *   CUDACORE (BSRHT_EUNSUP otherwise and for 16-bit A).
- * In the paper's orientation A_p = A^T (m x n).  Four block SRHTs (eq. 2.3,
- * the same Philox rules as bsrht_sketch): Omega (l x n, p blocks, key
- * seed), Gamma (l x m, one block, key seed+1), Phi (s x m, one block, key
- * seed+2), Psi (s x n, p blocks, key seed+3).  Steps: Y = A_p Omega^T,
- * X = A_p^T Gamma^T, Z = Phi A_p Psi^T (the m-side sketches run on an
- * on-device transpose of A: scratch n m size(A) bytes); Q = orth(Y) (FP64),
+ * In the paper's orientation A_p = A^T (m x n).  Sketching maps: block
+ * SRHTs (eq. 2.3, the same Philox rules as bsrht_sketch) Omega (l x n,
+ * p blocks, key seed), Phi (s x m, one block, key seed+2), Psi (s x n,
+ * p blocks, key seed+3); Gamma (l x m, key seed+1) is the Gaussian map of
+ * BSRHT_VARIANT_GAUSSIAN evaluated in FP64 (an SRHT sample of l rows out of
+ * r ~ m repeats rows and would make X rank deficient).  Steps:
+ * Y = A_p Omega^T, X = A_p^T Gamma^T = A Gamma^T, Z = Phi A_p Psi^T (A Phi^T
+ * through an on-device transpose of A: scratch n m size(A) bytes);
+ * Q = orth(Y) (FP64),
  * P = orth(X) (rank-robust CholeskyQR2); C = (Phi Q)^+ Z ((Psi P)^T)^+ by the
  * normal equations of the well-conditioned Phi Q and Psi P; C = U~ S~ V~^T
  * (FP64 Jacobi); U = P V~_k, S = S~_k, V = Q U~_k (signs as bsrht_rsvd).

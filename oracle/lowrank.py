@@ -36,7 +36,7 @@ import numpy as np
 import scipy.linalg as sla
 
 from .bsrht import dense_omega, sketch_dense
-from .gaussian import gaussian_sketch
+from .gaussian import gaussian_sketch, omega_gaussian
 
 EPS64 = 2.0 ** -52
 
@@ -106,9 +106,11 @@ def srsvd(a: np.ndarray, k: int, l: int, s: int, p: int, seed: int):
     """Single-view RSVD, Algorithm 3 of Sec. 3.3, for the tall n x m matrix
     ``a`` (the paper's m x n matrix is a^T); returns (U n x k, S k, V m x k).
 
-    Sketching matrices, all block SRHTs (eq. 2.3): Omega (l x n, p blocks),
-    Gamma (l x m) and Phi (s x m) along the short side with one block, Psi
-    (s x n, p blocks); seeds from ``srsvd_seeds``.  In the paper's notation
+    Sketching matrices, seeds from ``srsvd_seeds``: Omega (l x n, p blocks),
+    Phi (s x m, one block) and Psi (s x n, p blocks) are block SRHTs (eq. 2.3);
+    Gamma (l x m) is the Gaussian map of ``oracle.gaussian`` (an SRHT row
+    sample of l out of r ~ m repeats rows, which would make X rank deficient;
+    Algorithm 3 takes any oblivious embedding).  In the paper's notation
     (A_p = a^T): X = A_p^T Gamma^T, Y = A_p Omega^T, Z = Phi A_p Psi^T;
     Q = orth(Y) (m x l), P = orth(X) (n x l); C = (Phi Q)^+ Z ((Psi P)^T)^+
     (the reading of step 4: pseudo-inverses by least squares, the right one
@@ -119,7 +121,7 @@ def srsvd(a: np.ndarray, k: int, l: int, s: int, p: int, seed: int):
     s_om, s_ga, s_ph, s_ps = srsvd_seeds(seed)
     # Step 1: the three sketches (each a linear function of a alone).
     y = sketch_dense(a, p, l, s_om).T              # m x l = A_p Omega^T
-    x = sketch_dense(a.T, 1, l, s_ga).T            # n x l = A_p^T Gamma^T
+    x = a @ omega_gaussian(a.shape[1], l, s_ga).T  # n x l = A_p^T Gamma^T
     w = sketch_dense(a.T, 1, s, s_ph).T            # n x s = a Phi^T
     z = sketch_dense(w, p, s, s_ps).T              # s x s = Phi A_p Psi^T
     # Step 2: orthonormal bases.

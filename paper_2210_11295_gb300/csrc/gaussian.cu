@@ -32,28 +32,35 @@ __device__ __forceinline__ float gauss_uniform(uint64_t w) {
   return (float)(2u * (uint32_t)(w >> 41) + 1u) * 0x1.0p-24f;
 }
 
-__device__ __forceinline__ float box_muller(uint64_t a, uint64_t b) {
+// Box-Muller in the output type: FP32 for the comparator's Omega_G, FP64
+// where the map enters an FP64 computation.
+__device__ __forceinline__ float box_muller(uint64_t a, uint64_t b, float) {
   const float u1 = gauss_uniform(a), u2 = gauss_uniform(b);
   return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+__device__ __forceinline__ double box_muller(uint64_t a, uint64_t b, double) {
+  const double u1 = (double)gauss_uniform(a), u2 = (double)gauss_uniform(b);
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
 }
 
 // Om[j][k] (row stride ldo, ldo even) for j < l, k < n; columns [n, ldo)
 // are zeroed.  One thread per column pair of a row: one Philox block, one
-// 8-byte store.
-__global__ void k_gaussian_omega(float* __restrict__ Om, int64_t l, int64_t n, int64_t ldo, uint64_t seed,
-                                 float scale) {
+// paired store.
+template <typename T>
+__global__ void k_gaussian_omega(T* __restrict__ Om, int64_t l, int64_t n, int64_t ldo, uint64_t seed, T scale) {
   const int64_t npair = ldo / 2;
   const int64_t total = l * npair;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / npair, q = e - j * npair;
-    float2 v = make_float2(0.f, 0.f);
+    T v0 = T(0), v1 = T(0);
     if (2 * q < n) {
       const U64x4 w = philox4x64_10(U64x4{(uint64_t)q, (uint64_t)j, kStreamG, 0}, seed, 0);
-      v.x = scale * box_muller(w.x, w.y);
-      if (2 * q + 1 < n) v.y = scale * box_muller(w.z, w.w);
+      v0 = scale * box_muller(w.x, w.y, T(0));
+      if (2 * q + 1 < n) v1 = scale * box_muller(w.z, w.w, T(0));
     }
-    reinterpret_cast<float2*>(Om + j * ldo)[q] = v;
+    Om[j * ldo + 2 * q] = v0;
+    Om[j * ldo + 2 * q + 1] = v1;
   }
 }
 
@@ -96,7 +103,8 @@ int gaussian_run(const SketchPlan& pl, const void* A, uint64_t seed, void* out, 
   const int64_t ld = omega_ld(pl.n);
   const int64_t total = pl.l * (ld / 2);
   const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 16);
-  k_gaussian_omega<<<blocks, 256, 0, stream>>>(om, pl.l, pl.n, ld, seed, (float)(1.0 / std::sqrt((double)pl.l)));
+  k_gaussian_omega<float><<<blocks, 256, 0, stream>>>(om, pl.l, pl.n, ld, seed,
+                                                      (float)(1.0 / std::sqrt((double)pl.l)));
   BSRHT_CUDA_TRY(cudaGetLastError());
   note_launches(1);
   Arena ar;
@@ -104,6 +112,24 @@ int gaussian_run(const SketchPlan& pl, const void* A, uint64_t seed, void* out, 
   ar.cap = pl.work_bytes - pl.part_bytes;
   const Dla d{stream, nullptr};
   return gemm_tc(d, ar, pl.l, pl.m, pl.n, om, ld, DT::F32, A, pl.lda, false, DT::F32, out, ldo, false);
+}
+
+int gaussian_omega(cudaStream_t stream, DT t, void* out, int64_t rows, int64_t cols, int64_t ld, uint64_t seed,
+                   double scale) {
+  if (rows <= 0 || cols <= 0) return BSRHT_OK;
+  if ((ld & 1) || ld < cols) return BSRHT_EINVAL;
+  const int64_t total = rows * (ld / 2);
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 16);
+  if (t == DT::F64)
+    k_gaussian_omega<double><<<blocks, 256, 0, stream>>>(static_cast<double*>(out), rows, cols, ld, seed, scale);
+  else if (t == DT::F32)
+    k_gaussian_omega<float><<<blocks, 256, 0, stream>>>(static_cast<float*>(out), rows, cols, ld, seed,
+                                                        (float)scale);
+  else
+    return BSRHT_EUNSUP;
+  BSRHT_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  return BSRHT_OK;
 }
 
 }  // namespace bsrht

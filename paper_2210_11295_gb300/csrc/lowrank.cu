@@ -384,12 +384,16 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
 
 // ------------------------------------------------------ single-view RSVD
 // Algorithm 3 (Sec. 3.3) for the tall n x m A (the paper's m x n matrix is
-// A^T = A_p).  Four block SRHTs (eq. 2.3): Omega (l x n, p blocks), Gamma
-// (l x m) and Phi (s x m) along the short side with one block, Psi (s x n,
-// p blocks), keys seed + 0..3.  Step 1 forms the three sketches, each a
-// linear function of A alone: Y = A_p Omega^T = (Omega A)^T, X = A_p^T
-// Gamma^T = (Gamma A^T)^T and Z = Phi A_p Psi^T = (Psi (A Phi^T))^T; the
-// short-side sketches run the same kernels on an on-device transpose of A.
+// A^T = A_p).  Sketching maps, keys seed + 0..3: Omega (l x n, p blocks),
+// Phi (s x m, one block) and Psi (s x n, p blocks) are block SRHTs (eq. 2.3);
+// Gamma (l x m), the short side's range sketch, is the Gaussian map of the
+// comparator (N(0, 1/l), Philox / Box-Muller, in FP64): an SRHT row sample
+// of l out of r ~ m draws repeated rows (with replacement, about l^2 / 2r of
+// them), which would make X exactly rank deficient.  Step 1 forms the three
+// sketches, each a linear function of A alone: Y = A_p Omega^T =
+// (Omega A)^T, X = A_p^T Gamma^T = A Gamma^T (a tall product) and
+// Z = Phi A_p Psi^T = (Psi (A Phi^T))^T, A Phi^T through the sketch kernels
+// on an on-device transpose of A.
 // Step 2: Q = orth(Y) (FP64, m x l), P = orth(X) (n x l).  Steps 3-4:
 // C = (Phi Q)^+ Z ((Psi P)^T)^+, by the normal equations
 // C = G1^-1 (Phi Q)^T Z (Psi P) G2^-1, G1 = (Phi Q)^T (Phi Q),
@@ -408,7 +412,10 @@ int srsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, 
   d.status = static_cast<int*>(ar.take(sizeof(int)));
   void* At = ar.take(cs * m * n);
   void* Yb = ar.take(cs * l * m);
-  void* Xs = ar.take(cs * l * n);
+  const int64_t ldg = m + (m & 1);
+  double* Gm = static_cast<double*>(ar.take(8 * l * ldg));   // Gamma (l x m, FP64)
+  double* GT = static_cast<double*>(ar.take(8 * m * l));     // Gamma^T (m x l, FP64)
+  void* GTc = ar.take(cs * m * l);                            // Gamma^T in the type of A
   void* Ws = ar.take(cs * s * n);
   void* Wn = ar.take(cs * n * s);
   void* Zs = ar.take(cs * s * s);
@@ -441,15 +448,14 @@ int srsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, 
   void* Vc_c = ar.take(cs * l * l);
   const OrthBufs ob = take_orth_bufs(ar, l, 8);
   // Sketch plans; the scratch is shared (the sketches run one after another).
-  SketchPlan sp_y, sp_x, sp_w, sp_z, sp_q, sp_p;
+  SketchPlan sp_y, sp_w, sp_z, sp_q, sp_p;
   TRY(sketch_make_plan(sp_y, o.dtype, BSRHT_VARIANT_AUTO, n, m, lda, p, l, !dry, dry ? nullptr : A));
-  TRY(sketch_make_plan(sp_x, o.dtype, BSRHT_VARIANT_AUTO, m, n, n, 1, l, !dry, dry ? nullptr : At));
   TRY(sketch_make_plan(sp_w, o.dtype, BSRHT_VARIANT_AUTO, m, n, n, 1, s, !dry, dry ? nullptr : At));
   TRY(sketch_make_plan(sp_z, o.dtype, BSRHT_VARIANT_AUTO, n, s, s, p, s, !dry, dry ? nullptr : Wn));
   TRY(sketch_make_plan(sp_q, BSRHT_F64, BSRHT_VARIANT_AUTO, m, l, l, 1, s, !dry, nullptr));
   TRY(sketch_make_plan(sp_p, o.dtype, BSRHT_VARIANT_AUTO, n, l, l, p, s, !dry, nullptr));
-  const size_t skb = std::max({sp_y.work_bytes, sp_x.work_bytes, sp_w.work_bytes, sp_z.work_bytes,
-                               sp_q.work_bytes, sp_p.work_bytes});
+  const size_t skb = std::max({sp_y.work_bytes, sp_w.work_bytes, sp_z.work_bytes, sp_q.work_bytes,
+                               sp_p.work_bytes});
   void* sk_ws = ar.take(skb);
   if (!ar.ok()) return BSRHT_ENOMEM;
   if (!dry) BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
@@ -459,15 +465,18 @@ int srsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, 
     trace_begin(d.s);
     TRY(sketch_run(sp_y, A, s_om, Yb, m, sk_ws, d.s));                      // Omega A (l x m)
     TRY(transpose_cast(d, ta, A, n, m, lda, ta, At, n));                   // A^T (m x n)
-    TRY(sketch_run(sp_x, At, s_ga, Xs, n, sk_ws, d.s));                    // Gamma A^T (l x n)
     TRY(sketch_run(sp_w, At, s_ph, Ws, n, sk_ws, d.s));                    // Phi A^T (s x n)
     TRY(transpose_cast(d, tc, Ws, s, n, n, tc, Wn, s));                    // A Phi^T (n x s)
     TRY(sketch_run(sp_z, Wn, s_ps, Zs, s, sk_ws, d.s));                    // Psi A Phi^T = Z^T (s x s)
     TRY(transpose_cast(d, tc, Zs, s, s, s, DT::F64, Zp, s));               // Z (s x s, FP64)
     trace_mark(d.s, "sketches");
     TRY(transpose_cast(d, tc, Yb, l, m, m, DT::F64, Y1, l));               // Y (m x l, FP64)
-    TRY(transpose_cast(d, tc, Xs, l, n, n, tc, X1, l));                    // X (n x l)
+    TRY(gaussian_omega(d.s, DT::F64, Gm, l, m, ldg, s_ga, 1.0 / std::sqrt((double)l)));
+    TRY(transpose_cast(d, DT::F64, Gm, l, m, ldg, DT::F64, GT, l));        // Gamma^T (m x l)
+    if (tc == DT::F32) TRY(cast_copy(d, DT::F64, GT, DT::F32, GTc, m * l));
   }
+  TRY(tall_gemm(d, ar, ta, tc, tc, n, l, m, A, lda, GT, tc == DT::F32 ? GTc : (const void*)GT, l, X1, l,
+                false));                                                    // X = A Gamma^T (n x l)
   // Step 2: Q = orth(Y) in FP64, P = orth(X).
   void* Qv = nullptr;
   TRY(orth_robust(d, ar, dry, DT::F64, Y1, Y2, Y3, m, l, seed ^ 0x61ull, ob, nullptr, true, false, &Qv));

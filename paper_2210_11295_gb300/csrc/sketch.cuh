@@ -52,6 +52,12 @@ int num_sms();
 int gaussian_plan(SketchPlan& plan, int dtype, int64_t n, int64_t m, int64_t lda, int p, int64_t l);
 int gaussian_run(const SketchPlan& plan, const void* A, uint64_t seed, void* out, int64_t ldo, void* work,
                  cudaStream_t stream);
+// Gaussian map on its own (gaussian.cu): out[j][k] = scale * z(j, k) for
+// j < rows, k < cols (row stride ld, even; columns [cols, ld) zeroed), z the
+// comparator's Philox / Box-Muller normal evaluated in the type t (F32/F64).
+enum class DT;
+int gaussian_omega(cudaStream_t stream, DT t, void* out, int64_t rows, int64_t cols, int64_t ld, uint64_t seed,
+                   double scale);
 
 // Autotuner: times every candidate instance on A (scratch work, output out
 // of l x m) and records the fastest for the shape class; see
