@@ -88,7 +88,9 @@ typedef enum bsrht_variant {
  * evaluated in FP32); the entry is z / sqrt(l).  B = Omega_G A is a dense
  * product (2 l n m flops, tcgen05 tensor cores at FP32 accuracy); its
  * scratch holds Omega_G and a transposed, TF32-split copy of A (about
- * 4 l n + 8 n m bytes; the *_workspace queries report it).
+ * 4 l n + 8 n m bytes; the *_workspace queries report it).  The product's
+ * waits are bounded: a tile whose wait gives up is written as NaN (the
+ * low-rank calls see it in their status word and return BSRHT_ETIMEDOUT).
  */
 
 typedef struct bsrht_opts {
@@ -167,7 +169,8 @@ int bsrht_sketch_noalloc(const void* A, int64_t n, int64_t m, int32_t p,
  *   an eigen-based basis completed with seeded random directions.
  *   Synchronises opts->stream to read the status of the small factorizations;
  *   returns BSRHT_ENOTPD if a Gram matrix is numerically singular,
- *   BSRHT_ENOCONV if the Jacobi SVD does not converge.
+ *   BSRHT_ENOCONV if the Jacobi SVD does not converge, BSRHT_ETIMEDOUT if a
+ *   tensor-core product gave up one of its bounded waits.
  */
 int bsrht_rsvd(const void* A, int64_t n, int64_t m, int32_t k, int64_t l,
                int32_t p, uint64_t seed, double* U, double* S, double* V,
@@ -197,7 +200,7 @@ int bsrht_rsvd_workspace(int64_t n, int64_t m, int32_t k, int64_t l, int32_t p,
  * normal equations of the well-conditioned Phi Q and Psi P; C = U~ S~ V~^T
  * (FP64 Jacobi); U = P V~_k, S = S~_k, V = Q U~_k (signs as bsrht_rsvd).
  * Synchronises opts->stream like bsrht_rsvd; BSRHT_ENOTPD if Phi Q or Psi P
- * is numerically rank deficient.
+ * is numerically rank deficient, BSRHT_ETIMEDOUT as for bsrht_rsvd.
  */
 int bsrht_srsvd(const void* A, int64_t n, int64_t m, int32_t k, int64_t l,
                 int64_t s, int32_t p, uint64_t seed, double* U, double* S,
@@ -219,7 +222,7 @@ int bsrht_srsvd_workspace(int64_t n, int64_t m, int32_t k, int64_t l, int64_t s,
  *   replaced by the SVD square root's pseudo-inverse (Remark 3.1);
  *   Z = Y_nu C^-1; R factor of Z (CholeskyQR2, rank-robust); SVD
  *   R = U~ Sigma~ V~^T; U = Z V~_k Sigma~_k^-1; Lambda = max(Sigma~_k^2 - nu, 0).
- *   Synchronises opts->stream.
+ *   Synchronises opts->stream; status codes as for bsrht_rsvd.
  */
 int bsrht_nystrom(const void* A, int64_t n, int32_t k, int64_t l, int32_t p,
                   uint64_t seed, double* U, double* Lambda,

@@ -42,6 +42,9 @@ struct Dla {
 
 constexpr int kStatusNotPD = 1;
 constexpr int kStatusNoConv = 2;
+// A tensor-core product (gemm_tc) gave up one of its bounded waits; its
+// output is not valid.
+constexpr int kStatusTcWait = 8;
 
 // C[M x N] = alpha * op(A) B + beta C.  op(A) = A (M x K, lda) or A^T (A is
 // K x M, lda).  B is K x N (ldb).  Accumulation in FP64 when acc64, else

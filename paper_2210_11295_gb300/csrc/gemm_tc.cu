@@ -139,7 +139,14 @@ int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const floa
   if (pre && !make_tensor_map_2d(&mblo, Btlo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)N, (uint64_t)K,
                                  (uint64_t)ldk, tc::BK, tc::BN, CU_TENSOR_MAP_SWIZZLE_128B))
     return BSRHT_EUNSUP;
-  BSRHT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), d.s));
+  // A failed bounded wait sets kStatusTcWait in the caller's status word when
+  // it has one (read back by the low-rank drivers), else in a word of its own.
+  static_assert(tc::kErrWait == kStatusTcWait, "status bit");
+  if (d.status) {
+    err = d.status;
+  } else {
+    BSRHT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), d.s));
+  }
   if (tm * tn > 0x7FFFFFFF) return BSRHT_EUNSUP;
   dim3 grid((unsigned)(tm * tn), 1u, (unsigned)splits);
   tc::GemmTcArgs g{M, N, K, splits > 1 ? (void*)P : C, ldc, gram ? 1 : 0, err, (b_upper && !gram) ? 1 : 0};

@@ -48,6 +48,7 @@ constexpr uint32_t B_BYTES = BN * BK * 4;   // 16 KB
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo (hi parts via TMA)
 constexpr uint32_t TMEM_COLS = 2 * BN;      // two accumulator buffers
 constexpr uint32_t kWait = 1u << 24;
+constexpr int kErrWait = 8;  // the status bit a failed wait sets (kStatusTcWait of dla.cuh)
 constexpr size_t smem_bytes() { return 1024 + (size_t)STAGES * STAGE_BYTES + 256; }
 static_assert(STAGES * STAGE_BYTES + 1024 + 256 <= 227 * 1024, "shared memory");
 
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (failed) {
         // Shared memory must not be released under copies still landing.
         for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-          if (!mbar_wait_bounded(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1), kWait)) atomicOr(g.err, 4);
+          if (!mbar_wait_bounded(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1), kWait)) atomicOr(g.err, kErrWait);
       }
     }
   } else if (warp == 1) {
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       // phase has already completed and the wait returns at once).
       if (issued > 0) {
         const int kb = issued - 1;
-        if (!mbar_wait_bounded(&accf[kb & 1], (uint32_t)((kb >> 1) & 1), kWait)) atomicOr(g.err, 2);
+        if (!mbar_wait_bounded(&accf[kb & 1], (uint32_t)((kb >> 1) & 1), kWait)) atomicOr(g.err, kErrWait);
       }
     }
   } else if (warp >= 4) {
@@ -290,9 +291,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (kb > 0 && !fold(kb - 1)) failed = true;
     }
     if (!failed && nkb > 0 && !fold(nkb - 1)) failed = true;
+    // A warp that gave up a wait writes NaN over its rows, so a caller that
+    // does not read the status word still cannot take the tile for a result.
+    if (failed) {
+#pragma unroll
+      for (int i = 0; i < BN; ++i) run[i] = __int_as_float(0x7fc00000);
+    }
     // This warp's 32 TMEM lanes are tile rows 32 * wl + lane.
     const int64_t row = m0 + 32 * wl + lane;
-    if (!failed && row < g.M) {
+    if (row < g.M) {
       const int64_t ncol = g.N - n0;
       if (gridDim.z > 1) {
         float* dst = static_cast<float*>(g.C) + (int64_t)blockIdx.z * g.M * g.N + row * g.N + n0;
@@ -319,7 +326,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   }
-  if (failed) atomicOr(g.err, 1);
+  if (failed) atomicOr(g.err, kErrWait);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();

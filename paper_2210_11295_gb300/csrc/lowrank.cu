@@ -99,6 +99,7 @@ int read_status(const Dla& d, int* host) {
 }
 
 int status_to_code(int s) {
+  if (s & kStatusTcWait) return BSRHT_ETIMEDOUT;
   if (s & kStatusNotPD) return BSRHT_ENOTPD;
   if (s & kStatusNoConv) return BSRHT_ENOCONV;
   return BSRHT_OK;
@@ -180,6 +181,7 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
     TRY(chol_inv(d, b.G, b.LT1, b.Rinv, b.Ug, b.Vg, l));
     int hs = 0;
     TRY(read_status(d, &hs));
+    if (hs & kStatusTcWait) return BSRHT_ETIMEDOUT;
     if (hs) {
       fast = false;
       BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
@@ -193,6 +195,7 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
       TRY(chol_inv(d, b.G, b.LT2, b.Rinv, b.Ug, b.Vg, l));
       int hs = 0;
       TRY(read_status(d, &hs));
+      if (hs & kStatusTcWait) return BSRHT_ETIMEDOUT;
       if (hs) {
         fast = false;
         BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
@@ -265,7 +268,7 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
       TRY(chol_inv(d, b.G, b.LT1, b.Rinv, b.Ug, b.Vg, l));
       int hs = 0;
       TRY(read_status(d, &hs));
-      if (hs) return BSRHT_ENOTPD;
+      if (hs) return status_to_code(hs) != BSRHT_OK ? status_to_code(hs) : BSRHT_ENOTPD;
       if (tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
     }
     TRY(gemm_c(d, ar, tc, tc, tc, rows, l, l, src, l, false, RinvB, l, dst, l, true, false));
@@ -708,6 +711,7 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
     BSRHT_CUDA_TRY(cudaMemcpyAsync(&ratio, pr, sizeof(double), cudaMemcpyDeviceToHost, d.s));
     int hs = 0;
     TRY(read_status(d, &hs));
+    if (hs & kStatusTcWait) return BSRHT_ETIMEDOUT;
     if ((hs & kStatusNotPD) || !(ratio > tau_core)) {
       use_eig = true;
       BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
