@@ -88,10 +88,12 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
 // only tiles on or above the diagonal are formed and the rest mirrored.
 // A and Bt need 16-byte aligned rows (gemm_tc_eligible).
 // b_upper: B is upper triangular (B[k][n] = 0 for k > n); the zero K blocks
-// of each N tile are skipped.
+// of each N tile are skipped.  Ct (optional, FP32 output, not gram): also
+// Ct[j * M + i] = C[i][j], the transposed copy (N x M) that tall Gram
+// products read.
 int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, DT tb,
             const void* B, int64_t ldb, bool b_kmajor, DT tc_out, void* C, int64_t ldc, bool gram,
-            bool b_upper = false);
+            bool b_upper = false, float* Ct = nullptr);
 bool gemm_tc_eligible(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda);
 // Bt (N x ldk, FP32) = B^T for B K x N (FP32 or FP64, ldb); Bt[:, K:ldk] = 0.
 int transpose_to_f32(const Dla& d, DT tb, const void* B, int64_t K, int64_t N, int64_t ldb, float* Bt, int64_t ldk,

@@ -44,7 +44,7 @@ __global__ void k_transpose_f32(const TB* __restrict__ B, int64_t K, int64_t N, 
 // skipped below the diagonal are read from their mirror images.
 template <typename TC>
 __global__ void k_tc_reduce(const float* __restrict__ P, TC* __restrict__ C, int64_t M, int64_t N, int64_t ldc,
-                            int splits, int gram) {
+                            int splits, int gram, float* __restrict__ Ct, int64_t ldct) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= M * N) return;
   const int64_t i = idx / N, j = idx - i * N;
@@ -56,6 +56,7 @@ __global__ void k_tc_reduce(const float* __restrict__ P, TC* __restrict__ C, int
   double s = 0.0;
   for (int z = 0; z < splits; ++z) s += (double)P[(int64_t)z * M * N + si * N + sj];
   C[i * ldc + j] = (TC)s;
+  if (Ct) Ct[j * ldct + i] = (float)(TC)s;
 }
 
 template <typename TC, bool PRE>
@@ -90,9 +91,11 @@ int transpose_to_f32(const Dla& d, DT tb, const void* B, int64_t K, int64_t N, i
 }
 
 int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, DT tb,
-            const void* B, int64_t ldb, bool b_kmajor, DT tc_out, void* C, int64_t ldc, bool gram, bool b_upper) {
+            const void* B, int64_t ldb, bool b_kmajor, DT tc_out, void* C, int64_t ldc, bool gram, bool b_upper,
+            float* Ct) {
   if (M <= 0 || N <= 0) return BSRHT_OK;
   if (tc_out != DT::F32 && tc_out != DT::F64) return BSRHT_EUNSUP;
+  if (Ct && (gram || tc_out != DT::F32)) return BSRHT_EINVAL;
   const float* Bt = static_cast<const float*>(B);
   const float* Btlo = nullptr;
   int64_t ldk = ldb;
@@ -149,7 +152,8 @@ int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const floa
   }
   if (tm * tn > 0x7FFFFFFF) return BSRHT_EUNSUP;
   dim3 grid((unsigned)(tm * tn), 1u, (unsigned)splits);
-  tc::GemmTcArgs g{M, N, K, splits > 1 ? (void*)P : C, ldc, gram ? 1 : 0, err, (b_upper && !gram) ? 1 : 0};
+  tc::GemmTcArgs g{M,   N,   K,  splits > 1 ? (void*)P : C, ldc, gram ? 1 : 0, err, (b_upper && !gram) ? 1 : 0,
+                   splits > 1 ? nullptr : Ct, M};
   const bool f32_out = tc_out == DT::F32 || splits > 1;
   int st = pre ? (f32_out ? launch_tc<float, true>(d, ma, mb, mblo, g, grid)
                           : launch_tc<double, true>(d, ma, mb, mblo, g, grid))
@@ -160,9 +164,11 @@ int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const floa
   if (splits > 1) {
     const unsigned nb = (unsigned)((M * N + 255) / 256);
     if (tc_out == DT::F32)
-      k_tc_reduce<float><<<nb, 256, 0, d.s>>>(P, static_cast<float*>(C), M, N, ldc, (int)splits, gram ? 1 : 0);
+      k_tc_reduce<float><<<nb, 256, 0, d.s>>>(P, static_cast<float*>(C), M, N, ldc, (int)splits, gram ? 1 : 0, Ct,
+                                              M);
     else
-      k_tc_reduce<double><<<nb, 256, 0, d.s>>>(P, static_cast<double*>(C), M, N, ldc, (int)splits, gram ? 1 : 0);
+      k_tc_reduce<double><<<nb, 256, 0, d.s>>>(P, static_cast<double*>(C), M, N, ldc, (int)splits, gram ? 1 : 0,
+                                               nullptr, M);
     BSRHT_CUDA_TRY(cudaGetLastError());
     ++launches;
   }

@@ -30,6 +30,8 @@
 // 3-stage ring.  gridDim.z > 1 splits K: CTA z writes an FP32 partial to
 // C + z * M * N (leading dimension N) for a fixed-order FP64 reduce.  With
 // `gram` set (C = A A^T) tiles entirely below the diagonal are skipped.
+// With Ct set the epilogue also stores C^T in FP32 (the operand layout of a
+// following Gram product, which then needs no transpose pass).
 #pragma once
 
 #include <cuda.h>
@@ -120,6 +122,8 @@ struct GemmTcArgs {
   int gram;
   int* err;
   int b_upper;  // B[k][n] = 0 for k > n: the N tile at n0 stops at K = n0 + BN
+  float* Ct;    // optional FP32 copy of C transposed (N x M, leading dimension ldct)
+  int64_t ldct;
 };
 
 __host__ __device__ __forceinline__ bool tile_below_diagonal(int64_t bm, int64_t bn) {
@@ -322,6 +326,14 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int q = 0; q < BN; ++q)
             if (q < ncol) dst[q] = (TC)run[q];
+        }
+        if (g.Ct != nullptr) {
+          // Column q of the tile is row n0 + q of C^T; lane = row of C, so
+          // each store of the warp covers 32 consecutive floats.
+          float* ct = g.Ct + n0 * g.ldct + row;
+#pragma unroll
+          for (int q = 0; q < BN; ++q)
+            if (q < ncol) ct[(int64_t)q * g.ldct] = run[q];
         }
       }
     }

@@ -61,13 +61,19 @@ bool use_tc(DT tc, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda) 
   return tc == DT::F32 && M >= 256 && gemm_tc_eligible(M, N, K, A, lda);
 }
 
+// With Ct (FP32 output only) the tensor-core path also writes C^T (N x M)
+// there and sets *ct_done; the CUDA-core path leaves *ct_done false.
 int tall_gemm(const Dla& d, Arena& ar, DT ta, DT tc, DT tout, int64_t M, int64_t N, int64_t K, const void* A,
-              int64_t lda, const double* B64, const void* B32, int64_t ldb, void* C, int64_t ldc, bool tri_b) {
+              int64_t lda, const double* B64, const void* B32, int64_t ldb, void* C, int64_t ldc, bool tri_b,
+              float* Ct = nullptr, bool* ct_done = nullptr) {
+  if (ct_done) *ct_done = false;
   if (ta == DT::F32 && use_tc(tc, M, N, K, A, lda) && B64 != nullptr) {
+    if (tout != DT::F32) Ct = nullptr;
     const size_t mk = ar.mark();
     const int st = gemm_tc(d, ar, M, N, K, static_cast<const float*>(A), lda, DT::F64, B64, ldb, false, tout, C, ldc,
-                           false, tri_b);
+                           false, tri_b, Ct);
     ar.release(mk);
+    if (st == BSRHT_OK && ct_done) *ct_done = Ct != nullptr;
     return st;
   }
   return gemm_c(d, ar, ta, tc, tout, M, N, K, A, lda, false, tc == DT::F64 ? (const void*)B64 : B32, ldb, C, ldc,
@@ -75,11 +81,12 @@ int tall_gemm(const Dla& d, Arena& ar, DT ta, DT tc, DT tout, int64_t M, int64_t
 }
 
 // G (l x l, FP64) = X^T X for the tall X (rows x l, type tc); the tensor-core
-// path writes X^T into `scratch` (rows x l elements) first.
+// path writes X^T into `scratch` (rows x l elements) first, unless have_t
+// says the product that formed X already left X^T (FP32) there.
 int tall_gram(const Dla& d, Arena& ar, bool dry, DT tc, const void* X, int64_t rows, int64_t l, void* scratch,
-              double* G) {
+              double* G, bool have_t = false) {
   if (use_tc(tc, l, l, rows, scratch, rows) && (rows % 4) == 0 && (l % 4) == 0) {
-    if (!dry) {
+    if (!dry && !have_t) {
       const int st = transpose_to_f32(d, DT::F32, X, rows, l, l, static_cast<float*>(scratch), rows);
       if (st != BSRHT_OK) return st;
     }
@@ -170,13 +177,13 @@ OrthBufs take_orth_bufs(Arena& ar, int64_t l, size_t cs) {
 // less).  *Rinv_out is nullptr when Q is explicit.
 int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void* Z, int64_t rows, int64_t l,
                 uint64_t seed, const OrthBufs& b, double* R, bool need_q, bool keep_x, void** Qout,
-                const double** Rinv_out = nullptr) {
+                const double** Rinv_out = nullptr, bool x_t_in_z = false) {
   const void* RinvB = (tc == DT::F32) ? b.Rinv_c : (const void*)b.Rinv;
   if (Rinv_out) *Rinv_out = nullptr;
   // ---- fast path: CholeskyQR2 (Z serves as scratch for the transposed Grams)
   bool fast = true;
   // (b.Ug and b.Vg, used only by the fallback, are the scratch of chol_inv.)
-  TRY(tall_gram(d, ar, dry, tc, X, rows, l, Z, b.G));
+  TRY(tall_gram(d, ar, dry, tc, X, rows, l, Z, b.G, x_t_in_z));
   if (!dry) {
     TRY(chol_inv(d, b.G, b.LT1, b.Rinv, b.Ug, b.Vg, l));
     int hs = 0;
@@ -189,8 +196,12 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
   }
   if (fast || dry) {
     if (!dry && tc == DT::F32) TRY(cast_copy(d, DT::F64, b.Rinv, DT::F32, b.Rinv_c, l * l));
-    TRY(tall_gemm(d, ar, tc, tc, tc, rows, l, l, X, l, b.Rinv, RinvB, l, Y, l, true));
-    TRY(tall_gram(d, ar, dry, tc, Y, rows, l, Z, b.G));
+    // Y = X R1^-1, leaving Y^T in Z (the first Gram is done with it) for the
+    // second Gram.
+    bool y_t = false;
+    TRY(tall_gemm(d, ar, tc, tc, tc, rows, l, l, X, l, b.Rinv, RinvB, l, Y, l, true,
+                  tc == DT::F32 ? static_cast<float*>(Z) : nullptr, &y_t));
+    TRY(tall_gram(d, ar, dry, tc, Y, rows, l, Z, b.G, y_t));
     if (!dry) {
       TRY(chol_inv(d, b.G, b.LT2, b.Rinv, b.Ug, b.Vg, l));
       int hs = 0;
@@ -331,13 +342,15 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
     Qa = Qc;
   }
   // Step 3: the paper's Z = Q^T A_paper, i.e. Z^T = A Q (n x l): second pass over A.
-  TRY(tall_gemm(d, ar, ta, tc, tc, n, l, m, A, lda, Q, Qa, l, W1, l, false));
+  bool w_t = false;  // W1^T left in W3, the Gram scratch of the QR below
+  TRY(tall_gemm(d, ar, ta, tc, tc, n, l, m, A, lda, Q, Qa, l, W1, l, false,
+                tc == DT::F32 ? static_cast<float*>(W3) : nullptr, &w_t));
   if (!dry) trace_mark(d.s, "second_pass");
   // Step 4: Z^T = P R (CholeskyQR2, rank-robust).  On the CholeskyQR2 path P
   // stays factored, P = P1 R2^{-1} (Rinv2 != nullptr).
   void* Pv = nullptr;
   const double* Rinv2 = nullptr;
-  TRY(orth_robust(d, ar, dry, tc, W1, W2, W3, n, l, seed ^ 0x52ull, ob, R, true, false, &Pv, &Rinv2));
+  TRY(orth_robust(d, ar, dry, tc, W1, W2, W3, n, l, seed ^ 0x52ull, ob, R, true, false, &Pv, &Rinv2, w_t));
   if (!dry) trace_mark(d.s, "tall_qr");
   // Step 5: SVD of R^T = U~ Sigma~ V~^T.  FP64 data: Jacobi on the columns
   // of R^T (the rows of R) to FP64 tolerance.  FP32 data: Jacobi on the
@@ -478,14 +491,15 @@ int srsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, 
     TRY(transpose_cast(d, DT::F64, Gm, l, m, ldg, DT::F64, GT, l));        // Gamma^T (m x l)
     if (tc == DT::F32) TRY(cast_copy(d, DT::F64, GT, DT::F32, GTc, m * l));
   }
+  bool x_t = false;  // X^T left in X3, the Gram scratch of orth(X)
   TRY(tall_gemm(d, ar, ta, tc, tc, n, l, m, A, lda, GT, tc == DT::F32 ? GTc : (const void*)GT, l, X1, l,
-                false));                                                    // X = A Gamma^T (n x l)
+                false, tc == DT::F32 ? static_cast<float*>(X3) : nullptr, &x_t));  // X = A Gamma^T (n x l)
   // Step 2: Q = orth(Y) in FP64, P = orth(X).
   void* Qv = nullptr;
   TRY(orth_robust(d, ar, dry, DT::F64, Y1, Y2, Y3, m, l, seed ^ 0x61ull, ob, nullptr, true, false, &Qv));
   const double* Q = static_cast<const double*>(Qv);
   void* Pv = nullptr;
-  TRY(orth_robust(d, ar, dry, tc, X1, X2, X3, n, l, seed ^ 0x62ull, ob, nullptr, true, false, &Pv));
+  TRY(orth_robust(d, ar, dry, tc, X1, X2, X3, n, l, seed ^ 0x62ull, ob, nullptr, true, false, &Pv, nullptr, x_t));
   if (!dry) trace_mark(d.s, "orth");
   // Step 3: Phi Q and Psi P (s x l).
   if (!dry) {
@@ -723,10 +737,12 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
   if (!dry && tc == DT::F32) TRY(cast_copy(d, DT::F64, Y64, DT::F32, B, n * l));
   if (tc == DT::F32) Ynu = B;
   void* Z = Y;
+  bool z_t = false;  // Z^T left in Z3, the Gram scratch of the QR of step 4
+  float* const Zt = tc == DT::F32 ? static_cast<float*>(Z3) : nullptr;
   if (!use_eig || dry) {
     if (!dry && tc == DT::F32) TRY(cast_copy(d, DT::F64, Cinv, DT::F32, Cinv_c, l * l));
     TRY(tall_gemm(d, ar, tc, tc, tc, n, l, l, Ynu, l, Cinv, tc == DT::F32 ? Cinv_c : (const void*)Cinv, l, Z, l,
-                  true));
+                  true, Zt, &z_t));
   }
   int64_t lr = l;  // columns of Z (the kept rank on the SVD square root path)
   if (use_eig) {
@@ -756,14 +772,14 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
     }
     // Z = Y_nu V_r lambda_r^-1/2, n x lr (contiguous, leading dimension lr).
     TRY(tall_gemm(d, ar, tc, tc, tc, n, lr, l, Ynu, l, Cinv, tc == DT::F32 ? Cinv_c : (const void*)Cinv, l, Z, lr,
-                  false));
+                  false, Zt, &z_t));
   }
   if (!dry) trace_mark(d.s, "z");
   // Step 4: R factor of Z (CholeskyQR2, rank-robust); Z itself is kept for step 6.
   {
     void* scratch = (tc == DT::F32) ? B : (void*)Y64;
     void* Qv = nullptr;
-    TRY(orth_robust(d, ar, dry, tc, Z, scratch, Z3, n, lr, seed ^ 0x53ull, ob, R, false, true, &Qv));
+    TRY(orth_robust(d, ar, dry, tc, Z, scratch, Z3, n, lr, seed ^ 0x53ull, ob, R, false, true, &Qv, nullptr, z_t));
   }
   if (!dry) trace_mark(d.s, "tall_qr");
   // Step 5: SVD of R = U~ Sigma~ V~^T (Jacobi on the columns of R, i.e. rows of R^T).
