@@ -109,7 +109,7 @@ int sketch_launch_f64(const SketchPlan& plan, const SketchArgs& a, void* out, in
                       cudaStream_t stream);
 int sketch_occupancy_f32(const SketchPlan& plan);
 int sketch_occupancy_f64(const SketchPlan& plan);
-// TMA-fed path (sketch_tma.cu): W = 32, NT = 512, R2 = 512, JM in {32, 64}.
+// TMA-fed path (sketch_tma.cu): W = 32, NT = 512, R2 = 512, JM in {32, 48, 64}.
 int sketch_occupancy_tma(const SketchPlan& plan);
 int sketch_launch_tma(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo, int* err,
                       uint64_t* dtab, uint64_t* dttab, cudaStream_t stream);

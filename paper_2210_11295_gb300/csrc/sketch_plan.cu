@@ -60,7 +60,7 @@ static int make_plan_tma(SketchPlan& pl, bool query_device) {
   pl.W = 32;
   pl.NT = 512;
   pl.R2 = 512;
-  pl.JM = pl.l <= 512 ? 32 : 64;
+  pl.JM = pl.l <= 512 ? 32 : pl.l <= 768 ? 48 : 64;
   pl.NRL = pl.NT / pl.W;
   pl.jgroup = std::min<int64_t>(pl.l, (int64_t)pl.JM * pl.NRL);
   pl.nch = (pl.rb + pl.R2 - 1) / pl.R2;

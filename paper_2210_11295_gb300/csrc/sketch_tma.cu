@@ -620,12 +620,13 @@ EncodeFn encode_fn() {
 }
 
 // l <= 512 (JM = 32): 512 threads of 32 values (more warps hide the
-// shared-memory latency); l > 512 (JM = 64): 256 threads of 64 values, whose
-// 255-register budget holds the 128 accumulators without spilling much.
+// shared-memory latency); l > 512: 256 threads of 64 values, whose
+// 255-register budget holds the accumulators -- 96 for l <= 768 (JM = 48,
+// sketch-row groups of 768), 128 for larger l (JM = 64, groups of 1024).
 template <typename Tin, int JM>
 struct TmaKernel {
   static constexpr int STAGES = stages_for<Tin>();
-  static constexpr bool k256 = JM == 64;
+  static constexpr bool k256 = JM > 32;
   static constexpr int NT = k256 ? 256 : 512;
   static size_t smem() {
     if constexpr (k256)
@@ -680,6 +681,27 @@ int occ_tma() {
   return occ;
 }
 
+template <typename Tin>
+int occ_tma_jm(int jm) {
+  switch (jm) {
+    case 32: return occ_tma<Tin, 32>();
+    case 48: return occ_tma<Tin, 48>();
+    case 64: return occ_tma<Tin, 64>();
+  }
+  return 0;
+}
+
+template <typename Tin>
+int launch_tma_jm(const SketchPlan& plan, const SketchArgs& a, const CUtensorMap& map, int* err, uint64_t* dtab,
+                  uint64_t* dttab, void* out, int64_t ldo, cudaStream_t stream) {
+  switch (plan.JM) {
+    case 32: return launch_tma<Tin, 32>(plan, a, map, err, dtab, dttab, out, ldo, stream);
+    case 48: return launch_tma<Tin, 48>(plan, a, map, err, dtab, dttab, out, ldo, stream);
+    case 64: return launch_tma<Tin, 64>(plan, a, map, err, dtab, dttab, out, ldo, stream);
+  }
+  return BSRHT_EINVAL;
+}
+
 }  // namespace
 
 bool make_tensor_map_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dtype, size_t elem_bytes,
@@ -698,9 +720,9 @@ bool make_tensor_map_2d(CUtensorMap* map, const void* base, CUtensorMapDataType 
 
 int sketch_occupancy_tma(const SketchPlan& plan) {
   switch (plan.dtype) {
-    case BSRHT_F32: return plan.JM == 32 ? occ_tma<float, 32>() : occ_tma<float, 64>();
-    case BSRHT_BF16: return plan.JM == 32 ? occ_tma<__nv_bfloat16, 32>() : occ_tma<__nv_bfloat16, 64>();
-    case BSRHT_F16: return plan.JM == 32 ? occ_tma<__half, 32>() : occ_tma<__half, 64>();
+    case BSRHT_F32: return occ_tma_jm<float>(plan.JM);
+    case BSRHT_BF16: return occ_tma_jm<__nv_bfloat16>(plan.JM);
+    case BSRHT_F16: return occ_tma_jm<__half>(plan.JM);
   }
   return 0;
 }
@@ -716,15 +738,9 @@ int sketch_launch_tma(const SketchPlan& plan, const SketchArgs& a, void* out, in
                           256))
     return BSRHT_EUNSUP;
   switch (plan.dtype) {
-    case BSRHT_F32:
-      return plan.JM == 32 ? launch_tma<float, 32>(plan, a, map, err, dtab, dttab, out, ldo, stream)
-                           : launch_tma<float, 64>(plan, a, map, err, dtab, dttab, out, ldo, stream);
-    case BSRHT_BF16:
-      return plan.JM == 32 ? launch_tma<__nv_bfloat16, 32>(plan, a, map, err, dtab, dttab, out, ldo, stream)
-                           : launch_tma<__nv_bfloat16, 64>(plan, a, map, err, dtab, dttab, out, ldo, stream);
-    case BSRHT_F16:
-      return plan.JM == 32 ? launch_tma<__half, 32>(plan, a, map, err, dtab, dttab, out, ldo, stream)
-                           : launch_tma<__half, 64>(plan, a, map, err, dtab, dttab, out, ldo, stream);
+    case BSRHT_F32: return launch_tma_jm<float>(plan, a, map, err, dtab, dttab, out, ldo, stream);
+    case BSRHT_BF16: return launch_tma_jm<__nv_bfloat16>(plan, a, map, err, dtab, dttab, out, ldo, stream);
+    case BSRHT_F16: return launch_tma_jm<__half>(plan, a, map, err, dtab, dttab, out, ldo, stream);
   }
   return BSRHT_EINVAL;
 }

@@ -61,6 +61,9 @@ def _case(lib, n, m, p, l, dtype, seed=0, lda=None, variant=0):
     (256, 9, 64, 32),         # r = 4: direct path for both
     (300, 5, 300, 50),        # r = 1: Rademacher limit
     (2048, 8, 2, 1100),       # l > JG: several sketch-row groups
+    (8192, 40, 4, 600),       # 512 < l <= 768: 768-row groups of the 256-thread TMA kernel
+    (4096, 24, 2, 768),       # the largest l of those groups
+    (4096, 24, 2, 769),       # one more: 1024-row groups
     (512, 3, 4, 512),         # l > r: sampling with replacement
 ])
 def test_sketch_matches_oracle(lib, dtype, n, m, p, l):
@@ -70,7 +73,7 @@ def test_sketch_matches_oracle(lib, dtype, n, m, p, l):
 
 
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
-@pytest.mark.parametrize("n,m,p,l", [(8192, 64, 8, 256), (4096, 50, 2, 128), (1000, 40, 5, 64)])
+@pytest.mark.parametrize("n,m,p,l", [(8192, 64, 8, 256), (4096, 50, 2, 128), (1000, 40, 5, 64), (8192, 64, 8, 700)])
 def test_sketch_half_inputs(lib, dtype, n, m, p, l):
     got, ref = _case(lib, n, m, p, l, dtype)
     assert _rel(got, ref) <= TOL[dtype]
