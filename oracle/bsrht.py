@@ -2,13 +2,13 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-Definitions followed (BASELINE orientation: A is n x m, tall; the sketch is
-B = Omega A with Omega l x n):
+Definitions followed (orientation used throughout: A is n x m, tall; the
+sketch is B = Omega A with Omega l x n):
 
 * eq. 2.3: Omega = [Omega^(1) ... Omega^(p)],
   Omega^(i) = sqrt(r/l) * Dt^(i) R H D^(i), with one sampling matrix R shared
   by all blocks, D^(i) (r x r) and Dt^(i) (l x l) Rademacher diagonals, and H
-  the r x r Walsh-Hadamard matrix scaled by 1/sqrt(r) (Sec. 2, "rescaled by"
+  the r x r Walsh-Hadamard matrix scaled by 1/sqrt(r) (Sec. 2 normalises H by
   the square root of its size; the proof of Thm 2.1 uses the same 1/sqrt(r)).
   Every entry of Omega is therefore +-1/sqrt(l).
 * Sec. 2 (paragraph after eq. 2.4): R samples uniformly *with replacement*.
@@ -180,8 +180,8 @@ def sketch_dense(a: np.ndarray, p: int, l: int, seed: int,
 def fwht_rows(x: np.ndarray) -> np.ndarray:
     """Unnormalised Walsh-Hadamard transform along axis 0 (natural order).
 
-    Butterflies (u, v) -> (u + v, u - v) over every bit of the row index, the
-    "arrays of butterflies" of the tensor form in Sec. 2.
+    Butterflies (u, v) -> (u + v, u - v) over every bit of the row index: one
+    2 x 2 Kronecker factor of the tensor form of H (Sec. 2) per bit.
     """
     x = np.array(x, dtype=np.float64, copy=True)
     r = x.shape[0]
