@@ -77,3 +77,80 @@ def test_workspace_query_scales():
     assert 0 < w1 < 256 << 20 and 0 < w2 < 512 << 20
     # Tiny blocks take the direct path, which needs no scratch.
     assert b.bsrht_sketch_workspace(64, 8, 64, 16, torch.float32) == 0
+
+
+def _opts(dtype, variant=0):
+    import paper_2210_11295_gb300 as b
+    from paper_2210_11295_gb300 import _binding as bb
+    o = bb.Opts()
+    b.lib.bsrht_opts_init(ctypes.byref(o))
+    o.dtype = dtype
+    o.variant = variant
+    return o
+
+
+@pytest.mark.parametrize("n,m,k,l,p", [
+    (1000, 64, 10, 5, 2),     # k > l
+    (1000, 64, 10, 65, 2),    # l > m
+    (40, 64, 10, 48, 2),      # l > n
+    (1000, 64, 0, 8, 2),      # k = 0
+    (1000, 64, 4, 8, 0),      # p = 0
+    (1000, 64, 4, 8, 1001),   # p > n
+])
+def test_rsvd_rejects_bad_sizes_before_any_device_work(n, m, k, l, p):
+    """Algorithm 1 needs 1 <= k <= l <= min(n, m) and 1 <= p <= n; the
+    workspace query and the call itself (with placeholder pointers that are
+    never dereferenced) return EINVAL on the host."""
+    import paper_2210_11295_gb300 as b
+    from paper_2210_11295_gb300 import _binding as bb
+    o = _opts(bb.F32)
+    out = ctypes.c_size_t(0)
+    assert b.lib.bsrht_rsvd_workspace(n, m, k, l, p, ctypes.byref(o), ctypes.byref(out)) == bb.BSRHT_EINVAL
+    fake, dfake = ctypes.c_void_p(256), ctypes.cast(ctypes.c_void_p(256), ctypes.POINTER(ctypes.c_double))
+    assert b.lib.bsrht_rsvd(fake, n, m, k, l, p, 0, dfake, dfake, dfake, ctypes.byref(o)) == bb.BSRHT_EINVAL
+
+
+@pytest.mark.parametrize("n,m,k,l,s,p,dtype,status", [
+    (1000, 64, 10, 20, 65, 2, "F32", -22),    # s > min(n, m)
+    (1000, 64, 10, 30, 20, 2, "F32", -22),    # l > s
+    (1000, 64, 21, 20, 40, 2, "F32", -22),    # k > l
+    (1000, 64, 10, 20, 40, 2, "BF16", -95),   # 16-bit A: not supported by Algorithm 3 here
+])
+def test_srsvd_rejects_before_any_device_work(n, m, k, l, s, p, dtype, status):
+    import paper_2210_11295_gb300 as b
+    from paper_2210_11295_gb300 import _binding as bb
+    o = _opts(getattr(bb, dtype))
+    out = ctypes.c_size_t(0)
+    assert b.lib.bsrht_srsvd_workspace(n, m, k, l, s, p, ctypes.byref(o), ctypes.byref(out)) == status
+    fake, dfake = ctypes.c_void_p(256), ctypes.cast(ctypes.c_void_p(256), ctypes.POINTER(ctypes.c_double))
+    assert b.lib.bsrht_srsvd(fake, n, m, k, l, s, p, 0, dfake, dfake, dfake, ctypes.byref(o)) == status
+
+
+def test_nystrom_rejects_before_any_device_work():
+    import paper_2210_11295_gb300 as b
+    from paper_2210_11295_gb300 import _binding as bb
+    out = ctypes.c_size_t(0)
+    fake, dfake = ctypes.c_void_p(256), ctypes.cast(ctypes.c_void_p(256), ctypes.POINTER(ctypes.c_double))
+    o = _opts(bb.F32)
+    for n, k, l, p in ((500, 10, 600, 8), (500, 11, 10, 2), (500, 4, 8, 0)):  # l > n, k > l, p = 0
+        assert b.lib.bsrht_nystrom_workspace(n, k, l, p, ctypes.byref(o), ctypes.byref(out)) == bb.BSRHT_EINVAL
+        assert b.lib.bsrht_nystrom(fake, n, k, l, p, 0, dfake, dfake, ctypes.byref(o)) == bb.BSRHT_EINVAL
+    o = _opts(bb.F32, b.VARIANT_GAUSSIAN)  # the Gaussian comparator covers the sketch and Algorithm 1 only
+    assert b.lib.bsrht_nystrom_workspace(4096, 10, 64, 4, ctypes.byref(o), ctypes.byref(out)) == bb.BSRHT_EUNSUP
+
+
+def test_lowrank_workspace_queries_scale():
+    """Scratch of the low-rank calls grows with the tall dimension and with
+    the element size: the n x l tall factors dominate."""
+    import torch
+    import paper_2210_11295_gb300 as b
+    w20 = b.bsrht_rsvd_workspace(1 << 20, 4096, 100, 512, 4, torch.float32)
+    w19 = b.bsrht_rsvd_workspace(1 << 19, 4096, 100, 512, 4, torch.float32)
+    w64 = b.bsrht_rsvd_workspace(1 << 20, 4096, 100, 512, 4, torch.float64)
+    assert 1.6 < w20 / w19 < 2.1 and w64 > 1.5 * w20
+    # At least the three n x l FP32 tall factors of CholeskyQR2.
+    assert w20 >= 3 * (1 << 20) * 512 * 4
+    ws = b.bsrht_srsvd_workspace(1 << 20, 4096, 100, 512, 1024, 4, torch.float32)
+    assert ws > w20  # Algorithm 3 also holds the on-device transpose of A
+    wn = b.bsrht_nystrom_workspace(65536, 100, 600, 8, torch.float32)
+    assert wn >= 65536 * 600 * 4
