@@ -44,12 +44,12 @@ __global__ void k_transpose_f32(const TB* __restrict__ B, int64_t K, int64_t N, 
 // skipped below the diagonal are read from their mirror images.
 template <typename TC>
 __global__ void k_tc_reduce(const float* __restrict__ P, TC* __restrict__ C, int64_t M, int64_t N, int64_t ldc,
-                            int splits, int gram, float* __restrict__ Ct, int64_t ldct) {
+                            int splits, int gram, int tile_n, float* __restrict__ Ct, int64_t ldct) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= M * N) return;
   const int64_t i = idx / N, j = idx - i * N;
   int64_t si = i, sj = j;
-  if (gram && tc::tile_below_diagonal(i / tc::BM, j / tc::BN)) {
+  if (gram && tc::tile_below_diagonal(i / tc::BM, j / tile_n, tile_n)) {
     si = j;
     sj = i;
   }
@@ -59,15 +59,37 @@ __global__ void k_tc_reduce(const float* __restrict__ P, TC* __restrict__ C, int
   if (Ct) Ct[j * ldct + i] = (float)(TC)s;
 }
 
-template <typename TC, bool PRE>
+template <typename TC, bool PRE, int BNT>
 int launch_tc(const Dla& d, const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mblo, tc::GemmTcArgs g,
               dim3 grid) {
-  const size_t smem = tc::smem_bytes();
-  BSRHT_CUDA_TRY(
-      cudaFuncSetAttribute(tc::k_gemm_tf32x3<TC, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  tc::k_gemm_tf32x3<TC, PRE><<<grid, tc::THREADS, smem, d.s>>>(ma, mb, mblo, g);
+  const size_t smem = tc::Cfg<BNT>::smem_bytes();
+  auto kern = tc::k_gemm_tf32x3<TC, PRE, BNT>;
+  BSRHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, tc::Cfg<BNT>::THREADS, smem, d.s>>>(ma, mb, mblo, g);
   BSRHT_CUDA_TRY(cudaGetLastError());
   return BSRHT_OK;
+}
+
+template <int BNT>
+int launch_tc_any(const Dla& d, bool pre, bool f32_out, const CUtensorMap& ma, const CUtensorMap& mb,
+                  const CUtensorMap& mblo, tc::GemmTcArgs g, dim3 grid) {
+  return pre ? (f32_out ? launch_tc<float, true, BNT>(d, ma, mb, mblo, g, grid)
+                        : launch_tc<double, true, BNT>(d, ma, mb, mblo, g, grid))
+             : (f32_out ? launch_tc<float, false, BNT>(d, ma, mb, mblo, g, grid)
+                        : launch_tc<double, false, BNT>(d, ma, mb, mblo, g, grid));
+}
+
+// Tile width.  256 halves the shared-memory operand traffic per flop, but
+// its 64-byte K rows suit only operands whose rows are close together:
+// measured on GB300, A Q (K = 4096) 21.0 -> 17.9 ms, while the products
+// with K = n (the Grams, the Gaussian sketch: K-major rows megabytes apart)
+// slowed down (Gaussian sketch 53.6 -> 75.9 ms), and a triangular B or a
+// Gram skips less work in wider tiles.  So 256 only for plain products with
+// K <= 16384, and only if padding N to 256 wastes at most N / 8 columns.
+int tile_width(int64_t N, int64_t K, bool gram, bool b_upper) {
+  if (gram || b_upper || K > 16384 || N < 256) return 128;
+  const int64_t pad256 = (N + 255) / 256 * 256 - N;
+  return 8 * pad256 <= N ? 256 : 128;
 }
 
 }  // namespace
@@ -110,11 +132,13 @@ int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const floa
   } else if (tb != DT::F32 || (ldk % 4) != 0) {
     return BSRHT_EUNSUP;
   }
-  const int64_t tm = (M + tc::BM - 1) / tc::BM, tn = (N + tc::BN - 1) / tc::BN;
+  const int tw = tile_width(N, K, gram, b_upper);
+  const int tbk = tw == 128 ? tc::Cfg<128>::BK : tc::Cfg<256>::BK;
+  const int64_t tm = (M + tc::BM - 1) / tc::BM, tn = (N + tw - 1) / tw;
   int64_t tiles = 0;
   for (int64_t bm = 0; bm < tm; ++bm)
-    for (int64_t bn = 0; bn < tn; ++bn) tiles += (gram && tc::tile_below_diagonal(bm, bn)) ? 0 : 1;
-  const int64_t nkb = (K + tc::BK - 1) / tc::BK;
+    for (int64_t bn = 0; bn < tn; ++bn) tiles += (gram && tc::tile_below_diagonal(bm, bn, tw)) ? 0 : 1;
+  const int64_t nkb = (K + tbk - 1) / tbk;
   // Split K when the tiles alone do not fill the GPU, and in any case so
   // that no CTA folds more than 256 K blocks into its FP32 running sums.
   int64_t splits = 1;
@@ -132,15 +156,18 @@ int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const floa
   if (!ar.ok()) return BSRHT_ENOMEM;
   if (ar.measure) return BSRHT_OK;
   CUtensorMap ma, mb, mblo;
-  if (!make_tensor_map_2d(&ma, A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)M, (uint64_t)K, (uint64_t)lda, tc::BK,
-                          tc::BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !make_tensor_map_2d(&mb, Bt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)N, (uint64_t)K, (uint64_t)ldk, tc::BK,
-                          tc::BN, CU_TENSOR_MAP_SWIZZLE_128B))
+  // Box: BK x 128 rows of A, BK x tw rows of B^T; rows of BK floats fill the
+  // swizzle span (128 bytes for tw = 128, 64 bytes for tw = 256).
+  const CUtensorMapSwizzle swz = tw == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  if (!make_tensor_map_2d(&ma, A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)M, (uint64_t)K, (uint64_t)lda,
+                          (uint32_t)tbk, tc::BM, swz) ||
+      !make_tensor_map_2d(&mb, Bt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)N, (uint64_t)K, (uint64_t)ldk,
+                          (uint32_t)tbk, (uint32_t)tw, swz))
     return BSRHT_EUNSUP;
   const bool pre = Btlo != nullptr;
   mblo = mb;
   if (pre && !make_tensor_map_2d(&mblo, Btlo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)N, (uint64_t)K,
-                                 (uint64_t)ldk, tc::BK, tc::BN, CU_TENSOR_MAP_SWIZZLE_128B))
+                                 (uint64_t)ldk, (uint32_t)tbk, (uint32_t)tw, swz))
     return BSRHT_EUNSUP;
   // A failed bounded wait sets kStatusTcWait in the caller's status word when
   // it has one (read back by the low-rank drivers), else in a word of its own.
@@ -155,20 +182,18 @@ int gemm_tc(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const floa
   tc::GemmTcArgs g{M,   N,   K,  splits > 1 ? (void*)P : C, ldc, gram ? 1 : 0, err, (b_upper && !gram) ? 1 : 0,
                    splits > 1 ? nullptr : Ct, M};
   const bool f32_out = tc_out == DT::F32 || splits > 1;
-  int st = pre ? (f32_out ? launch_tc<float, true>(d, ma, mb, mblo, g, grid)
-                          : launch_tc<double, true>(d, ma, mb, mblo, g, grid))
-               : (f32_out ? launch_tc<float, false>(d, ma, mb, mblo, g, grid)
-                          : launch_tc<double, false>(d, ma, mb, mblo, g, grid));
+  const int st = tw == 128 ? launch_tc_any<128>(d, pre, f32_out, ma, mb, mblo, g, grid)
+                           : launch_tc_any<256>(d, pre, f32_out, ma, mb, mblo, g, grid);
   if (st != BSRHT_OK) return st;
   int launches = 1;
   if (splits > 1) {
     const unsigned nb = (unsigned)((M * N + 255) / 256);
     if (tc_out == DT::F32)
-      k_tc_reduce<float><<<nb, 256, 0, d.s>>>(P, static_cast<float*>(C), M, N, ldc, (int)splits, gram ? 1 : 0, Ct,
-                                              M);
+      k_tc_reduce<float><<<nb, 256, 0, d.s>>>(P, static_cast<float*>(C), M, N, ldc, (int)splits, gram ? 1 : 0, tw,
+                                              Ct, M);
     else
       k_tc_reduce<double><<<nb, 256, 0, d.s>>>(P, static_cast<double*>(C), M, N, ldc, (int)splits, gram ? 1 : 0,
-                                               nullptr, M);
+                                               tw, nullptr, M);
     BSRHT_CUDA_TRY(cudaGetLastError());
     ++launches;
   }
