@@ -1097,34 +1097,49 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
 }
 
 // ------------------------------------------------------------ helpers
-template <typename TI, typename TO>
-__global__ void k_transpose_cast(const TI* __restrict__ in, int64_t rows, int64_t cols, int64_t ldin,
-                                 TO* __restrict__ out, int64_t ldout) {
-  __shared__ double t[32][33];
-  const int64_t bc = (int64_t)blockIdx.x * 32, br = (int64_t)blockIdx.y * 32;
+// 64 x 64 tiles through shared memory (TS: float unless a side is double;
+// one padding column keeps both passes free of bank conflicts), 16 elements
+// per thread in flight.  A 1-D grid of tile indices, so any row count fits.
+template <typename TI, typename TO, typename TS>
+__global__ void __launch_bounds__(256) k_transpose_cast(const TI* __restrict__ in, int64_t rows, int64_t cols,
+                                                        int64_t ldin, TO* __restrict__ out, int64_t ldout,
+                                                        int64_t tiles_c) {
+  __shared__ TS t[64][65];
+  const int64_t tr = (int64_t)blockIdx.x / tiles_c, tcol = (int64_t)blockIdx.x - tr * tiles_c;
+  const int64_t br = tr * 64, bc = tcol * 64;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  for (int r = ty; r < 32; r += 8) {
-    const int64_t i = br + r, j = bc + tx;
-    t[r][tx] = (i < rows && j < cols) ? (double)Elem<TI>::to_f64(in[i * ldin + j]) : 0.0;
+#pragma unroll
+  for (int r = ty; r < 64; r += 8) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t i = br + r, j = bc + tx + 32 * h;
+      t[r][tx + 32 * h] = (i < rows && j < cols) ? (TS)in[i * ldin + j] : (TS)0;
+    }
   }
   __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int64_t j = bc + r, i = br + tx;
-    if (i < rows && j < cols) out[j * ldout + i] = (TO)t[tx][r];
+#pragma unroll
+  for (int r = ty; r < 64; r += 8) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t j = bc + r, i = br + tx + 32 * h;
+      if (i < rows && j < cols) out[j * ldout + i] = (TO)t[tx + 32 * h][r];
+    }
   }
 }
 
 int transpose_cast(const Dla& d, DT tin, const void* in, int64_t rows, int64_t cols, int64_t ldin, DT tout,
                    void* out, int64_t ldout) {
   if (rows <= 0 || cols <= 0) return BSRHT_OK;
-  dim3 grid(blocks_for(cols, 32), blocks_for(rows, 32));
-#define TC_CASE(TIT, TOT)                                                                                  \
-  k_transpose_cast<TIT, TOT><<<grid, 256, 0, d.s>>>(static_cast<const TIT*>(in), rows, cols, ldin,         \
-                                                    static_cast<TOT*>(out), ldout)
-  if (tin == DT::F64 && tout == DT::F64) TC_CASE(double, double);
-  else if (tin == DT::F32 && tout == DT::F64) TC_CASE(float, double);
-  else if (tin == DT::F32 && tout == DT::F32) TC_CASE(float, float);
-  else if (tin == DT::F64 && tout == DT::F32) TC_CASE(double, float);
+  const int64_t tiles_c = (cols + 63) / 64, tiles = tiles_c * ((rows + 63) / 64);
+  if (tiles > 0x7FFFFFFF) return BSRHT_EUNSUP;
+  const unsigned grid = (unsigned)tiles;
+#define TC_CASE(TIT, TOT, TST)                                                                           \
+  k_transpose_cast<TIT, TOT, TST><<<grid, 256, 0, d.s>>>(static_cast<const TIT*>(in), rows, cols, ldin, \
+                                                         static_cast<TOT*>(out), ldout, tiles_c)
+  if (tin == DT::F64 && tout == DT::F64) TC_CASE(double, double, double);
+  else if (tin == DT::F32 && tout == DT::F64) TC_CASE(float, double, float);
+  else if (tin == DT::F32 && tout == DT::F32) TC_CASE(float, float, float);
+  else if (tin == DT::F64 && tout == DT::F32) TC_CASE(double, float, double);
   else return BSRHT_EUNSUP;
 #undef TC_CASE
   DLA_LAUNCH_CHECK();

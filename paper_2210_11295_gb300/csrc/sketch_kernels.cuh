@@ -317,49 +317,47 @@ __global__ void k_sketch_reduce_grouped(const __grid_constant__ SketchGroup grp)
 }
 
 // Fixed-order reduce of the TMA-fed kernels' partials; NaN output if any CTA
-// reported a failed wait.  One thread per (sketch row, column panel): the
-// panel's slot range is worked out once (64-bit divisions), each slot is one
-// contiguous run of W floats, and the W sums stay in registers.  Launch with
-// jn * P threads; consecutive threads take consecutive rows of one panel, so
-// the slot loop is warp-uniform.
+// reported a failed wait.  One warp per (column panel, group of kReduceRows
+// sketch rows), lane = column of the panel (W = 32): every slot row read and
+// every output row written is one contiguous 128-byte run, and the panel's
+// slot range (64-bit divisions) is found once per warp.  Each entry is summed
+// over the slots in CTA order.  Launch with
+// ceil(jn / kReduceRows) * P * 32 threads.
+constexpr int kReduceRows = 8;
 template <int W>
 __global__ void k_sketch_reduce_checked(SketchArgs g, float* __restrict__ out, int64_t ldo, float scale,
                                         const int* __restrict__ err) {
-  static_assert(W % 4 == 0, "panel width");
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.jn * g.P) return;
-  const int64_t pc = idx / g.jn;
-  const int64_t jl = idx - pc * g.jn;
-  const int64_t c0 = pc * W;
-  const int64_t left = g.m - c0;
-  const int nc = left < W ? (int)left : W;
-  float* o = out + (g.j0 + jl) * ldo + c0;
+  static_assert(W == 32, "one lane per panel column");
+  constexpr int RG = kReduceRows;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t nrg = (g.jn + RG - 1) / RG;
+  if (gw >= nrg * g.P) return;  // warp-uniform
+  const int64_t pc = gw / nrg;
+  const int64_t jb = (gw - pc * nrg) * RG;
+  const int nr = (int)(g.jn - jb < RG ? g.jn - jb : RG);
+  const int64_t col = pc * W + lane;
+  const bool colok = col < g.m;
+  float* o = out + (g.j0 + jb) * ldo + col;
   if (*err) {
-    for (int cw = 0; cw < nc; ++cw) o[cw] = __int_as_float(0x7fc00000);
+    for (int r = 0; r < nr; ++r)
+      if (colok) o[(int64_t)r * ldo] = __int_as_float(0x7fc00000);
     return;
   }
-  float s[W];
+  float s[RG];
 #pragma unroll
-  for (int cw = 0; cw < W; ++cw) s[cw] = 0.f;
+  for (int r = 0; r < RG; ++r) s[r] = 0.f;
   const float* part = static_cast<const float*>(g.part);
   for_panel_slots(g, pc, [&](int64_t slot) {
-    const float4* v = reinterpret_cast<const float4*>(part + (slot * g.jn + jl) * W);
+    const float* v = part + (slot * g.jn + jb) * W + lane;
 #pragma unroll
-    for (int q = 0; q < W / 4; ++q) {
-      const float4 x = v[q];
-      s[4 * q] += x.x;
-      s[4 * q + 1] += x.y;
-      s[4 * q + 2] += x.z;
-      s[4 * q + 3] += x.w;
-    }
+    for (int r = 0; r < RG; ++r)
+      if (r < nr) s[r] += v[(int64_t)r * W];
   });
-  if (nc == W) {
+  if (colok) {
 #pragma unroll
-    for (int cw = 0; cw < W; ++cw) o[cw] = s[cw] * scale;
-  } else {
-#pragma unroll
-    for (int cw = 0; cw < W; ++cw)
-      if (cw < nc) o[cw] = s[cw] * scale;
+    for (int r = 0; r < RG; ++r)
+      if (r < nr) o[(int64_t)r * ldo] = s[r] * scale;
   }
 }
 

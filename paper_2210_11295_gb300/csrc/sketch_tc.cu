@@ -434,7 +434,7 @@ int launch_tc(const SketchPlan& plan, const SketchArgs& a, int* err, void* out, 
   kern<<<plan.G, kNT, smem, stream>>>(map, a, err);
   BSRHT_CUDA_TRY(cudaGetLastError());
   trace_mark(stream, "sketch_kernel");
-  const int64_t total = a.jn * a.P;  // one reduce thread per (sketch row, panel)
+  const int64_t total = (a.jn + kReduceRows - 1) / kReduceRows * a.P * 32;  // one warp per (row group, panel)
   const float scale = (float)(1.0 / sqrt((double)plan.l));
   k_sketch_reduce_checked<kW><<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(a, static_cast<float*>(out), ldo,
                                                                                    scale, err);

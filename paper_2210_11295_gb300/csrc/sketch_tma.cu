@@ -660,7 +660,7 @@ int launch_tma(const SketchPlan& plan, const SketchArgs& a, const CUtensorMap& m
   kern<<<plan.G, NT, smem, stream>>>(map, a, dmtab, dttab, tw, err);
   BSRHT_CUDA_TRY(cudaGetLastError());
   trace_mark(stream, "sketch_kernel");
-  const int64_t total = a.jn * a.P;  // one reduce thread per (sketch row, panel)
+  const int64_t total = (a.jn + kReduceRows - 1) / kReduceRows * a.P * 32;  // one warp per (row group, panel)
   const float scale = (float)(1.0 / sqrt((double)plan.l));
   k_sketch_reduce_checked<W><<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(a, static_cast<float*>(out), ldo,
                                                                                   scale, err);
