@@ -18,24 +18,36 @@ namespace {
 // Bt[n][k] = B[k][n] in FP32 (B is K x N, FP32 or FP64, leading dimension
 // ldb); columns k in [K, ldk) are zero.  With Blo != nullptr also
 // Blo[n][k] = Bt[n][k] - (Bt[n][k] with the low 13 mantissa bits cleared),
-// the lo part of the TF32 split.
+// the lo part of the TF32 split.  64 x 64 tiles through shared memory (16
+// elements per thread in flight), a 1-D grid of tiles (tiles_n per row of
+// tiles).
 template <typename TB>
-__global__ void k_transpose_f32(const TB* __restrict__ B, int64_t K, int64_t N, int64_t ldb, float* __restrict__ Bt,
-                                int64_t ldk, float* __restrict__ Blo) {
-  __shared__ float tile[32][33];
-  const int64_t k0 = (int64_t)blockIdx.x * 32, nb = (int64_t)blockIdx.y * 32;
+__global__ void __launch_bounds__(256) k_transpose_f32(const TB* __restrict__ B, int64_t K, int64_t N, int64_t ldb,
+                                                       float* __restrict__ Bt, int64_t ldk, float* __restrict__ Blo,
+                                                       int64_t tiles_n) {
+  __shared__ float tile[64][65];
+  const int64_t tk = (int64_t)blockIdx.x / tiles_n, tnb = (int64_t)blockIdx.x - tk * tiles_n;
+  const int64_t k0 = tk * 64, nb = tnb * 64;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  for (int r = ty; r < 32; r += 8) {
-    const int64_t k = k0 + r, n = nb + tx;
-    tile[r][tx] = (k < K && n < N) ? (float)B[k * ldb + n] : 0.f;
+#pragma unroll
+  for (int r = ty; r < 64; r += 8) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t k = k0 + r, n = nb + tx + 32 * h;
+      tile[r][tx + 32 * h] = (k < K && n < N) ? (float)B[k * ldb + n] : 0.f;
+    }
   }
   __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int64_t n = nb + r, k = k0 + tx;
-    if (n < N && k < ldk) {
-      const float x = tile[tx][r];
-      Bt[n * ldk + k] = x;
-      if (Blo) Blo[n * ldk + k] = x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+#pragma unroll
+  for (int r = ty; r < 64; r += 8) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t n = nb + r, k = k0 + tx + 32 * h;
+      if (n < N && k < ldk) {
+        const float x = tile[tx + 32 * h][r];
+        Bt[n * ldk + k] = x;
+        if (Blo) Blo[n * ldk + k] = x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+      }
     }
   }
 }
@@ -83,9 +95,11 @@ int launch_tc_any(const Dla& d, bool pre, bool f32_out, const CUtensorMap& ma, c
 // its 64-byte K rows suit only operands whose rows are close together:
 // measured on GB300, A Q (K = 4096) 21.0 -> 17.9 ms, while the products
 // with K = n (the Grams, the Gaussian sketch: K-major rows megabytes apart)
-// slowed down (Gaussian sketch 53.6 -> 75.9 ms), and a triangular B or a
-// Gram skips less work in wider tiles.  So 256 only for plain products with
-// K <= 16384, and only if padding N to 256 wastes at most N / 8 columns.
+// slowed down (Gaussian sketch 53.6 -> 75.9 ms), and a Gram skips less work
+// in wider tiles.  So 256 only for plain products with
+// K <= 16384 and a full B (a triangular B skips less work in wide tiles: the
+// tall QR's W R1^-1 measured no faster), and only if padding N to 256 wastes
+// at most N / 8 columns.
 int tile_width(int64_t N, int64_t K, bool gram, bool b_upper) {
   if (gram || b_upper || K > 16384 || N < 256) return 128;
   const int64_t pad256 = (N + 255) / 256 * 256 - N;
@@ -100,11 +114,13 @@ bool gemm_tc_eligible(int64_t M, int64_t N, int64_t K, const void* A, int64_t ld
 
 int transpose_to_f32(const Dla& d, DT tb, const void* B, int64_t K, int64_t N, int64_t ldb, float* Bt, int64_t ldk,
                      float* Blo) {
-  dim3 g((unsigned)((ldk + 31) / 32), (unsigned)((N + 31) / 32));
+  const int64_t tiles_n = (N + 63) / 64, tiles = tiles_n * ((ldk + 63) / 64);
+  if (tiles > 0x7FFFFFFF) return BSRHT_EUNSUP;
+  const unsigned g = (unsigned)tiles;
   if (tb == DT::F32)
-    k_transpose_f32<float><<<g, 256, 0, d.s>>>(static_cast<const float*>(B), K, N, ldb, Bt, ldk, Blo);
+    k_transpose_f32<float><<<g, 256, 0, d.s>>>(static_cast<const float*>(B), K, N, ldb, Bt, ldk, Blo, tiles_n);
   else if (tb == DT::F64)
-    k_transpose_f32<double><<<g, 256, 0, d.s>>>(static_cast<const double*>(B), K, N, ldb, Bt, ldk, Blo);
+    k_transpose_f32<double><<<g, 256, 0, d.s>>>(static_cast<const double*>(B), K, N, ldb, Bt, ldk, Blo, tiles_n);
   else
     return BSRHT_EUNSUP;
   BSRHT_CUDA_TRY(cudaGetLastError());
