@@ -54,8 +54,10 @@ extern "C" {
 #define BSRHT_ENOMEM (-12)     /* scratch allocation failed / workspace short  */
 #define BSRHT_EUNSUP (-95)     /* valid but unsupported combination            */
 #define BSRHT_ETIMEDOUT (-110) /* a bounded wait gave up                       */
-#define BSRHT_ENOTPD (-1001)   /* Nystrom core not positive definite after all
-                                  shift doublings (Remark 3.1)                  */
+#define BSRHT_ENOTPD (-1001)   /* a Gram or core matrix numerically singular
+                                  where no remedy applies (e.g. the Nystrom
+                                  sketch A Omega^T is zero, or Phi Q / Psi P of
+                                  Algorithm 3 lose rank)                        */
 #define BSRHT_ENOCONV (-1002)  /* Jacobi SVD hit its sweep limit               */
 #define BSRHT_ECUDA (-1003)    /* a CUDA runtime call or launch failed          */
 
@@ -159,14 +161,19 @@ int bsrht_sketch_noalloc(const void* A, int64_t n, int64_t m, int32_t p,
  * bsrht_rsvd - rank-k randomized SVD, Algorithm 1 of Sec. 3.1, on the sketch.
  *   A (n x m) ~ U diag(S) V^T with U n x k, S k (descending), V m x k, all
  *   double, U and V with orthonormal columns.  Requires 1 <= k <= l <= m and
- *   l <= n.  Steps: B = Omega A; Q = orth(B^T) (FP64 CholeskyQR2);
- *   W = A Q (second pass over A, in the arithmetic of A: FP64 for F64, FP32
- *   otherwise); W = P R (CholeskyQR2); SVD of R^T (FP64 one-sided Jacobi);
- *   U = P V~_k, S = Sigma~_k, V = Q U~_k.  Each column of U is flipped so its
- *   largest-magnitude entry is positive (V gets the same flip).  When a tall
- *   factor is numerically rank deficient (repeated rows of Omega, or rank(A)
- *   < l) CholeskyQR2 is replaced by Householder QR (FP64, m up to 2^17) or by
- *   an eigen-based basis completed with seeded random directions.
+ *   l <= n.  Steps: B = Omega A; Q = an orthonormal basis of range(B^T), FP64
+ *   and rank revealing: m x l' with l' <= l the number of singular values of
+ *   B above l 2^-52 sigma_1 (CholeskyQR2 when B is well conditioned, else
+ *   Householder QR and a Jacobi SVD of its R factor; l' < l when Omega
+ *   repeats a row up to sign in every block, which sampling with replacement
+ *   allows, or when rank(A) < l); W = A Q (second pass over A, in the
+ *   arithmetic of A: FP64 for F64, FP32 otherwise); W = P R (CholeskyQR2;
+ *   Householder QR for ill-conditioned FP64 W up to 2^17 rows, else an
+ *   eigen-based basis); SVD of R^T (one-sided Jacobi);
+ *   U = P V~_k, S = Sigma~_k, V = Q U~_k.  If l' < k the trailing k - l'
+ *   singular values and the matching columns of U and V are zero.  Each
+ *   column of U is flipped so its largest-magnitude entry is positive (V gets
+ *   the same flip).
  *   Synchronises opts->stream to read the status of the small factorizations;
  *   returns BSRHT_ENOTPD if a Gram matrix is numerically singular,
  *   BSRHT_ENOCONV if the Jacobi SVD does not converge, BSRHT_ETIMEDOUT if a
@@ -195,10 +202,12 @@ int bsrht_rsvd_workspace(int64_t n, int64_t m, int32_t k, int64_t l, int32_t p,
  * r ~ m repeats rows and would make X rank deficient).  Steps:
  * Y = A_p Omega^T, X = A_p^T Gamma^T = A Gamma^T, Z = Phi A_p Psi^T (A Phi^T
  * through an on-device transpose of A: scratch n m size(A) bytes);
- * Q = orth(Y) (FP64),
- * P = orth(X) (rank-robust CholeskyQR2); C = (Phi Q)^+ Z ((Psi P)^T)^+ by the
+ * Q = orth(Y) (FP64, rank revealing as in bsrht_rsvd: m x rq),
+ * P = orth(X) (FP64 data: rank revealing, n x rp; FP32: rank-robust
+ * CholeskyQR2, rp = l); C = (Phi Q)^+ Z ((Psi P)^T)^+ (rq x rp) by the
  * normal equations of the well-conditioned Phi Q and Psi P; C = U~ S~ V~^T
- * (FP64 Jacobi); U = P V~_k, S = S~_k, V = Q U~_k (signs as bsrht_rsvd).
+ * (FP64 Jacobi on C in a zero-padded square frame); U = P V~_k, S = S~_k,
+ * V = Q U~_k (signs as bsrht_rsvd; zero beyond min(rq, rp)).
  * Synchronises opts->stream like bsrht_rsvd; BSRHT_ENOTPD if Phi Q or Psi P
  * is numerically rank deficient, BSRHT_ETIMEDOUT as for bsrht_rsvd.
  */

@@ -9,8 +9,15 @@ U = P V~_k, S = Sigma~_k, V = Q U~_k.
 
 Readings of the paper used here (each also listed with the design notes):
 
-* Algorithm 1 uses Householder QR (LAPACK geqrf/orgqr via numpy) and the SVD
-  of the small R^T factor (LAPACK gesdd).
+* Algorithm 1, step 2: Q is an orthonormal basis of range(Y) (Sec. 3.1).
+  Sampling with replacement (Sec. 2) lets Omega repeat a row up to sign in
+  every block, and then range(Y) has dimension r' < l; completing Q with
+  arbitrary directions would make the result depend on them. Q is therefore
+  rank revealing: the left singular vectors of Y (LAPACK SVD) whose singular
+  value exceeds tau * sigma_1, tau = l * 2^-52. Steps 3-6 then run on r'
+  columns; with r' < k the trailing singular values and the matching columns
+  of U and V are zero. Step 4 uses Householder QR (LAPACK geqrf/orgqr via
+  numpy) and step 5 the SVD of the small R^T factor (LAPACK gesdd).
 * Algorithm 2, step 6 writes (Y V~_k) Sigma~_k^-1; with Z = Q~ R and
   R = U~ Sigma~ V~^T the quantity that equals Q~ U~_k (the stabler variant
   the text mentions) is (Z V~_k) Sigma~_k^-1, so Z is used.
@@ -19,9 +26,10 @@ Readings of the paper used here (each also listed with the design notes):
   core = sym(Omega Y_nu), Lambda = max(Sigma~_k^2 - nu, 0). The shift does not
   help when Omega itself has repeated rows (sampling with replacement allows
   them), so when the Cholesky factorisation fails or its squared pivots fall
-  below tau = l * 2^-52 of the largest, Remark 3.1's other remedy is used:
-  the SVD square root of the core, as a pseudo-inverse (eigenvalues below
-  tau * lambda_max dropped).
+  below tau = l * u of the largest (u the unit roundoff of the arithmetic of
+  A's tall products: 2^-52 for FP64 data, 2^-23 otherwise), Remark 3.1's
+  other remedy is used: the SVD square root of the core, as a pseudo-inverse
+  (eigenvalues below tau * lambda_max dropped).
 * Cholesky convention: C upper triangular with C^T C = core, Z = Y C^-1.
 * Singular vectors are only defined up to sign: each column of U is flipped
   so its largest-magnitude entry (lowest index on ties) is positive, and the
@@ -72,28 +80,55 @@ def truncated_svd(a: np.ndarray, k: int):
     return uk, s[:k], vk
 
 
+def range_tol(l: int) -> float:
+    """Rank rule of the basis of range(Y): directions with sigma <= tau sigma_1
+    are numerically absent, tau = l * 2^-52 (l columns, FP64 unit roundoff)."""
+    return l * EPS64
+
+
+def range_basis(y: np.ndarray) -> np.ndarray:
+    """Orthonormal basis of the numerical range of y (rows x l): the left
+    singular vectors (LAPACK SVD) with sigma_i > range_tol(l) * sigma_1.
+    Returns a rows x r' matrix, r' <= l (r' = 0 for y = 0)."""
+    y = np.asarray(y, dtype=np.float64)
+    if y.shape[1] == 0:
+        return np.zeros((y.shape[0], 0))
+    u, s, _ = np.linalg.svd(y, full_matrices=False)
+    if s[0] == 0.0:
+        return np.zeros((y.shape[0], 0))
+    keep = s > range_tol(y.shape[1]) * s[0]
+    return np.ascontiguousarray(u[:, keep])
+
+
 def rsvd(a: np.ndarray, k: int, l: int, p: int, seed: int, sketch: str = "bsrht"):
     """Algorithm 1 for the tall n x m matrix ``a``; returns (U n x k, S k, V m x k).
     ``sketch="gaussian"`` takes Omega from ``oracle.gaussian`` (the comparator
     of Sec. 4; p is then unused)."""
     a = np.asarray(a, dtype=np.float64)
+    n, m = a.shape
     # Step 1: Y = A_paper Omega^T = (Omega A)^T, m x l.
     if sketch == "gaussian":
         y = gaussian_sketch(a, l, seed).T
     else:
         y = sketch_dense(a, p, l, seed).T
-    # Step 2: orthonormal basis Q of range(Y).
-    q, _ = np.linalg.qr(y)
+    # Step 2: orthonormal basis Q of range(Y), rank revealing (m x r').
+    q = range_basis(y)
+    r = q.shape[1]
     # Step 3: Z = Q^T A_paper = (A Q)^T; step 4 needs Z^T = A Q = P R.
     zt = a @ q
     pmat, rmat = np.linalg.qr(zt)
-    # Step 5: SVD of R^T (l x l), truncated to rank k.
+    # Step 5: SVD of R^T (r' x r'), truncated to rank k.
     ut, st, vtt = np.linalg.svd(rmat.T)
     # Step 6: A_paper ~ (Q U~_k) S~_k (P V~_k)^T, so A ~ (P V~_k) S~_k (Q U~_k)^T.
-    u = pmat @ vtt[:k].T
-    v = q @ ut[:, :k]
+    kk = min(k, r)
+    u = np.zeros((n, k))
+    v = np.zeros((m, k))
+    s = np.zeros(k)
+    u[:, :kk] = pmat @ vtt[:kk].T
+    v[:, :kk] = q @ ut[:, :kk]
+    s[:kk] = st[:kk]
     u, v = sign_normalize(u, v)
-    return u, st[:k].copy(), v
+    return u, s, v
 
 
 def srsvd_seeds(seed: int):
@@ -112,7 +147,8 @@ def srsvd(a: np.ndarray, k: int, l: int, s: int, p: int, seed: int):
     sample of l out of r ~ m repeats rows, which would make X rank deficient;
     Algorithm 3 takes any oblivious embedding).  In the paper's notation
     (A_p = a^T): X = A_p^T Gamma^T, Y = A_p Omega^T, Z = Phi A_p Psi^T;
-    Q = orth(Y) (m x l), P = orth(X) (n x l); C = (Phi Q)^+ Z ((Psi P)^T)^+
+    Q = orth(Y) (m x rq), P = orth(X) (n x rp), both rank revealing
+    (``range_basis``); C = (Phi Q)^+ Z ((Psi P)^T)^+
     (the reading of step 4: pseudo-inverses by least squares, the right one
     applied to (Psi P)^T so that the product is defined); C = U~ S~ V~^T;
     A_p ~ (Q U~_k) S~_k (P V~_k)^T, i.e. a ~ (P V~_k) S~_k (Q U~_k)^T.
@@ -124,21 +160,28 @@ def srsvd(a: np.ndarray, k: int, l: int, s: int, p: int, seed: int):
     x = a @ omega_gaussian(a.shape[1], l, s_ga).T  # n x l = A_p^T Gamma^T
     w = sketch_dense(a.T, 1, s, s_ph).T            # n x s = a Phi^T
     z = sketch_dense(w, p, s, s_ps).T              # s x s = Phi A_p Psi^T
-    # Step 2: orthonormal bases.
-    q, _ = np.linalg.qr(y)
-    pm, _ = np.linalg.qr(x)
-    # Step 3: Phi Q (s x l) and Psi P (s x l).
+    # Step 2: orthonormal bases, rank revealing as in Algorithm 1
+    # (range_basis): Q is m x rq, P is n x rp.
+    q = range_basis(y)
+    pm = range_basis(x)
+    # Step 3: Phi Q (s x rq) and Psi P (s x rp).
     phq = sketch_dense(q, 1, s, s_ph)
     psp = sketch_dense(pm, p, s, s_ps)
-    # Step 4: C = (Phi Q)^+ Z ((Psi P)^T)^+ by least squares.
-    c1 = np.linalg.lstsq(phq, z, rcond=None)[0]    # l x s
-    c = np.linalg.lstsq(psp, c1.T, rcond=None)[0].T  # l x l
-    # Step 5: SVD of C; step 6: the factors.
+    # Step 4: C = (Phi Q)^+ Z ((Psi P)^T)^+ by least squares (rq x rp).
+    c1 = np.linalg.lstsq(phq, z, rcond=None)[0]    # rq x s
+    c = np.linalg.lstsq(psp, c1.T, rcond=None)[0].T  # rq x rp
+    # Step 5: SVD of C; step 6: the factors (zero beyond the numerical rank).
     uc, sc, vct = np.linalg.svd(c)
-    u = pm @ vct[:k].T
-    v = q @ uc[:, :k]
+    n, m = a.shape
+    kk = min(k, sc.size)
+    u = np.zeros((n, k))
+    v = np.zeros((m, k))
+    sv = np.zeros(k)
+    u[:, :kk] = pm @ vct[:kk].T
+    v[:, :kk] = q @ uc[:, :kk]
+    sv[:kk] = sc[:kk]
     u, v = sign_normalize(u, v)
-    return u, sc[:k].copy(), v
+    return u, sv, v
 
 
 def nystrom_shift(y: np.ndarray) -> float:
@@ -146,14 +189,44 @@ def nystrom_shift(y: np.ndarray) -> float:
     return math.sqrt(y.shape[0]) * EPS64 * float(np.linalg.norm(y))
 
 
+def nystrom_core_factor(core: np.ndarray, l: int, unit_roundoff: float = EPS64):
+    """Right factor F of Algorithm 2 step 3 (Z = Y_nu F) and its rank.
+
+    Step 2 takes the Cholesky factor C (upper, C^T C = core) and F = C^-1.
+    Remark 3.1: when the core is numerically rank deficient -- the
+    factorization fails, or its squared pivots fall below tau times the
+    largest -- F is the SVD square root's pseudo-inverse V_r lambda_r^-1/2
+    (eigenvalues lambda <= tau lambda_max dropped, the columns of the dropped
+    directions zero).  tau = l * unit_roundoff, the unit roundoff of the
+    arithmetic of the tall products (2^-52 for FP64 data, 2^-23 for FP32 and
+    16-bit data).  Returns (F l x l, rank)."""
+    tau = l * unit_roundoff
+    try:
+        c = sla.cholesky(core, lower=False)
+        piv = np.diag(c) ** 2
+        if piv.min() > tau * piv.max():
+            return sla.solve_triangular(c, np.eye(l), lower=False), l
+    except np.linalg.LinAlgError:
+        pass
+    lam_c, v_c = np.linalg.eigh(core)
+    lam_c, v_c = lam_c[::-1], v_c[:, ::-1]   # descending
+    keep = lam_c > tau * lam_c[0]
+    r = int(keep.sum())
+    f = np.zeros((l, l))
+    f[:, :r] = v_c[:, :r] / np.sqrt(lam_c[:r])
+    return f, r
+
+
 def nystrom(a: np.ndarray, k: int, l: int, p: int, seed: int, shift: bool = True,
             unit_roundoff: float = EPS64):
     """Algorithm 2 (with the Z fix in step 6 and the remedies of Remark 3.1).
 
     ``a`` is n x n symmetric PSD. Returns (U n x k, Lambda k, nu) with
-    A ~ U diag(Lambda) U^T. ``unit_roundoff`` sets the rank threshold
-    tau = l * unit_roundoff of Remark 3.1's SVD square root (the arithmetic
-    of the tall products decides which core directions are resolvable).
+    A ~ U diag(Lambda) U^T. ``unit_roundoff`` is the unit roundoff of the
+    arithmetic of A's tall products (2^-52 for FP64 data, 2^-23 for FP32 and
+    16-bit data, as on the device): it sets the rank threshold
+    tau = l * unit_roundoff of Remark 3.1's SVD square root
+    (``nystrom_core_factor``).
     """
     a = np.asarray(a, dtype=np.float64)
     n = a.shape[0]
@@ -164,25 +237,10 @@ def nystrom(a: np.ndarray, k: int, l: int, p: int, seed: int, shift: bool = True
     y_nu = y + nu * om.T
     core = om @ y_nu
     core = 0.5 * (core + core.T)
-    # Step 2: Cholesky factor C (upper, C^T C = core), Step 3: Z = Y C^-1.
-    # Remark 3.1: when the core is numerically rank deficient (the factorization
-    # fails, or its pivots fall below tau of the largest), C^-1 is replaced by
-    # the SVD square root's pseudo-inverse V_r lambda_r^-1/2 (lambda <= tau
-    # lambda_max dropped).
-    tau = l * unit_roundoff
-    z = None
-    try:
-        c = sla.cholesky(core, lower=False)
-        piv = np.diag(c) ** 2
-        if piv.min() > tau * piv.max():
-            z = sla.solve_triangular(c, y_nu.T, trans="T", lower=False).T
-    except np.linalg.LinAlgError:
-        pass
-    if z is None:
-        lam_c, v_c = np.linalg.eigh(core)
-        keep = lam_c > tau * lam_c.max()
-        z = np.zeros_like(y_nu)
-        z[:, :int(keep.sum())] = y_nu @ (v_c[:, keep] / np.sqrt(lam_c[keep]))
+    # Steps 2-3: Z = Y_nu F with F = C^-1 (Cholesky) or Remark 3.1's SVD
+    # square root (see nystrom_core_factor).
+    f, _ = nystrom_core_factor(core, l, unit_roundoff)
+    z = y_nu @ f
     # Step 4: R factor of Z.
     rmat = np.linalg.qr(z, mode="r")
     # Step 5: SVD of R.

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 #include "dla.cuh"
@@ -20,6 +21,48 @@ namespace bsrht {
   } while (0)
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------ cooperative grids
+// The kernels below with grid-wide barriers (grid.sync()) need every CTA of
+// their grid resident at once.  One such grid, sized within the device's
+// occupancy, is what cudaLaunchCooperativeKernel provides; but two of them
+// enqueued on different streams (the server's executor streams, or callers
+// of the library on several streams or host threads) could each hold part
+// of the SMs while their barriers wait for CTAs that cannot start.  So every
+// cooperative grid of this library runs on one stream per device: the
+// caller's stream records an event, that stream waits for it, runs the grid
+// and records an event that the caller's stream waits for, all under one
+// host mutex.  Cooperative grids of different callers then run one after
+// another; what runs beside them are ordinary kernels, which finish without
+// waiting on any other grid (their own waits are bounded), so each
+// cooperative grid finds its SMs as those kernels drain.
+namespace {
+std::mutex g_coop_mu;
+cudaStream_t g_coop_stream[64] = {};
+}  // namespace
+
+static int launch_cooperative(const void* func, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t s) {
+  int dev = 0;
+  BSRHT_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return BSRHT_EUNSUP;
+  std::lock_guard<std::mutex> lock(g_coop_mu);
+  if (!g_coop_stream[dev]) BSRHT_CUDA_TRY(cudaStreamCreateWithFlags(&g_coop_stream[dev], cudaStreamNonBlocking));
+  cudaStream_t cs = g_coop_stream[dev];
+  cudaEvent_t before = nullptr, after = nullptr;
+  BSRHT_CUDA_TRY(cudaEventCreateWithFlags(&before, cudaEventDisableTiming));
+  if (cudaEventCreateWithFlags(&after, cudaEventDisableTiming) != cudaSuccess) {
+    cudaEventDestroy(before);
+    return BSRHT_ECUDA;
+  }
+  cudaError_t e = cudaEventRecord(before, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, before, 0);
+  if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(func, grid, block, args, smem, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(after, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, after, 0);
+  cudaEventDestroy(before);  // released once the recorded work completes
+  cudaEventDestroy(after);
+  return e == cudaSuccess ? BSRHT_OK : BSRHT_ECUDA;
+}
 
 // ------------------------------------------------------------------ GEMM
 namespace {
@@ -512,7 +555,8 @@ int chol_inv(const Dla& d, double* g, double* LT, double* Rinv, double* T, doubl
   BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chol_inv, 256, 0));
   const int blocks = num_sms() * std::max(1, std::min(occ, 1));
   void* args[] = {&a};
-  BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_chol_inv, dim3(blocks), dim3(256), args, 0, d.s));
+  const int st = launch_cooperative((const void*)k_chol_inv, dim3(blocks), dim3(256), args, 0, d.s);
+  if (st != BSRHT_OK) return st;
   note_launches(1);
   return BSRHT_OK;
 }
@@ -758,7 +802,8 @@ int launch_jacobi_wp(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, double tol
     int occ = 0;
     BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0));
     const int blocks = std::max(1, std::min(pairs, num_sms() * std::max(occ, 1)));
-    BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(threads), args, 0, d.s));
+    const int st = launch_cooperative((const void*)kern, dim3(blocks), dim3(threads), args, 0, d.s);
+    if (st != BSRHT_OK) return st;
     note_launches(1);
     return BSRHT_OK;
   };
@@ -963,8 +1008,8 @@ int launch_jacobi_blk_b(const Dla& d, float* M, float* V, int64_t l, double tol,
   BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_blk<B, JR>, 32 * B, smem));
   if ((int64_t)(nblk / 2) > (int64_t)occ * num_sms()) return BSRHT_EUNSUP;  // not co-resident: caller falls back
   void* args[] = {&M, &V, &li, &nblk, &tol, &tol_stop, &fnorm, &tiny_rel, &msw, &rot};
-  BSRHT_CUDA_TRY(
-      cudaLaunchCooperativeKernel((void*)k_jacobi_blk<B, JR>, dim3(nblk / 2), dim3(32 * B), args, smem, d.s));
+  const int st = launch_cooperative((const void*)k_jacobi_blk<B, JR>, dim3(nblk / 2), dim3(32 * B), args, smem, d.s);
+  if (st != BSRHT_OK) return st;
   note_launches(1);
   return BSRHT_OK;
 }
@@ -1415,9 +1460,11 @@ int householder_q(const Dla& d, Arena& ar, double* X, int64_t rows, int64_t l, d
   if (!ar.ok()) return BSRHT_ENOMEM;
   if (ar.measure) return BSRHT_OK;
   void* a1[] = {&X, &rows, &l, &tau, &part};
-  BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_house_qr, dim3(nb), dim3(threads), a1, 0, d.s));
+  int st = launch_cooperative((const void*)k_house_qr, dim3(nb), dim3(threads), a1, 0, d.s);
+  if (st != BSRHT_OK) return st;
   void* a2[] = {&X, &rows, &l, &tau, &Q, &part};
-  BSRHT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_house_formq, dim3(nb), dim3(threads), a2, 0, d.s));
+  st = launch_cooperative((const void*)k_house_formq, dim3(nb), dim3(threads), a2, 0, d.s);
+  if (st != BSRHT_OK) return st;
   note_launches(2);
   return BSRHT_OK;
 }

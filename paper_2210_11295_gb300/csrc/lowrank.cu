@@ -135,6 +135,28 @@ __global__ void k_svqb_scale(const double* __restrict__ lam, double* __restrict_
   scale[c] = (l0 > 0.0 && v > tau * l0) ? 1.0 / sqrt(v) : 0.0;
 }
 
+// min / max of the squared diagonal of the Cholesky factor L (l x l).
+__global__ void k_pivot_ratio(const double* __restrict__ L, int64_t l, double* __restrict__ out) {
+  __shared__ double mn[256], mx[256];
+  double a = INFINITY, b = 0.0;
+  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
+    const double v = L[i * l + i] * L[i * l + i];
+    a = fmin(a, v);
+    b = fmax(b, v);
+  }
+  mn[threadIdx.x] = a;
+  mx[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      mn[threadIdx.x] = fmin(mn[threadIdx.x], mn[threadIdx.x + o]);
+      mx[threadIdx.x] = fmax(mx[threadIdx.x], mx[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = mx[0] > 0.0 ? mn[0] / mx[0] : 0.0;
+}
+
 struct OrthBufs {
   double* G;      // l x l
   double* LT1;    // l x l
@@ -145,6 +167,7 @@ struct OrthBufs {
   double* Vg;     // l x l (fallback)
   double* lam;    // l (fallback)
   double* sc;     // l (fallback)
+  double* ratio;  // 1: min / max squared Cholesky pivot (pivot check)
 };
 
 OrthBufs take_orth_bufs(Arena& ar, int64_t l, size_t cs) {
@@ -158,8 +181,18 @@ OrthBufs take_orth_bufs(Arena& ar, int64_t l, size_t cs) {
   b.Vg = static_cast<double*>(ar.take(8 * l * l));
   b.lam = static_cast<double*>(ar.take(8 * l));
   b.sc = static_cast<double*>(ar.take(8 * l));
+  b.ratio = static_cast<double*>(ar.take(8));
   return b;
 }
+
+// Smallest accepted ratio of squared Cholesky pivots (min / max) on the
+// CholeskyQR2 path of FP64 data.  CholeskyQR2 is accurate while the
+// condition number of X stays below about u^-1/2 (u = 2^-53); a Gram whose
+// pivots spread by more than 2^44 is past that, or numerically singular
+// (its smallest eigenvalues are then rounding noise, and a Cholesky factor
+// that happens to exist is meaningless).  Such inputs take the Householder /
+// rank-revealing paths instead.
+constexpr double kCholQrPivotMin64 = 0x1.0p-44;
 
 // Orthonormal basis Q (rows x l, type tc) of the tall X, robust to rank
 // deficiency, and R (l x l FP64) with X = Q R when R != nullptr.
@@ -175,23 +208,40 @@ OrthBufs take_orth_bufs(Arena& ar, int64_t l, size_t cs) {
 // upper-triangular FP64 R2^{-1} (l x l), and the caller applies R2^{-1} to its
 // small right-hand factor instead of forming Q (one rows x l x l product
 // less).  *Rinv_out is nullptr when Q is explicit.
+// With declined != nullptr only the fast path runs: when it cannot be used
+// (a Cholesky factorization fails, or for FP64 data the pivot check above),
+// *declined is set and nothing else is done.
 int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void* Z, int64_t rows, int64_t l,
                 uint64_t seed, const OrthBufs& b, double* R, bool need_q, bool keep_x, void** Qout,
-                const double** Rinv_out = nullptr, bool x_t_in_z = false) {
+                const double** Rinv_out = nullptr, bool x_t_in_z = false, bool* declined = nullptr) {
   const void* RinvB = (tc == DT::F32) ? b.Rinv_c : (const void*)b.Rinv;
   if (Rinv_out) *Rinv_out = nullptr;
+  if (declined) *declined = false;
   // ---- fast path: CholeskyQR2 (Z serves as scratch for the transposed Grams)
   bool fast = true;
   // (b.Ug and b.Vg, used only by the fallback, are the scratch of chol_inv.)
   TRY(tall_gram(d, ar, dry, tc, X, rows, l, Z, b.G, x_t_in_z));
   if (!dry) {
     TRY(chol_inv(d, b.G, b.LT1, b.Rinv, b.Ug, b.Vg, l));
+    // FP64 data: the squared pivots of the first factor must stay above
+    // kCholQrPivotMin64 of the largest (see there).
+    double ratio = 1.0;
+    if (tc == DT::F64) {
+      k_pivot_ratio<<<1, 256, 0, d.s>>>(b.G, l, b.ratio);
+      BSRHT_CUDA_TRY(cudaGetLastError());
+      note_launches(1);
+      BSRHT_CUDA_TRY(cudaMemcpyAsync(&ratio, b.ratio, sizeof(double), cudaMemcpyDeviceToHost, d.s));
+    }
     int hs = 0;
     TRY(read_status(d, &hs));
     if (hs & kStatusTcWait) return BSRHT_ETIMEDOUT;
-    if (hs) {
+    if (hs || !(ratio > kCholQrPivotMin64)) {
       fast = false;
       BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
+      if (declined) {
+        *declined = true;
+        return BSRHT_OK;
+      }
     }
   }
   if (fast || dry) {
@@ -210,6 +260,10 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
       if (hs) {
         fast = false;
         BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
+        if (declined) {
+          *declined = true;
+          return BSRHT_OK;
+        }
       }
     }
     if (fast || dry) {
@@ -289,6 +343,82 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
   return BSRHT_OK;
 }
 
+// cols[c * l + i] = R[i][c] for the upper triangle R of the first l rows of
+// the Householder output Z (rows x l): the column storage of R for the
+// Jacobi SVD.
+__global__ void k_upper_to_cols(const double* __restrict__ Z, int64_t l, double* __restrict__ cols) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= l * l) return;
+  const int64_t c = idx / l, i = idx - c * l;
+  cols[idx] = i <= c ? Z[i * l + c] : 0.0;
+}
+
+// Rank rule of the basis of range(Y): directions with sigma <= tau sigma_1
+// are numerically absent, tau = l 2^-52.
+double range_tol(int64_t l) { return (double)l * 0x1.0p-52; }
+
+// Orthonormal basis Q of the numerical range of the FP64 sketch matrix X
+// (rows x l), Algorithm 1 step 2: range(Q) = range(Y).  Sampling with
+// replacement (Sec. 2) lets Omega repeat a row up to sign in every block;
+// range(Y) then has dimension r' < l, and Q must not be completed with
+// arbitrary directions (the result would depend on them).  Rule: keep the
+// left singular directions of X with sigma > range_tol(l) sigma_1.
+// Fast path: CholeskyQR2 with the pivot check of kCholQrPivotMin64, which
+// accepts only inputs whose smallest singular value is far above the rule's
+// cutoff (every direction kept, r' = l).  Otherwise: Householder QR
+// X = Qh R, one-sided Jacobi SVD R = Ur S Vr^T (FP64), and
+// Q = Qh Ur[:, :r'] with r' the count of sigma > tau sigma_1.
+// Buffers: X (input, overwritten), Y and Z (rows x l scratch).  On return
+// *Qout (rows x r', leading dimension r') and *rank = r'; reads r' back on
+// the stream.  In dry mode both paths are measured and r' = l.
+int range_basis(const Dla& d, Arena& ar, bool dry, double* X, double* Y, double* Z, int64_t rows, int64_t l,
+                uint64_t seed, const OrthBufs& b, double** Qout, int64_t* rank) {
+  *rank = l;
+  void* Qv = nullptr;
+  bool declined = false;
+  TRY(orth_robust(d, ar, dry, DT::F64, X, Y, Z, rows, l, seed, b, nullptr, true, false, &Qv, nullptr, false,
+                  &declined));
+  if (!dry && !declined) {
+    *Qout = static_cast<double*>(Qv);
+    return BSRHT_OK;
+  }
+  // Householder QR of a copy of X: Z holds R (upper triangle of its first
+  // l rows) and the reflectors, Y = Qh.
+  if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(Z, X, sizeof(double) * rows * l, cudaMemcpyDeviceToDevice, d.s));
+  {
+    const size_t mk = ar.mark();
+    TRY(householder_q(d, ar, Z, rows, l, Y));
+    ar.release(mk);
+  }
+  if (!dry) {
+    k_upper_to_cols<<<(unsigned)((l * l + 255) / 256), 256, 0, d.s>>>(Z, l, b.G);
+    BSRHT_CUDA_TRY(cudaGetLastError());
+    note_launches(1);
+  }
+  {
+    const size_t mk = ar.mark();
+    TRY(jacobi_svd(d, ar, b.G, l, b.Ug, b.lam, b.Vg));  // R V = U S: b.Ug = Ur (l x l), b.lam = S
+    ar.release(mk);
+  }
+  int64_t r = l;
+  if (!dry) {
+    std::vector<double> sig((size_t)l);
+    BSRHT_CUDA_TRY(cudaMemcpyAsync(sig.data(), b.lam, sizeof(double) * l, cudaMemcpyDeviceToHost, d.s));
+    int hs = 0;
+    TRY(read_status(d, &hs));
+    if (hs) return status_to_code(hs) != BSRHT_OK ? status_to_code(hs) : BSRHT_ENOCONV;
+    r = 0;
+    const double cut = range_tol(l) * sig[0];
+    for (int64_t c = 0; c < l; ++c)
+      if (sig[0] > 0.0 && sig[c] > cut) ++r;
+  }
+  // Q = Qh Ur[:, :r'] into X (rows x r').
+  if (r > 0) TRY(gemm64(d, ar, rows, r, l, Y, l, false, b.Ug, l, X, r));
+  *Qout = X;
+  *rank = r;
+  return BSRHT_OK;
+}
+
 // Cosine threshold of the FP64 Jacobi polish for FP32 data: 16 sqrt(l) 2^-40
 // (sweeps stop once none exceeds 16 times that), about 3.3e-10 at l = 512:
 // far below the FP32 accuracy of the tall factors it is combined with, and
@@ -330,62 +460,75 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
   if (!dry) trace_begin(d.s);
   if (!dry) TRY(sketch_run(sp, A, seed, B, m, sk_ws, d.s));
   if (!dry) trace_mark(d.s, "sketch");
-  // Step 2: Q = orth(B^T) in FP64 (X1 = B^T, m x l).
+  // Step 2: Q = orth(B^T) in FP64 (X1 = B^T, m x l), rank revealing:
+  // Q is m x lq with lq = dim range(Y) <= l (range_basis).
   if (!dry) TRY(transpose_cast(d, tc, B, l, m, m, DT::F64, X1, l));
-  void* Qv = nullptr;
-  TRY(orth_robust(d, ar, dry, DT::F64, X1, X2, X3, m, l, seed ^ 0x51ull, ob, nullptr, true, false, &Qv));
-  const double* Q = static_cast<const double*>(Qv);  // m x l, FP64
+  double* Q = nullptr;
+  int64_t lq = l;
+  TRY(range_basis(d, ar, dry, X1, X2, X3, m, l, seed ^ 0x51ull, ob, &Q, &lq));
   if (!dry) trace_mark(d.s, "orth_sketch");
+  // Below the numerical rank of Y the factors are zero (lq < k).
+  const int64_t kk = std::min<int64_t>(k, lq);
+  if (!dry && kk < k) {
+    BSRHT_CUDA_TRY(cudaMemsetAsync(U, 0, sizeof(double) * n * k, d.s));
+    BSRHT_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(double) * k, d.s));
+    BSRHT_CUDA_TRY(cudaMemsetAsync(V, 0, sizeof(double) * m * k, d.s));
+  }
+  if (!dry && lq == 0) {  // Y = 0: A Omega^T vanishes, the approximation is 0
+    int hs = 0;
+    TRY(read_status(d, &hs));
+    return status_to_code(hs);
+  }
   const void* Qa = Q;
   if (tc == DT::F32) {
-    if (!dry) TRY(cast_copy(d, DT::F64, Q, DT::F32, Qc, m * l));
+    if (!dry) TRY(cast_copy(d, DT::F64, Q, DT::F32, Qc, m * lq));
     Qa = Qc;
   }
-  // Step 3: the paper's Z = Q^T A_paper, i.e. Z^T = A Q (n x l): second pass over A.
+  // Step 3: the paper's Z = Q^T A_paper, i.e. Z^T = A Q (n x lq): second pass over A.
   bool w_t = false;  // W1^T left in W3, the Gram scratch of the QR below
-  TRY(tall_gemm(d, ar, ta, tc, tc, n, l, m, A, lda, Q, Qa, l, W1, l, false,
+  TRY(tall_gemm(d, ar, ta, tc, tc, n, lq, m, A, lda, Q, Qa, lq, W1, lq, false,
                 tc == DT::F32 ? static_cast<float*>(W3) : nullptr, &w_t));
   if (!dry) trace_mark(d.s, "second_pass");
   // Step 4: Z^T = P R (CholeskyQR2, rank-robust).  On the CholeskyQR2 path P
   // stays factored, P = P1 R2^{-1} (Rinv2 != nullptr).
   void* Pv = nullptr;
   const double* Rinv2 = nullptr;
-  TRY(orth_robust(d, ar, dry, tc, W1, W2, W3, n, l, seed ^ 0x52ull, ob, R, true, false, &Pv, &Rinv2, w_t));
+  TRY(orth_robust(d, ar, dry, tc, W1, W2, W3, n, lq, seed ^ 0x52ull, ob, R, true, false, &Pv, &Rinv2, w_t));
   if (!dry) trace_mark(d.s, "tall_qr");
   // Step 5: SVD of R^T = U~ Sigma~ V~^T.  FP64 data: Jacobi on the columns
   // of R^T (the rows of R) to FP64 tolerance.  FP32 data: Jacobi on the
   // columns of R (R = V~ Sigma~ U~^T), so that the accumulated rotations,
   // orthogonal to FP64 rounding, give U~ (multiplied by the FP64 Q below),
-  // and the polish stops at cosines of polish_tol_fp32(l): the other factor
+  // and the polish stops at cosines of polish_tol_fp32(lq): the other factor
   // V~ meets P, itself orthogonal only to FP32 accuracy.
   {
     const size_t mk = ar.mark();
     if (tc == DT::F32) {
-      if (!dry) TRY(transpose_lower_to_upper(d, R, RT, l));
-      TRY(jacobi_svd(d, ar, RT, l, Vs, sig, Us, polish_tol_fp32(l)));
+      if (!dry) TRY(transpose_lower_to_upper(d, R, RT, lq));
+      TRY(jacobi_svd(d, ar, RT, lq, Vs, sig, Us, polish_tol_fp32(lq)));
     } else {
-      TRY(jacobi_svd(d, ar, R, l, Us, sig, Vs));
+      TRY(jacobi_svd(d, ar, R, lq, Us, sig, Vs));
     }
     ar.release(mk);
   }
   if (!dry) trace_mark(d.s, "small_svd");
   // Step 6: U = P V~_k, V = Q U~_k, S = Sigma~_k.  With P factored, U =
-  // P1 (R2^{-1} V~_k): the l x k factor is formed in FP64 first.
+  // P1 (R2^{-1} V~_k): the lq x k factor is formed in FP64 first.
   const double* Vk64 = Vs;
-  int64_t ldv = l;
+  int64_t ldv = lq;
   if (Rinv2) {
-    TRY(gemm64(d, ar, l, k, l, Rinv2, l, false, Vs, l, Vp, k));
+    TRY(gemm64(d, ar, lq, kk, lq, Rinv2, lq, false, Vs, lq, Vp, kk));
     Vk64 = Vp;
-    ldv = k;
+    ldv = kk;
   }
   const void* Vk = Vk64;
   if (tc == DT::F32) {
-    if (!dry) TRY(cast_copy(d, DT::F64, Vk64, DT::F32, Vs_c, ldv == l ? l * l : l * k));
+    if (!dry) TRY(cast_copy(d, DT::F64, Vk64, DT::F32, Vs_c, lq * ldv));
     Vk = Vs_c;
   }
-  TRY(tall_gemm(d, ar, tc, tc, DT::F64, n, k, l, Pv, l, Vk64, Vk, ldv, U, k, false));
-  TRY(gemm64(d, ar, m, k, l, Q, l, false, Us, l, V, k));
-  if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(S, sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, d.s));
+  TRY(tall_gemm(d, ar, tc, tc, DT::F64, n, kk, lq, Pv, lq, Vk64, Vk, ldv, U, k, false));
+  TRY(gemm64(d, ar, m, kk, lq, Q, lq, false, Us, lq, V, k));
+  if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(S, sig, sizeof(double) * kk, cudaMemcpyDeviceToDevice, d.s));
   {
     const size_t mk = ar.mark();
     TRY(sign_normalize(d, ar, U, n, k, V, m));
@@ -494,55 +637,84 @@ int srsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, 
   bool x_t = false;  // X^T left in X3, the Gram scratch of orth(X)
   TRY(tall_gemm(d, ar, ta, tc, tc, n, l, m, A, lda, GT, tc == DT::F32 ? GTc : (const void*)GT, l, X1, l,
                 false, tc == DT::F32 ? static_cast<float*>(X3) : nullptr, &x_t));  // X = A Gamma^T (n x l)
-  // Step 2: Q = orth(Y) in FP64, P = orth(X).
-  void* Qv = nullptr;
-  TRY(orth_robust(d, ar, dry, DT::F64, Y1, Y2, Y3, m, l, seed ^ 0x61ull, ob, nullptr, true, false, &Qv));
-  const double* Q = static_cast<const double*>(Qv);
+  // Step 2: Q = orth(Y) in FP64 (m x rq), P = orth(X) (n x rp), rank
+  // revealing as in Algorithm 1 (range_basis) for FP64 bases; FP32 data
+  // keep the rank-robust CholeskyQR2 basis of X (rp = l).
+  double* Q = nullptr;
+  int64_t rq = l, rp = l;
+  TRY(range_basis(d, ar, dry, Y1, Y2, Y3, m, l, seed ^ 0x61ull, ob, &Q, &rq));
   void* Pv = nullptr;
-  TRY(orth_robust(d, ar, dry, tc, X1, X2, X3, n, l, seed ^ 0x62ull, ob, nullptr, true, false, &Pv, nullptr, x_t));
+  if (tc == DT::F64) {
+    double* P64 = nullptr;
+    TRY(range_basis(d, ar, dry, static_cast<double*>(X1), static_cast<double*>(X2), static_cast<double*>(X3), n, l,
+                    seed ^ 0x62ull, ob, &P64, &rp));
+    Pv = P64;
+  } else {
+    TRY(orth_robust(d, ar, dry, tc, X1, X2, X3, n, l, seed ^ 0x62ull, ob, nullptr, true, false, &Pv, nullptr, x_t));
+  }
   if (!dry) trace_mark(d.s, "orth");
-  // Step 3: Phi Q and Psi P (s x l).
+  const int64_t L = std::max(rq, rp);              // the core is zero-padded to L x L
+  const int64_t kk = std::min<int64_t>(k, std::min(rq, rp));
+  if (!dry && kk < k) {
+    BSRHT_CUDA_TRY(cudaMemsetAsync(U, 0, sizeof(double) * n * k, d.s));
+    BSRHT_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(double) * k, d.s));
+    BSRHT_CUDA_TRY(cudaMemsetAsync(V, 0, sizeof(double) * m * k, d.s));
+  }
+  if (!dry && kk == 0) {
+    int hs = 0;
+    TRY(read_status(d, &hs));
+    return status_to_code(hs);
+  }
+  // Step 3: Phi Q (s x rq) and Psi P (s x rp).
   if (!dry) {
-    TRY(sketch_run(sp_q, Q, s_ph, PhQ, l, sk_ws, d.s));
-    TRY(sketch_run(sp_p, Pv, s_ps, PsPc, l, sk_ws, d.s));
+    SketchPlan pq = sp_q, pp = sp_p;
+    if (rq != l) TRY(sketch_make_plan(pq, BSRHT_F64, BSRHT_VARIANT_AUTO, m, rq, rq, 1, s, true, nullptr));
+    if (rp != l) TRY(sketch_make_plan(pp, o.dtype, BSRHT_VARIANT_AUTO, n, rp, rp, p, s, true, nullptr));
+    if (pq.work_bytes > skb || pp.work_bytes > skb) return BSRHT_ENOMEM;
+    TRY(sketch_run(pq, Q, s_ph, PhQ, rq, sk_ws, d.s));
+    TRY(sketch_run(pp, Pv, s_ps, PsPc, rp, sk_ws, d.s));
     if (tc == DT::F32)
-      TRY(cast_copy(d, DT::F32, PsPc, DT::F64, PsP, s * l));
+      TRY(cast_copy(d, DT::F32, PsPc, DT::F64, PsP, s * rp));
     else
-      BSRHT_CUDA_TRY(cudaMemcpyAsync(PsP, PsPc, 8 * s * l, cudaMemcpyDeviceToDevice, d.s));
+      BSRHT_CUDA_TRY(cudaMemcpyAsync(PsP, PsPc, 8 * s * rp, cudaMemcpyDeviceToDevice, d.s));
   }
-  // Step 4: C = G1^-1 (Phi Q)^T Z (Psi P) G2^-1.
-  TRY(gemm64(d, ar, l, l, s, PhQ, l, true, PhQ, l, G1, l, false, true));   // G1 = (Phi Q)^T (Phi Q)
-  TRY(gemm64(d, ar, l, l, s, PsP, l, true, PsP, l, G2, l, false, true));   // G2 = (Psi P)^T (Psi P)
+  // Step 4: C = G1^-1 (Phi Q)^T Z (Psi P) G2^-1 (rq x rp, in an L x L zero frame).
+  TRY(gemm64(d, ar, rq, rq, s, PhQ, rq, true, PhQ, rq, G1, rq, false, true));  // G1 = (Phi Q)^T (Phi Q)
+  TRY(gemm64(d, ar, rp, rp, s, PsP, rp, true, PsP, rp, G2, rp, false, true));  // G2 = (Psi P)^T (Psi P)
   if (!dry) {
-    TRY(chol_inv(d, G1, LT, Ri1, ob.Ug, ob.Vg, l));                         // Ri1 = L1^-T
-    TRY(chol_inv(d, G2, LT, Ri2, ob.Ug, ob.Vg, l));
-    TRY(transpose_lower_to_upper(d, Ri1, RiT, l));
+    TRY(chol_inv(d, G1, LT, Ri1, ob.Ug, ob.Vg, rq));                        // Ri1 = L1^-T
+    TRY(chol_inv(d, G2, LT, Ri2, ob.Ug, ob.Vg, rp));
+    TRY(transpose_lower_to_upper(d, Ri1, RiT, rq));
   }
-  TRY(gemm64(d, ar, l, l, l, RiT, l, true, RiT, l, Gi1, l));              // G1^-1 = Ri1 Ri1^T
-  if (!dry) TRY(transpose_lower_to_upper(d, Ri2, RiT, l));
-  TRY(gemm64(d, ar, l, l, l, RiT, l, true, RiT, l, Gi2, l));              // G2^-1
-  TRY(gemm64(d, ar, l, s, s, PhQ, l, true, Zp, s, T1, s));                // (Phi Q)^T Z
-  TRY(gemm64(d, ar, l, l, s, T1, s, false, PsP, l, Mm, l));               // ... (Psi P)
-  TRY(gemm64(d, ar, l, l, l, Gi1, l, false, Mm, l, T2, l));
-  TRY(gemm64(d, ar, l, l, l, T2, l, false, Gi2, l, C, l));
+  TRY(gemm64(d, ar, rq, rq, rq, RiT, rq, true, RiT, rq, Gi1, rq));       // G1^-1 = Ri1 Ri1^T
+  if (!dry) TRY(transpose_lower_to_upper(d, Ri2, RiT, rp));
+  TRY(gemm64(d, ar, rp, rp, rp, RiT, rp, true, RiT, rp, Gi2, rp));       // G2^-1
+  TRY(gemm64(d, ar, rq, s, s, PhQ, rq, true, Zp, s, T1, s));             // (Phi Q)^T Z
+  TRY(gemm64(d, ar, rq, rp, s, T1, s, false, PsP, rp, Mm, rp));          // ... (Psi P)
+  TRY(gemm64(d, ar, rq, rp, rq, Gi1, rq, false, Mm, rp, T2, rp));
+  if (!dry && L != rq) BSRHT_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * L * L, d.s));
+  if (!dry && L != rp) BSRHT_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * L * L, d.s));
+  TRY(gemm64(d, ar, rq, rp, rp, T2, rp, false, Gi2, rp, C, L));
   if (!dry) trace_mark(d.s, "core");
-  // Step 5: SVD of C (Jacobi on its columns, the rows of C^T).
-  if (!dry) TRY(transpose_lower_to_upper(d, C, CT, l));
+  // Step 5: SVD of C (Jacobi on its columns, the rows of C^T); the zero
+  // frame leaves the nonzero singular triplets unchanged.
+  if (!dry) TRY(transpose_lower_to_upper(d, C, CT, L));
   {
     const size_t mk = ar.mark();
-    TRY(jacobi_svd(d, ar, CT, l, Uc, sig, Vc));
+    TRY(jacobi_svd(d, ar, CT, L, Uc, sig, Vc));
     ar.release(mk);
   }
   if (!dry) trace_mark(d.s, "small_svd");
-  // Step 6: U = P V~_k, V = Q U~_k, S = S~_k.
+  // Step 6: U = P V~_k, V = Q U~_k, S = S~_k (the first rp / rq rows of the
+  // L x L factors).
   const void* Vk = Vc;
   if (tc == DT::F32) {
-    if (!dry) TRY(cast_copy(d, DT::F64, Vc, DT::F32, Vc_c, l * l));
+    if (!dry) TRY(cast_copy(d, DT::F64, Vc, DT::F32, Vc_c, L * L));
     Vk = Vc_c;
   }
-  TRY(tall_gemm(d, ar, tc, tc, DT::F64, n, k, l, Pv, l, Vc, Vk, l, U, k, false));
-  TRY(gemm64(d, ar, m, k, l, Q, l, false, Uc, l, V, k));
-  if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(S, sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, d.s));
+  TRY(tall_gemm(d, ar, tc, tc, DT::F64, n, kk, rp, Pv, rp, Vc, Vk, L, U, k, false));
+  TRY(gemm64(d, ar, m, kk, rq, Q, rq, false, Uc, L, V, k));
+  if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(S, sig, sizeof(double) * kk, cudaMemcpyDeviceToDevice, d.s));
   {
     const size_t mk = ar.mark();
     TRY(sign_normalize(d, ar, U, n, k, V, m));
@@ -606,28 +778,6 @@ __global__ void k_symmetrize(const T* __restrict__ G, double* __restrict__ Gs, i
   if (idx >= l * l) return;
   const int64_t i = idx / l, j = idx % l;
   Gs[idx] = 0.5 * ((double)G[i * l + j] + (double)G[j * l + i]);
-}
-
-// min / max of the squared diagonal of the Cholesky factor L (l x l).
-__global__ void k_pivot_ratio(const double* __restrict__ L, int64_t l, double* __restrict__ out) {
-  __shared__ double mn[256], mx[256];
-  double a = INFINITY, b = 0.0;
-  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
-    const double v = L[i * l + i] * L[i * l + i];
-    a = fmin(a, v);
-    b = fmax(b, v);
-  }
-  mn[threadIdx.x] = a;
-  mx[threadIdx.x] = b;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      mn[threadIdx.x] = fmin(mn[threadIdx.x], mn[threadIdx.x + o]);
-      mx[threadIdx.x] = fmax(mx[threadIdx.x], mx[threadIdx.x + o]);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = mx[0] > 0.0 ? mn[0] / mx[0] : 0.0;
 }
 
 __global__ void k_lambda(const double* __restrict__ sig, const double* __restrict__ nu, double* __restrict__ lam,

@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "sketch.cuh"
+#include "trace.cuh"
 
 namespace bsrht {
 namespace {
@@ -70,5 +71,7 @@ extern "C" int bsrht_sketch_noalloc(const void* A, int64_t n, int64_t m, int32_t
   void* scratch = nullptr;
   st = noalloc_scratch(&scratch);
   if (st != BSRHT_OK) return st;
+  // Stage tracing (bsrht_profile_enable) starts afresh, as in bsrht_sketch.
+  trace_begin(static_cast<cudaStream_t>(o.stream));
   return sketch_run(pl, A, seed, out, m, scratch, static_cast<cudaStream_t>(o.stream));
 }

@@ -1,5 +1,6 @@
 // Host planning and launch of the block SRHT sketch.
 #include <algorithm>
+#include <atomic>
 
 #include <cmath>
 #include <map>
@@ -14,18 +15,20 @@
 namespace bsrht {
 
 int num_sms() {
-  static int cached[64] = {0};
+  // Per-device cache; host threads may plan at the same time, so the
+  // entries are atomics (every writer stores the same value).
+  static std::atomic<int> cached[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-  if (cached[dev] == 0) {
-    int v = 0;
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
       cudaGetLastError();
       v = 152;
     }
-    cached[dev] = v;
+    cached[dev].store(v, std::memory_order_relaxed);
   }
-  return cached[dev];
+  return v;
 }
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

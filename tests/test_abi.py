@@ -10,6 +10,16 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
+def _placeholders_only_without_gpu():
+    """The launch calls below pass placeholder addresses that host-side
+    validation must reject before any device work.  They run only where no
+    GPU is visible: on a GPU host a regression in that validation would send
+    a kernel to an unmapped address, so there the check stops here."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("placeholder-pointer launch checks run on hosts without a GPU")
+
+
 def _declared():
     src = open(os.path.join(ROOT, "include", "bsrht.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
@@ -47,6 +57,7 @@ def test_sketch_rejects_bad_sizes(n, m, p, l):
     st = b.lib.bsrht_sketch_workspace(n, m, p, l, ctypes.byref(o), ctypes.byref(out))
     assert st == bb.BSRHT_EINVAL
     # The launch path validates before touching the device.
+    _placeholders_only_without_gpu()
     st = b.lib.bsrht_sketch(ctypes.c_void_p(16), n, m, p, l, 0, ctypes.c_void_p(16), ctypes.byref(o))
     assert st == bb.BSRHT_EINVAL
 
@@ -57,6 +68,7 @@ def test_sketch_rejects_null_and_bad_stride():
     o = bb.Opts()
     b.lib.bsrht_opts_init(ctypes.byref(o))
     o.dtype = bb.F64
+    _placeholders_only_without_gpu()
     assert b.lib.bsrht_sketch(None, 64, 4, 2, 8, 0, ctypes.c_void_p(16), ctypes.byref(o)) == bb.BSRHT_EINVAL
     o.lda = 3  # lda < m
     assert b.lib.bsrht_sketch(ctypes.c_void_p(16), 64, 4, 2, 8, 0, ctypes.c_void_p(16),
@@ -106,6 +118,7 @@ def test_rsvd_rejects_bad_sizes_before_any_device_work(n, m, k, l, p):
     o = _opts(bb.F32)
     out = ctypes.c_size_t(0)
     assert b.lib.bsrht_rsvd_workspace(n, m, k, l, p, ctypes.byref(o), ctypes.byref(out)) == bb.BSRHT_EINVAL
+    _placeholders_only_without_gpu()
     fake, dfake = ctypes.c_void_p(256), ctypes.cast(ctypes.c_void_p(256), ctypes.POINTER(ctypes.c_double))
     assert b.lib.bsrht_rsvd(fake, n, m, k, l, p, 0, dfake, dfake, dfake, ctypes.byref(o)) == bb.BSRHT_EINVAL
 
@@ -122,6 +135,7 @@ def test_srsvd_rejects_before_any_device_work(n, m, k, l, s, p, dtype, status):
     o = _opts(getattr(bb, dtype))
     out = ctypes.c_size_t(0)
     assert b.lib.bsrht_srsvd_workspace(n, m, k, l, s, p, ctypes.byref(o), ctypes.byref(out)) == status
+    _placeholders_only_without_gpu()
     fake, dfake = ctypes.c_void_p(256), ctypes.cast(ctypes.c_void_p(256), ctypes.POINTER(ctypes.c_double))
     assert b.lib.bsrht_srsvd(fake, n, m, k, l, s, p, 0, dfake, dfake, dfake, ctypes.byref(o)) == status
 
@@ -132,11 +146,14 @@ def test_nystrom_rejects_before_any_device_work():
     out = ctypes.c_size_t(0)
     fake, dfake = ctypes.c_void_p(256), ctypes.cast(ctypes.c_void_p(256), ctypes.POINTER(ctypes.c_double))
     o = _opts(bb.F32)
-    for n, k, l, p in ((500, 10, 600, 8), (500, 11, 10, 2), (500, 4, 8, 0)):  # l > n, k > l, p = 0
+    bad = ((500, 10, 600, 8), (500, 11, 10, 2), (500, 4, 8, 0))  # l > n, k > l, p = 0
+    for n, k, l, p in bad:
         assert b.lib.bsrht_nystrom_workspace(n, k, l, p, ctypes.byref(o), ctypes.byref(out)) == bb.BSRHT_EINVAL
+    og = _opts(bb.F32, b.VARIANT_GAUSSIAN)  # the Gaussian comparator covers the sketch and Algorithm 1 only
+    assert b.lib.bsrht_nystrom_workspace(4096, 10, 64, 4, ctypes.byref(og), ctypes.byref(out)) == bb.BSRHT_EUNSUP
+    _placeholders_only_without_gpu()
+    for n, k, l, p in bad:
         assert b.lib.bsrht_nystrom(fake, n, k, l, p, 0, dfake, dfake, ctypes.byref(o)) == bb.BSRHT_EINVAL
-    o = _opts(bb.F32, b.VARIANT_GAUSSIAN)  # the Gaussian comparator covers the sketch and Algorithm 1 only
-    assert b.lib.bsrht_nystrom_workspace(4096, 10, 64, 4, ctypes.byref(o), ctypes.byref(out)) == bb.BSRHT_EUNSUP
 
 
 def test_lowrank_workspace_queries_scale():

@@ -130,3 +130,20 @@ def test_sketch_full_size_sampled_columns(lib, p):
     del a
     ref = orc.sketch_fast(sub, p, l, 7)
     assert _rel(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("p", [4, 64])
+def test_sketch_full_size_sampled_columns_fp64(lib, p):
+    """n = 2^20, m = 4096, l = 512 in FP64 (the paper's arithmetic), the
+    launch configuration of the FP64 benchmark line; eight columns (first,
+    last, panel edges, spread) against the oracle at 1e-12."""
+    n, m, l = 1 << 20, 4096, 512
+    gen = torch.Generator("cuda").manual_seed(200 + p)
+    a = torch.randn(n, m, device="cuda", dtype=torch.float64, generator=gen)
+    out = lib.bsrht_sketch(a, p, l, 9)
+    cols = [0, 1, 15, 16, 1000, 2047, 4080, 4095]
+    sub = a[:, cols].cpu().numpy()
+    got = out[:, cols].cpu().numpy()
+    del a
+    ref = orc.sketch_fast(sub, p, l, 9)
+    assert _rel(got, ref) <= 1e-12

@@ -3,7 +3,8 @@ oracle (oracle.lowrank.srsvd), through the C ABI.
 
 What is unique is compared: for A of exact (or near-exact) rank below l the
 bases Q, P capture range(A) on both sides and the outputs are determined, so
-the FP64 path matches the oracle to rounding (1e-12 on exact recovery); for
+the FP64 path matches the oracle to rounding (1e-12, on exact recovery and
+against the oracle on a near-low-rank matrix); for
 FP32 data the reduced-precision bar applies (singular values within
 2e-5 sigma_1, residuals within 1e-5 ||A||_F, orthonormal factors to 1e-5).  At the full benchmark size: orthonormal factors, descending S and an
 error within 1.5x of Algorithm 1's on the same data."""
@@ -41,8 +42,9 @@ def test_srsvd_exact_recovery_fp64(lib, p):
 
 
 def test_srsvd_matches_oracle_fp64(lib):
-    """Rank 10 plus a 1e-9 noise floor: both sides determine the same
-    rank-10 factors up to the noise (1e-7 relative allowed)."""
+    """Rank 10 plus a 1e-9 noise floor: Q and P are rank-revealing bases on
+    both sides (every direction above l 2^-52 sigma_1 kept), so both
+    determine the same rank-10 factors: 1e-12 relative."""
     rng = np.random.default_rng(30)
     a = synth.exact_rank(4096, 1024, 10, seed=31) + 1e-9 * rng.standard_normal((4096, 1024))
     k, l, s, p = 10, 40, 96, 4
@@ -50,9 +52,9 @@ def test_srsvd_matches_oracle_fp64(lib):
     torch.cuda.synchronize()
     u, sv, v = u.cpu().numpy(), sv.cpu().numpy(), v.cpu().numpy()
     ur, sr, vr = orl.srsvd(a, k, l, s, p, 3)
-    assert np.max(np.abs(sv - sr)) <= 1e-7 * sr[0]
+    assert np.max(np.abs(sv - sr)) <= 1e-12 * sr[0]
     approx, ref = (u * sv) @ v.T, (ur * sr) @ vr.T
-    assert np.linalg.norm(approx - ref) <= 1e-7 * np.linalg.norm(ref)
+    assert np.linalg.norm(approx - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
 def test_srsvd_fp32_matches_oracle(lib):
