@@ -14,7 +14,8 @@ struct SketchPlan {
   int dtype = 0;      // bsrht_dtype of A
   int variant = 1;    // 1 = CUDA-core butterflies (K1), 2 = tensor cores (K2)
   int path = 0;       // 0 = chunked FWHT kernel, 1 = small-r direct kernel, 2 = TMA-fed chunked kernel,
-                      // 3 = tensor-core kernel (K2, 16-bit inputs), 4 = Gaussian comparator (gaussian.cu)
+                      // 3 = tensor-core kernel (K2, 16-bit inputs), 4 = Gaussian comparator (gaussian.cu),
+                      // 5 = TMA-fed FP64 kernel with the exact integer transform (sketch_f64x.cu)
   int inst = 0;       // kernel instance id within the dtype family
   int W = 0, NT = 0, R2 = 0, JM = 0, NRL = 0;
   int64_t n = 0, m = 0, lda = 0, l = 0;
@@ -28,9 +29,9 @@ struct SketchPlan {
   int paired = 0;     // TMA-fed paths: CTA pairs share panel pairs (16-bit inputs)
   int64_t jgroup = 0; // sketch rows handled per launch
   size_t smem = 0;    // dynamic shared memory per CTA
-  size_t part_bytes = 0;  // partial-sum scratch (path 2 then: status word, D and Dt sign tables)
-  size_t dtab_bytes = 0;  // path 2: D^(i) sign table
-  size_t dttab_bytes = 0; // path 2: Dt^(i) sign table (one sketch-row group)
+  size_t part_bytes = 0;  // partial-sum scratch (paths 2, 5 then: status word, D and Dt sign tables)
+  size_t dtab_bytes = 0;  // paths 2, 5: D^(i) sign table
+  size_t dttab_bytes = 0; // paths 2, 5: Dt^(i) sign table (one sketch-row group)
   size_t work_bytes = 0;  // total scratch
 };
 
@@ -113,6 +114,11 @@ int sketch_occupancy_f64(const SketchPlan& plan);
 int sketch_occupancy_tma(const SketchPlan& plan);
 int sketch_launch_tma(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo, int* err,
                       uint64_t* dtab, uint64_t* dttab, cudaStream_t stream);
+// FP64 path with the exact integer transform (sketch_f64x.cu): W = 16,
+// NT = 512, R2 = 512, JM (sketch rows per thread) in {8, 16}.
+int sketch_occupancy_f64x(const SketchPlan& plan);
+int sketch_launch_f64x(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo, int* err,
+                       uint64_t* dtab, uint64_t* dttab, cudaStream_t stream);
 // Tensor-core path (sketch_tc.cu, K2): BF16 / F16, W = 32, R2 = 512.
 int sketch_occupancy_tc(const SketchPlan& plan);
 int sketch_launch_tc(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo, int* err,

@@ -39,9 +39,9 @@ static int ilog2_host(int64_t v) {
   return k;
 }
 
-// The TMA path needs 16-byte aligned rows: base address and row stride.
+// The TMA paths need 16-byte aligned rows: base address and row stride.
 static bool tma_layout_ok(int dtype, const void* A, int64_t lda) {
-  const size_t es = dtype == BSRHT_F32 ? 4 : 2;
+  const size_t es = dtype_size(dtype);
   if ((lda * (int64_t)es) % 16 != 0) return false;
   return A == nullptr || (reinterpret_cast<uintptr_t>(A) % 16) == 0;
 }
@@ -76,6 +76,32 @@ static int make_plan_tma(SketchPlan& pl, bool query_device) {
   pl.G = (int)std::max<int64_t>(1, std::min<int64_t>(g, std::max<int64_t>(pl.T, 1)));
   set_pairing(pl);
   pl.dtab_bytes = align_up(4 * (size_t)pl.p * (size_t)pl.nch * 16, 256);
+  pl.dttab_bytes = align_up(8 * (size_t)pl.p * (size_t)((pl.jgroup + 63) / 64), 256);
+  pl.work_bytes = pl.part_bytes + 256 + pl.dtab_bytes + pl.dttab_bytes;
+  return BSRHT_OK;
+}
+
+// FP64 kernel with the exact integer transform: 16-column panels, 512-row
+// chunks, sketch-row groups of 256 (l <= 256) or 512.
+static int make_plan_f64x(SketchPlan& pl, bool query_device) {
+  pl.path = 5;
+  pl.W = 16;
+  pl.NT = 512;
+  pl.R2 = 512;
+  pl.JM = pl.l <= 256 ? 8 : 16;
+  pl.NRL = 32;
+  pl.jgroup = std::min<int64_t>(pl.l, (int64_t)pl.JM * 32);
+  pl.nch = (pl.rb + pl.R2 - 1) / pl.R2;
+  pl.C = (int64_t)pl.p * pl.nch;
+  pl.P = (pl.m + pl.W - 1) / pl.W;
+  pl.T = pl.P * pl.C;
+  int occ = query_device ? sketch_occupancy_f64x(pl) : 0;
+  if (occ <= 0) occ = 1;
+  const int64_t g = (int64_t)num_sms() * occ;
+  pl.G = (int)std::max<int64_t>(1, std::min<int64_t>(g, std::max<int64_t>(pl.T, 1)));
+  pl.paired = 0;
+  pl.part_bytes = align_up(8 * (size_t)(pl.G + pl.P) * (size_t)pl.jgroup * pl.W, 256);
+  pl.dtab_bytes = align_up(4 * (size_t)pl.p * (size_t)pl.nch * 32, 256);
   pl.dttab_bytes = align_up(8 * (size_t)pl.p * (size_t)((pl.jgroup + 63) / 64), 256);
   pl.work_bytes = pl.part_bytes + 256 + pl.dtab_bytes + pl.dttab_bytes;
   return BSRHT_OK;
@@ -166,7 +192,7 @@ TuneKey tune_key(int dtype, int64_t r, int64_t m, int64_t l, int64_t lda) {
   while ((int64_t(1) << lm) < std::max<int64_t>(m, 1)) ++lm;
   k.log2m = lm;
   k.big_l = l > 512 ? 1 : 0;
-  k.tma_rows = (dtype != BSRHT_F64 && tma_layout_ok(dtype, nullptr, lda)) ? 1 : 0;
+  k.tma_rows = tma_layout_ok(dtype, nullptr, lda) ? 1 : 0;
   return k;
 }
 }  // namespace
@@ -217,16 +243,19 @@ static int make_plan_choice(SketchPlan& pl, int dtype, int64_t n, int64_t m, int
     inst = choice;
   }
   plan_chunked(pl, inst, query_device);
-  // FP32-arithmetic inputs with blocks of at least one 512-row chunk and
-  // TMA-compatible rows take the TMA-fed kernel unless a chunked instance was
-  // chosen; the plain kernel stays the fallback, so a plan made without A
-  // reserves scratch for both.
-  const bool tma_ok = !f64 && pl.r >= 512 && tma_layout_ok(dtype, A, lda);
-  if (choice == -1 && !(tma_ok || (A == nullptr && !f64 && pl.r >= 512 && tma_layout_ok(dtype, nullptr, lda))))
+  // Inputs with blocks of at least one 512-row chunk and TMA-compatible rows
+  // take the TMA-fed kernel (FP64: the one with the integer transform)
+  // unless a chunked instance was chosen; the plain kernel stays the
+  // fallback, so a plan made without A reserves scratch for both.
+  const bool tma_ok = pl.r >= 512 && tma_layout_ok(dtype, A, lda);
+  if (choice == -1 && !(tma_ok || (A == nullptr && pl.r >= 512 && tma_layout_ok(dtype, nullptr, lda))))
     return BSRHT_EINVAL;
   if (tma_ok && choice < 0) {
     SketchPlan t = pl;
-    make_plan_tma(t, query_device);
+    if (f64)
+      make_plan_f64x(t, query_device);
+    else
+      make_plan_tma(t, query_device);
     const size_t plain = pl.work_bytes;
     pl = t;
     if (A == nullptr) pl.work_bytes = std::max(pl.work_bytes, plain);
@@ -293,7 +322,7 @@ int sketch_autotune(const void* A, int dtype, int64_t n, int64_t m, int64_t lda,
   for (int c : cands) {
     SketchPlan pl;
     if (make_plan_choice(pl, dtype, n, m, lda, p, l, true, A, c) != BSRHT_OK) continue;
-    if ((c == -1 && pl.path != 2) || (c == -3 && pl.path != 3)) continue;
+    if ((c == -1 && pl.path != 2 && pl.path != 5) || (c == -3 && pl.path != 3)) continue;
     if (pl.path == 1) {  // nothing to choose for tiny blocks
       best = -2;
       break;
@@ -381,13 +410,14 @@ int sketch_run(const SketchPlan& pl, const void* A, uint64_t seed, void* out, in
       int* err = reinterpret_cast<int*>(static_cast<char*>(work) + pl.part_bytes);
       if (j0 == 0) BSRHT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), stream));
       st = sketch_launch_tc(pl, a, out, ldo, err, stream);
-    } else if (pl.path == 2) {
+    } else if (pl.path == 2 || pl.path == 5) {
       char* w = static_cast<char*>(work);
       int* err = reinterpret_cast<int*>(w + pl.part_bytes);
       uint64_t* dtab = reinterpret_cast<uint64_t*>(w + pl.part_bytes + 256);
       uint64_t* dttab = reinterpret_cast<uint64_t*>(w + pl.part_bytes + 256 + pl.dtab_bytes);
       if (j0 == 0) BSRHT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), stream));
-      st = sketch_launch_tma(pl, a, out, ldo, err, dtab, dttab, stream);
+      st = pl.path == 5 ? sketch_launch_f64x(pl, a, out, ldo, err, dtab, dttab, stream)
+                        : sketch_launch_tma(pl, a, out, ldo, err, dtab, dttab, stream);
     } else {
       st = pl.dtype == BSRHT_F64 ? sketch_launch_f64(pl, a, out, ldo, stream)
                                  : sketch_launch_f32(pl, a, out, ldo, stream);
@@ -405,7 +435,7 @@ int sketch_make_plan_grouped(SketchPlan& pl, int dtype, int64_t n, int64_t m, in
   // plan as the plain kernel in that case.
   int st = sketch_make_plan(pl, dtype, BSRHT_VARIANT_CUDACORE, n, m, lda, p, l, true, nullptr);
   if (st != BSRHT_OK) return st;
-  if (pl.path == 2) {
+  if (pl.path == 2 || pl.path == 5) {
     // Same sizes through the plain kernel: plan with an address the TMA
     // rules reject (odd), which only steers the path choice.
     st = sketch_make_plan(pl, dtype, BSRHT_VARIANT_CUDACORE, n, m, lda, p, l, true,
