@@ -29,10 +29,11 @@
 // entries are NaN.
 //
 // Thread layout (512 threads, cg = tid % 16 the column in every phase):
-// register phase rows rl + 32 e (rl = tid / 16, e < 16: row bits 5-8);
-// exchange phase rows 16 g + b (g = tid / 16, b < 16: bits 0-3); the last
-// butterfly stage (bit 4) is folded into the gather, which reads the two
-// rows s_j & ~16 and s_j | 16 of each sampled row s_j.
+// register phase rows rl + 32 e (rl = tid / 16, e < 16): row bits 5-8 in
+// registers, then row bit 0 (= bit 0 of rl = lane bit 4) with one warp
+// shuffle; exchange phase rows (g & 1) + 2 b + 32 (g >> 1) (g = tid / 16,
+// b < 16): bits 1-4 in registers.  The gather then reads the transformed
+// row s_j of each sampled row.
 #include <algorithm>
 #include <cmath>
 
@@ -118,6 +119,19 @@ __device__ __forceinline__ uint64_t to_fixed(uint64_t raw, int S, uint32_t dneg)
   return (q ^ sm) - sm;
 }
 
+// The same conversion for columns with S >= 48, where zero and subnormal
+// values convert to 0 with or without the subnormal rules (the shift then
+// exceeds the 53 significand bits): no implicit-bit test, no exponent clamp.
+// c0 = 5 + S; bit 31 of dsign is the D sign.
+__device__ __forceinline__ uint64_t to_fixed_fast(uint64_t raw, int c0, uint32_t dsign) {
+  const uint32_t hi = (uint32_t)(raw >> 32);
+  const int sh = min(c0 - (int)((hi >> 20) & 0x7FFu), 63);
+  const uint64_t mant = ((uint64_t)((hi & 0xFFFFFu) | 0x100000u) << 32) | (uint32_t)raw;
+  const uint64_t q = mant >> sh;
+  const uint64_t sm = (uint64_t)(int64_t)((int32_t)(hi ^ dsign) >> 31);
+  return (q ^ sm) - sm;
+}
+
 template <int JU>
 __global__ void __launch_bounds__(kNT, 1)
     k_sketch_f64x(const __grid_constant__ CUtensorMap tmap, SketchArgs g, const uint32_t* __restrict__ dmtab,
@@ -127,8 +141,8 @@ __global__ void __launch_bounds__(kNT, 1)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128 - (reinterpret_cast<uintptr_t>(smem_raw) & 127)) & 127);
   uint64_t* stage = reinterpret_cast<uint64_t*>(base);                         // [kStages][kR2][kW]
-  uint32_t* s_off = reinterpret_cast<uint32_t*>(base + kStages * kStageBytes);  // [rg][u]: (s_j & ~16) * kW
-  uint32_t* s_hi = s_off + JG;                                                  // s_j >> 9, and bit 4 at bit 31
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(base + kStages * kStageBytes);  // [rg][u]: (s_j & 511) * kW
+  uint32_t* s_hi = s_off + JG;                                                  // s_j >> 9
   int* s_scale = reinterpret_cast<int*>(s_hi + JG);                            // column scales S
   uint64_t* bar = reinterpret_cast<uint64_t*>(s_scale + kW);
 
@@ -183,8 +197,8 @@ __global__ void __launch_bounds__(kNT, 1)
     uint32_t off = 0, hi = 0;
     if (jl < jn) {
       const uint64_t sv = sample_word(g.seed, (uint64_t)(g.j0 + jl)) & (uint64_t)(g.r - 1);
-      off = (uint32_t)(sv & (kR2 - 1) & ~16u) * kW;
-      hi = (uint32_t)(sv >> 9) | ((uint32_t)((sv >> 4) & 1u) << 31);
+      off = (uint32_t)(sv & (kR2 - 1)) * kW;
+      hi = (uint32_t)(sv >> 9);
     }
     s_off[(jl & 31) * JU + (jl >> 5)] = off;  // [rg][u]: jl = rg + 32 u
     s_hi[jl] = hi;
@@ -197,19 +211,21 @@ __global__ void __launch_bounds__(kNT, 1)
   // Gather: sketch rows jl = rl + 32 u (u < JU), column cg.  The 16 lanes
   // of a row lane share its rows: lane cg evaluates the outer-factor x
   // Dt^(i) sign of u = 16 h + cg, a ballot hands each lane its row lane's
-  // 16 bits.  tau: bit 4 of s_j (the sign of the folded last stage).
+  // 16 bits.
   uint32_t my_hi[NH];
   uint64_t my_dt[NH];
-  uint32_t tau = 0;
   int64_t dt_block = -1;
 #pragma unroll
   for (int h = 0; h < NH; ++h) {
     const int u = 16 * h + cg;
-    my_hi[h] = u < JU ? (s_hi[rl + 32 * u] & 0x7FFFFFFFu) : 0u;
+    my_hi[h] = u < JU ? s_hi[rl + 32 * u] : 0u;
     my_dt[h] = 0;
   }
-#pragma unroll
-  for (int u = 0; u < JU; ++u) tau |= (s_hi[rl + 32 * u] >> 31) << u;
+  // Shuffle stage on row bit 0: this thread holds the rows with bit 0 =
+  // rl & 1; the partner (lane ^ 16) the others.  Bit 0 clear: own + other;
+  // set: other - own = other + (own ^ -1) + 1.
+  const uint32_t hbit = (uint32_t)(rl & 1);
+  const uint64_t hmask = 0ull - hbit;
 
   uint64_t acc[JU];
 #pragma unroll
@@ -281,18 +297,20 @@ __global__ void __launch_bounds__(kNT, 1)
     const bool ok = mbar_wait_bounded(&bar[s], parity, kWaitLimit64);
     uint64_t* st = stage + (size_t)s * kR2 * kW;
 
-    // Register phase: raw bits of rows rl + 32 e, their largest exponent.
+    // Register phase: raw bits of rows rl + 32 e, their largest exponent
+    // (kept in place in bits 20-30 of the high word).
     uint64_t v[16];
-    int me = 1;
+    uint32_t mex = 0x00100000u;  // exponent field 1 (the subnormal floor)
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int rr = rl + 32 * e;
       const uint64_t raw = rr < nvalid ? st[rr * kW + cg] : 0ull;
       v[e] = raw;
-      me = max(me, (int)((raw >> 52) & 0x7FFu));
+      mex = max(mex, (uint32_t)(raw >> 32) & 0x7FF00000u);
     }
+    const int me = (int)(mex >> 20);
     if (new_panel && tid < kW) s_scale[tid] = 0;
-    const bool raise = me > scale;
+    const bool raise = scale < kNonFinite && me > scale;
     // One barrier checks the (bounded) TMA wait and whether any column's
     // scale must grow; both are rare, and then handled CTA-uniformly.
     if (__syncthreads_or(!ok || raise)) {
@@ -316,20 +334,32 @@ __global__ void __launch_bounds__(kNT, 1)
       fence_proxy_async_smem();
       issue_next();
     }
+    if (scale >= 48) {
+      const int c0 = 5 + scale;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = to_fixed(v[e], scale, (dmask >> e) & 1u);
+      for (int e = 0; e < 16; ++e) v[e] = to_fixed_fast(v[e], c0, dmask << (31 - e));
+    } else {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) v[e] = to_fixed(v[e], scale, (dmask >> e) & 1u);
+    }
     fwht_u64<16>(v);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const uint64_t other = __shfl_xor_sync(0xffffffffu, v[e], 16);
+      v[e] = other + (v[e] ^ hmask) + hbit;
+    }
 #pragma unroll
     for (int e = 0; e < 16; ++e) st[(rl + 32 * e) * kW + cg] = v[e];
     __syncthreads();
-    // Exchange phase: rows 16 g + b (g = rl).
+    // Exchange phase: rows (g & 1) + 2 b + 32 (g >> 1), g = rl.
+    const int xr0 = (rl & 1) + 32 * (rl >> 1);
 #pragma unroll
-    for (int b = 0; b < 16; ++b) v[b] = st[(16 * rl + b) * kW + cg];
+    for (int b = 0; b < 16; ++b) v[b] = st[(xr0 + 2 * b) * kW + cg];
     fwht_u64<16>(v);
 #pragma unroll
-    for (int b = 0; b < 16; ++b) st[(16 * rl + b) * kW + cg] = v[b];
+    for (int b = 0; b < 16; ++b) st[(xr0 + 2 * b) * kW + cg] = v[b];
     __syncthreads();
-    // Gather with the last stage folded in: T[s] = T'[s0] + (-1)^tau T'[s0 + 16].
+    // Gather: T[s_j] with the outer-factor x Dt^(i) sign.
     const uint4* offv = reinterpret_cast<const uint4*>(s_off + rl * JU);
     const uint64_t* tq = st + cg;
 #pragma unroll
@@ -339,11 +369,9 @@ __global__ void __launch_bounds__(kNT, 1)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int u = 4 * u4 + q;
-        const uint64_t x0 = tq[oo[q]], x1 = tq[oo[q] + 16 * kW];
-        const uint32_t sg = (gmask[u >> 4] >> (u & 15)) & 1u;
-        const uint32_t st1 = sg ^ ((tau >> u) & 1u);
-        const uint64_t m0 = 0ull - sg, m1 = 0ull - st1;
-        acc[u] += ((x0 ^ m0) + (x1 ^ m1)) + (uint64_t)(sg + st1);
+        const uint64_t x = tq[oo[q]];
+        const uint64_t m = (uint64_t)(int64_t)((int32_t)(gmask[u >> 4] << (31 - (u & 15))) >> 31);
+        acc[u] += (x ^ m) - m;
       }
     }
     if (++nacc == kFlushChunks) flush(pc);
