@@ -66,6 +66,10 @@ def parse_args():
                     help="sketch kernel: library choice, CUDA-core butterflies (K1), tensor cores (K2, 16-bit A), "
                          "or the Gaussian-embedding comparator of Sec. 4 (FP32)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the metric's other parts (FP64 sketch, small FP64 workload, 16-bit workload, "
+                         "stated rSVD error, Nystrom, serving summary)")
+    ap.add_argument("--serve-summary-requests", type=int, default=120)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cols", type=int, default=64)
     ap.add_argument("--cpu-sample-rows", type=int, default=1 << 14)
@@ -182,12 +186,10 @@ def torch_dtype(name):
 
 
 def make_input(args, rank):
+    """The tall-skinny workload in the storage type of --dtype; the generator
+    converts each row panel (no full-size FP32 temporary for 16-bit A)."""
     import synth
     dt = torch_dtype(args.dtype)
-    import torch
-    if dt in (torch.bfloat16, torch.float16):
-        a = synth.lowrank_noise_device(args.n, args.m, seed=1236 + rank, dtype=torch.float32)
-        return a.to(dt)
     return synth.lowrank_noise_device(args.n, args.m, seed=1236 + rank, dtype=dt)
 
 
@@ -267,18 +269,44 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- our arm
-# DRAM bytes of one bsrht_sketch call from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum of k_sketch_tma), captured at n = 2^18 (4.2956 GB
-# read, 0.0120 GB of partials written) and scaled to n = 2^20 by the rows
-# processed (reads grow with n, the partials do not).  Valid only for the
-# FP32 kernel at m = 4096, p = 4, l = 512 as it stood when captured.
-SKETCH_TRAFFIC_F32_N2E20_M4096 = 4 * 4.2956e9 + 0.0120e9
+# DRAM traffic of the dominant sketch kernel, one launch at the benchmark
+# shape: dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture
+# at n = 2^18 (the full-size capture would exceed the profiler's size
+# limits), scaled to n = 2^20 by the rows processed (reads grow with n, the
+# partial-sum writes do not).  Each record holds the SHA-256 of the kernel
+# sources it was taken on; once those files change the record no longer
+# describes the kernel and the line reports null (profiles/ holds the
+# capture, its command and the hash).
+TRAFFIC_RECORDS = {
+    ("f32", 1 << 20, 4096, 4, 512): {
+        "kernel": "k_sketch_tma", "read_n2e18": None, "write": None,
+        "sources": ("paper_2210_11295_gb300/csrc/sketch_tma.cu", "paper_2210_11295_gb300/csrc/tma.cuh"),
+        "sha256": None},
+    ("f64", 1 << 20, 4096, 4, 512): {
+        "kernel": "k_sketch_f64x", "read_n2e18": None, "write": None,
+        "sources": ("paper_2210_11295_gb300/csrc/sketch_f64x.cu", "paper_2210_11295_gb300/csrc/tma.cuh"),
+        "sha256": None},
+}
 
 
-def sketch_traffic(args, mode):
-    if (args.dtype, args.n, args.m, args.p, args.l, args.variant) == ("f32", 1 << 20, 4096, 4, 512, "auto"):
-        return SKETCH_TRAFFIC_F32_N2E20_M4096
-    return None
+def _sources_sha(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def sketch_traffic(dtype, n, m, p, l, variant="auto"):
+    """Recorded DRAM bytes of one launch of the dominant sketch kernel, or
+    None (no record for this shape, or the kernel changed since)."""
+    rec = TRAFFIC_RECORDS.get((dtype, n, m, p, l))
+    if variant != "auto" or rec is None or rec["read_n2e18"] is None or rec["sha256"] is None:
+        return None
+    if _sources_sha(rec["sources"]) != rec["sha256"]:
+        return None
+    return 4 * rec["read_n2e18"] + rec["write"]
 
 
 def gaussian_comparator(args, lib, a, sketch_ms, step_ms, mode, stream):
@@ -360,6 +388,305 @@ def single_view_rsvd(args, lib, a, stream):
     torch.cuda.empty_cache()
     return {"kind": "Algorithm 3 (single view): Omega, Phi, Psi block SRHTs, Gamma Gaussian, s = 2 l", "s": s,
             "ms": round(ms, 3), "stages_ms": stages}
+
+
+# --------------------------------------------------------------- metric extras
+# The rest of the benchmark's metric, measured after the timed steps on rank
+# 0: the FP64 sketch (the paper's arithmetic), the small FP64 workload, the
+# 16-bit workload with its per-dtype errors, the stated error of the rSVD,
+# the kernel-matrix Nystrom workload and a short serving stream.  Each part
+# reports its own CUDA-event times; the oracle is used only for the stated
+# errors.
+def _events_ms(stream, fn, reps):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+
+
+def _kernel_ms(lib, fn, reps):
+    """Mean of the library's own CUDA-event time of the sketch kernel."""
+    lib.bsrht_profile_enable(True)
+    ks = []
+    for _ in range(reps):
+        fn()
+        st = dict(lib.bsrht_profile_stages())
+        if "sketch_kernel" in st:
+            ks.append(st["sketch_kernel"])
+    lib.bsrht_profile_enable(False)
+    return statistics.mean(ks) if ks else None
+
+
+def _rel(a, b):
+    import numpy as np
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def f64_sketch_object(lib, a32, p, l, peak, stream):
+    """The sketch in FP64 at the full tall-skinny shape: the FP32 workload
+    plus an FP64 perturbation of 1e-7 (full 53-bit significands)."""
+    import numpy as np
+    import torch
+    from oracle import bsrht as orc
+    n, m = a32.shape
+    a = torch.empty(n, m, device=a32.device, dtype=torch.float64)
+    gen = torch.Generator(device=a32.device)
+    gen.manual_seed(1250)
+    for r0 in range(0, n, 1 << 16):
+        r1 = min(n, r0 + (1 << 16))
+        a[r0:r1] = a32[r0:r1].double() + 1e-7 * torch.randn(r1 - r0, m, device=a32.device, dtype=torch.float64,
+                                                             generator=gen)
+    out = torch.empty(l, m, device=a.device, dtype=torch.float64)
+    ws = torch.empty(max(lib.bsrht_sketch_workspace(n, m, p, l, torch.float64), 1), dtype=torch.uint8, device=a.device)
+    run = lambda s: lib.bsrht_sketch(a, p, l, s, out=out, workspace=ws)  # noqa: E731
+    for w in range(3):
+        run(w)
+    call_ms = _events_ms(stream, lambda: run(7), 5)
+    k_ms = _kernel_ms(lib, lambda: run(8), 5) or call_ms
+    run(9)
+    torch.cuda.synchronize()
+    cols = [0, 1, 15, 16, 1000, 2047, m - 16, m - 1]
+    got = out[:, cols].cpu().numpy()
+    ref = orc.sketch_fast(a[:, cols].cpu().numpy(), p, l, 9)
+    nbytes = n * m * 8 + l * m * 8
+    ach = nbytes / (k_ms * 1e-3) / 1e9
+    del a, out, ws
+    torch.cuda.empty_cache()
+    return {"workload": f"tall-skinny lowrank+noise n={n} m={m} f64 p={p} l={l} (sketch)", "dtype": "f64",
+            "kernel": "k_sketch_f64x (exact 64-bit integer Walsh-Hadamard transform, TMA-fed)",
+            "ms": round(call_ms, 4), "kernel_ms": round(k_ms, 4), "gbs": round(nbytes / (call_ms * 1e-3) / 1e9, 2),
+            "roofline": {"bound": "hbm", "achieved": round(ach, 2), "peak": peak, "unit": "GB/s",
+                         "frac": round(ach / peak, 4), "traffic": sketch_traffic("f64", n, m, p, l)},
+            "parity": {"columns": cols, "rel_fro_vs_oracle": float(f"{_rel(got, ref):.3e}"), "tol": 1e-12}}
+
+
+def config1_object(lib, stream):
+    """The small FP64 workload: A = U diag(e^(-i/10)) V^T, n = 4096, m = 256,
+    p = 4, l = 128, rank-20 Algorithm 1, against the oracle."""
+    import numpy as np
+    import torch
+    import synth
+    from oracle import lowrank as orl
+    a_np, _ = synth.haar_spectrum(4096, 256, seed=1235)
+    a = torch.from_numpy(a_np).cuda()
+    k, l, p = 20, 128, 4
+    for _ in range(3):
+        lib.bsrht_rsvd(a, k, l, p, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 10
+    for _ in range(reps):
+        u, s, v = lib.bsrht_rsvd(a, k, l, p, 0)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / reps
+    ur, sr, vr = orl.rsvd(a_np, k, l, p, 0)
+    u, s, v = u.cpu().numpy(), s.cpu().numpy(), v.cpu().numpy()
+    approx, ref = (u * s) @ v.T, (ur * sr) @ vr.T
+    return {"workload": "haar spectrum n=4096 m=256 f64 p=4 l=128 k=20 seed 0", "ms_per_call": round(ms, 3),
+            "usvt_rel_err_vs_oracle": float(f"{_rel(approx, ref):.3e}"),
+            "sigma_max_rel_err_vs_oracle": float(f"{np.max(np.abs(s - sr)) / sr[0]:.3e}"), "tol": 1e-12,
+            "timing": "host wall clock per call (the call synchronizes on its status)"}
+
+
+def config3_object(lib, peak, stream, sample_rows=1 << 15):
+    """The 16-bit workload: n = 2^20, m = 8192 in BF16 and FP16 (FP32
+    arithmetic), p = 8, l = 1024, rank 200: sketch with the CUDA-core (K1)
+    and tensor-core (K2) kernels, one Algorithm 1 call (BF16), and on an
+    n = 2^15 sample of the same generator the errors against the FP64 oracle
+    -- on the same stored values (arithmetic error) and, for Omega A,
+    against the FP32 source before rounding to 16 bits (storage included)."""
+    import numpy as np
+    import torch
+    import synth
+    from oracle import bsrht as orc
+    from oracle import lowrank as orl
+    n, m, p, l, k = 1 << 20, 8192, 8, 1024, 200
+    res = {"workload": f"tall-skinny lowrank+noise n={n} m={m} p={p} l={l} k={k}, 16-bit storage"}
+    for name, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        a = synth.lowrank_noise_device(n, m, seed=1237, dtype=dt)
+        out = torch.empty(l, m, device=a.device, dtype=torch.float32)
+        d = {}
+        for vname, var in (("k1_cudacore", lib.VARIANT_AUTO), ("k2_tensor", lib.VARIANT_TENSOR)):
+            ws = torch.empty(max(lib.bsrht_sketch_workspace(n, m, p, l, dt, variant=var), 1), dtype=torch.uint8,
+                             device=a.device)
+            run = lambda s: lib.bsrht_sketch(a, p, l, s, out=out, workspace=ws, variant=var)  # noqa: E731
+            for w in range(2):
+                run(w)
+            call_ms = _events_ms(stream, lambda: run(5), 3)
+            k_ms = _kernel_ms(lib, lambda: run(6), 3) or call_ms
+            ach = (n * m * 2 + l * m * 4) / (k_ms * 1e-3) / 1e9
+            d[vname] = {"ms": round(call_ms, 3), "kernel_ms": round(k_ms, 3), "gbs": round(ach, 1),
+                        "frac_of_measured_peak": round(ach / peak, 4)}
+            del ws
+        if name == "bf16":
+            rws = torch.empty(lib.bsrht_rsvd_workspace(n, m, k, l, p, dt), dtype=torch.uint8, device=a.device)
+            outs = (torch.empty(n, k, device=a.device, dtype=torch.float64),
+                    torch.empty(k, device=a.device, dtype=torch.float64),
+                    torch.empty(m, k, device=a.device, dtype=torch.float64))
+            lib.bsrht_rsvd(a, k, l, p, 0, workspace=rws, outs=outs)
+            d["rsvd_ms"] = round(_events_ms(stream, lambda: lib.bsrht_rsvd(a, k, l, p, 1, workspace=rws, outs=outs),
+                                            1), 3)
+            del rws, outs
+        del a, out
+        torch.cuda.empty_cache()
+        # Errors on the sample.
+        a32 = synth.lowrank_noise_device(sample_rows, m, seed=1237, dtype=torch.float32)
+        a_s = a32.to(dt)
+        b = lib.bsrht_sketch(a_s, p, l, 1)
+        u, s, v = lib.bsrht_rsvd(a_s, k, l, p, 1)
+        torch.cuda.synchronize()
+        a64 = a_s.double().cpu().numpy()
+        src = a32.double().cpu().numpy()
+        b = b.double().cpu().numpy()
+        u, s, v = u.cpu().numpy(), s.cpu().numpy(), v.cpu().numpy()
+        ur, sr, vr = orl.rsvd(a64, k, l, p, 1)
+        e = float(np.linalg.norm(a64 - (u * s) @ v.T))
+        e_ref = float(np.linalg.norm(a64 - (ur * sr) @ vr.T))
+        d["errors_on_sample"] = {
+            "rows": sample_rows,
+            "sketch_rel_fro_vs_fp64_oracle_same_values": float(f"{_rel(b, orc.sketch_fast(a64, p, l, 1)):.3e}"),
+            "sketch_rel_fro_vs_fp64_oracle_fp32_source": float(f"{_rel(b, orc.sketch_fast(src, p, l, 1)):.3e}"),
+            "rank200_residual_rel_diff_vs_oracle": float(f"{abs(e - e_ref) / e_ref:.3e}"),
+            "rank200_residual_rel": float(f"{e / np.linalg.norm(a64):.4e}"),
+            "sigma_max_rel_err_vs_oracle": float(f"{np.max(np.abs(s - sr)) / sr[0]:.3e}")}
+        del a32, a_s
+        torch.cuda.empty_cache()
+        res[name] = d
+    return res
+
+
+def rsvd_error_object(lib, a, u, s, v, args, sample_rows=1 << 16):
+    """The stated error of the benchmark's rank-k approximation.  Full size:
+    ||A V - U S||_F / ||S|| (zero in exact arithmetic for Algorithm 1) and the
+    orthogonality of U and V.  On an n = 2^16 sample of the generator: the
+    oracle's Algorithm 1, the Eckart-Young optimum ||A - [[A]]_k||_F
+    (eigenvalues of A^T A on the GPU, in FP64) and sigma_{k+1}."""
+    import numpy as np
+    import torch
+    import synth
+    from oracle import lowrank as orl
+    n, m = a.shape
+    k, l, p = args.k, args.l, args.p
+    av = torch.cat([(a[i:i + 65536].double() @ v) for i in range(0, n, 65536)])
+    full = {"av_minus_us_rel": float(f"{(torch.linalg.norm(av - u * s) / torch.linalg.norm(s)).item():.3e}"),
+            "u_orth": float(f"{torch.linalg.norm(u.T @ u - torch.eye(k, device=u.device, dtype=u.dtype)).item():.3e}"),
+            "v_orth": float(f"{torch.linalg.norm(v.T @ v - torch.eye(k, device=v.device, dtype=v.dtype)).item():.3e}")}
+    del av
+    a_s = synth.lowrank_noise_device(sample_rows, m, seed=1236, dtype=torch.float32)
+    us, ss, vs = lib.bsrht_rsvd(a_s, k, l, p, 0)
+    gram = a_s.double().T @ a_s.double()
+    sig = torch.sqrt(torch.clamp(torch.linalg.eigvalsh(gram), min=0.0)).flip(0).cpu().numpy()
+    a64 = a_s.double().cpu().numpy()
+    us, ss, vs = us.cpu().numpy(), ss.cpu().numpy(), vs.cpu().numpy()
+    ur, sr, vr = orl.rsvd(a64, k, l, p, 0)
+    e = float(np.linalg.norm(a64 - (us * ss) @ vs.T))
+    e_ref = float(np.linalg.norm(a64 - (ur * sr) @ vr.T))
+    opt = orl.best_rank_k_errors(sig, k)
+    del a_s, gram
+    torch.cuda.empty_cache()
+    return {"full_size": full,
+            "sample": {"rows": sample_rows, "residual_fro": float(f"{e:.6e}"), "oracle_residual_fro": float(f"{e_ref:.6e}"),
+                       "rel_diff_vs_oracle": float(f"{abs(e - e_ref) / e_ref:.3e}"),
+                       "sigma_max_rel_err_vs_oracle": float(f"{np.max(np.abs(ss - sr)) / sr[0]:.3e}"),
+                       "eckart_young_fro": float(f"{opt['fro']:.6e}"), "ratio_to_optimum": round(e / opt["fro"], 5),
+                       "sigma_k_plus_1": float(f"{opt['spectral']:.6e}")}}
+
+
+def nystrom_object(lib, peak, stream, n=65536, p=8, l=600, ks=(100, 200, 400), sub=4096):
+    """The kernel-matrix workload: A_ij = exp(-|xi - xj|^2 / (2 h^2)),
+    x_i ~ U[0,1]^784, h the median pairwise distance, n = 65536 (FP32),
+    p = 8, l = 600.  Per k: time of Algorithm 2 and the trace error
+    tr(A) - sum(Lambda) (exact: the residual is PSD).  On the 4096-point
+    subsample: the same against the oracle and the optimum sum_{i>k} lambda_i."""
+    import numpy as np
+    import torch
+    import synth
+    from oracle import lowrank as orl
+    x = synth.rbf_points(n, 784, seed=1238)
+    h = synth.rbf_bandwidth(x)
+    a = synth.rbf_kernel_device(torch.from_numpy(x).cuda(), h, dtype=torch.float32)
+    tr = float(torch.trace(a.double()).item())
+    per_k = []
+    for k in ks:
+        ws = torch.empty(lib.bsrht_nystrom_workspace(n, k, l, p, torch.float32), dtype=torch.uint8, device="cuda")
+        outs = (torch.empty(n, k, device="cuda", dtype=torch.float64), torch.empty(k, device="cuda", dtype=torch.float64))
+        lib.bsrht_nystrom(a, k, l, p, 0, workspace=ws, outs=outs)
+        ms = _events_ms(stream, lambda: lib.bsrht_nystrom(a, k, l, p, 1, workspace=ws, outs=outs), 3)
+        lam = outs[1]
+        per_k.append({"k": k, "ms": round(ms, 3), "trace_error_rel": float(f"{(tr - float(lam.sum())) / tr:.5e}")})
+        del ws, outs
+    out = torch.empty(l, n, device="cuda", dtype=torch.float32)
+    sws = torch.empty(max(lib.bsrht_sketch_workspace(n, n, p, l, torch.float32), 1), dtype=torch.uint8, device="cuda")
+    lib.bsrht_sketch(a, p, l, 0, out=out, workspace=sws)
+    sk_ms = _events_ms(stream, lambda: lib.bsrht_sketch(a, p, l, 1, out=out, workspace=sws), 3)
+    del a, out, sws
+    torch.cuda.empty_cache()
+    # The subsample against the oracle (FP32 arithmetic threshold on both sides).
+    idx = np.sort(np.random.default_rng(1239).choice(n, size=sub, replace=False))
+    a_sub = synth.rbf_kernel(x[idx], h).astype(np.float32)
+    lam_all = np.linalg.eigvalsh(a_sub.astype(np.float64))[::-1]
+    tr_s = float(np.trace(a_sub.astype(np.float64)))
+    sub_rows = []
+    for k in ks:
+        _, lam_d = lib.bsrht_nystrom(torch.from_numpy(a_sub).cuda(), k, l, p, 0)
+        torch.cuda.synchronize()
+        _, lam_o, _ = orl.nystrom(a_sub.astype(np.float64), k, l, p, 0, unit_roundoff=2.0 ** -23)
+        sub_rows.append({"k": k, "trace_error_rel": float(f"{(tr_s - float(lam_d.sum())) / tr_s:.5e}"),
+                         "oracle_trace_error_rel": float(f"{(tr_s - float(lam_o.sum())) / tr_s:.5e}"),
+                         "optimum_rel": float(f"{float(np.sum(lam_all[k:])) / tr_s:.5e}")})
+    gbs = (n * n * 4 + l * n * 4) / (sk_ms * 1e-3) / 1e9
+    return {"workload": f"RBF kernel n={n} (x ~ U[0,1]^784, median bandwidth h={h:.4f}) fp32 p={p} l={l}",
+            "per_k": per_k, "sketch": {"ms": round(sk_ms, 3), "gbs": round(gbs, 1), "frac_of_measured_peak": round(gbs / peak, 4)},
+            "subsample": {"points": sub, "per_k": sub_rows}}
+
+
+def serve_object(lib, requests=120, compare=40):
+    """A short config-5 stream through the serving loop (the serve mode runs
+    the long one): saturation throughput, Poisson arrivals at 0.5x of it
+    with p50 / p99 latency, and a reduced stream (n <= 2^17, m <= 1024)
+    served in FP32 against the plain FP64 one-request-at-a-time path."""
+    import numpy as np
+    import torch
+    import synth
+    reqs = synth.request_stream(requests, seed=1240, rate_hz=1.0)
+    rng = np.random.default_rng(1242)
+    dtypes = [torch.bfloat16 if rng.random() < 0.5 and r["kind"] != "nystrom" else torch.float32 for r in reqs]
+    inputs = _ServeInputs()
+    kw = dict(hbm_budget=24 << 30, executors=4, max_group=16)
+    _serve_run(lib, inputs, reqs[:20], dtypes, math.inf, 96, **kw)
+    sat_s, lat_sat, st_sat, _ = _serve_run(lib, inputs, reqs, dtypes, math.inf, 96, **kw)
+    x_sat = len(reqs) / sat_s
+    ms, lat, st, _ = _serve_run(lib, inputs, reqs, dtypes, 0.5 * x_sat, 96, **kw)
+    small = [r for r in synth.request_stream(20 * compare, seed=1243, rate_hz=1.0, nystrom_max_log2n=14)
+             if r["n"] <= 1 << 17 and (r["m"] <= 1024 or r["kind"] == "nystrom")][:compare]
+    sdt = [torch.float32] * len(small)
+    p_s, _, p_outs = _plain_run(lib, inputs, small, math.inf, keep_outputs=True)
+    s_s, _, _, s_outs = _serve_run(lib, inputs, small, sdt, math.inf, len(small), keep_outputs=True, **kw)
+    acc = _accuracy(lib, inputs, small, s_outs, p_outs, sdt)
+    del inputs
+    torch.cuda.empty_cache()
+    return {"stream": f"{len(reqs)} config-5 requests (sketch / rSVD / Nystrom, half BF16)",
+            "saturation_req_s": round(x_sat, 2), "saturation_p50_ms": round(_pct(lat_sat, 50), 2),
+            "saturation_p99_ms": round(_pct(lat_sat, 99), 2),
+            "poisson_0.5x": {"rate_req_s": round(0.5 * x_sat, 2), "p50_ms": round(_pct(lat, 50), 2),
+                             "p99_ms": round(_pct(lat, 99), 2), "makespan_s": round(ms, 2)},
+            "grouped_requests": st_sat["grouped_requests"], "graph_launches": st_sat["graph_launches"],
+            "vs_plain_fp64": {"requests": len(small), "closed_batch_speedup": round(p_s / s_s, 2),
+                              "accuracy_worst": {kk: float(f"{vv:.3e}") for kk, vv in acc.items()}}}
+
+
+def _extra(name, fn, out):
+    """Runs one extra measurement; a failure is recorded, not fatal."""
+    t0 = time.perf_counter()
+    try:
+        out[name] = fn()
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+    except Exception as e:  # noqa: BLE001 -- reported in the JSON line
+        out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
 
 
 def run_ours(args):
@@ -466,6 +793,18 @@ def run_ours(args):
     # its stages.
     single_view = single_view_rsvd(args, lib, a, stream) if mode == "full" and args.variant == "auto" else None
 
+    # The metric's other parts (rank 0, the default tall-skinny FP32 run).
+    extras = {}
+    default_shape = (args.dtype, n, m, p, l, k, args.variant) == ("f32", 1 << 20, 4096, 4, 512, 100, "auto")
+    if mode == "full" and default_shape and rank == 0 and not args.no_extras:
+        peak_v = peaks()[0]
+        _extra("rsvd_error", lambda: rsvd_error_object(lib, a, u, s, v, args), extras)
+        _extra("f64", lambda: f64_sketch_object(lib, a, p, l, peak_v, stream), extras)
+        _extra("config1_fp64", lambda: config1_object(lib, stream), extras)
+        _extra("nystrom", lambda: nystrom_object(lib, peak_v, stream), extras)
+        _extra("config3_16bit", lambda: config3_object(lib, peak_v, stream), extras)
+        _extra("serve", lambda: serve_object(lib, args.serve_summary_requests), extras)
+
     # End to end through the C ABI from pinned host buffers.
     a_host = a.cpu().pin_memory()
     e2e_ms = None
@@ -524,7 +863,8 @@ def run_ours(args):
                    "frac_of_measured_peak": round(achieved_call / peak, 4),
                    "kernel_ms": round(kernel_ms, 4) if kernel_ms else None},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": sketch_traffic(args, mode),
+                     "frac": round(achieved / peak, 4),
+                     "traffic": sketch_traffic(args.dtype, n, m, p, l, args.variant),
                      "kernel": ("k_sketch_chunked + k_sketch_reduce (one bsrht_sketch call)" if args.dtype == "f64"
                                 else ("k_sketch_tc" if args.variant == "tensor" else "k_sketch_tma")
                                 + " (its own CUDA events; the whole bsrht_sketch call, with the sign tables and "
@@ -543,6 +883,7 @@ def run_ours(args):
         line["gaussian_comparator"] = comparator
     if single_view:
         line["single_view_rsvd"] = single_view
+    line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:

@@ -163,7 +163,8 @@ int bsrht_sketch_noalloc(const void* A, int64_t n, int64_t m, int32_t p,
  *   double, U and V with orthonormal columns.  Requires 1 <= k <= l <= m and
  *   l <= n.  Steps: B = Omega A; Q = an orthonormal basis of range(B^T), FP64
  *   and rank revealing: m x l' with l' <= l the number of singular values of
- *   B above l 2^-52 sigma_1 (CholeskyQR2 when B is well conditioned, else
+ *   B above l 2^-44 sigma_1 (l times the relative precision of the FP64
+ *   sketch) (CholeskyQR2 when B is well conditioned, else
  *   Householder QR and a Jacobi SVD of its R factor; l' < l when Omega
  *   repeats a row up to sign in every block, which sampling with replacement
  *   allows, or when rank(A) < l); W = A Q (second pass over A, in the

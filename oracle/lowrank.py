@@ -14,8 +14,8 @@ Readings of the paper used here (each also listed with the design notes):
   every block, and then range(Y) has dimension r' < l; completing Q with
   arbitrary directions would make the result depend on them. Q is therefore
   rank revealing: the left singular vectors of Y (LAPACK SVD) whose singular
-  value exceeds tau * sigma_1, tau = l * 2^-52. Steps 3-6 then run on r'
-  columns; with r' < k the trailing singular values and the matching columns
+  value exceeds tau * sigma_1, tau = l * 2^-44 (see range_tol). Steps 3-6
+  then run on r' columns; with r' < k the trailing singular values and the matching columns
   of U and V are zero. Step 4 uses Householder QR (LAPACK geqrf/orgqr via
   numpy) and step 5 the SVD of the small R^T factor (LAPACK gesdd).
 * Algorithm 2, step 6 writes (Y V~_k) Sigma~_k^-1; with Z = Q~ R and
@@ -80,10 +80,18 @@ def truncated_svd(a: np.ndarray, k: int):
     return uk, s[:k], vk
 
 
+# Relative precision the FP64 sketch is computed to: its Walsh-Hadamard
+# transform is exact on fixed-point values with at least 45 fraction bits
+# below each column's largest magnitude; 2^-44 bounds that conversion.
+SKETCH_PRECISION = 2.0 ** -44
+
+
 def range_tol(l: int) -> float:
     """Rank rule of the basis of range(Y): directions with sigma <= tau sigma_1
-    are numerically absent, tau = l * 2^-52 (l columns, FP64 unit roundoff)."""
-    return l * EPS64
+    are numerically absent, tau = l * 2^-44 (l columns times the relative
+    precision of the FP64 sketch), so that directions that are zero in exact
+    arithmetic are dropped whatever rounding the sketch carried."""
+    return l * SKETCH_PRECISION
 
 
 def range_basis(y: np.ndarray) -> np.ndarray:

@@ -1,5 +1,7 @@
 // extern "C" entry points of libbsrht (declared in include/bsrht.h).
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 
 #include "capi_internal.cuh"
@@ -25,6 +27,12 @@ Pool g_pool[64];
 }  // namespace
 
 void note_launches(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+
+int cuda_failure(cudaError_t e, const char* file, int line) {
+  static const bool debug = std::getenv("BSRHT_DEBUG") != nullptr;
+  if (debug) std::fprintf(stderr, "bsrht: %s at %s:%d\n", cudaGetErrorName(e), file, line);
+  return BSRHT_ECUDA;
+}
 
 int pool_get(size_t bytes, void** out) {
   *out = nullptr;

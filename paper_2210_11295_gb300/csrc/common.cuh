@@ -120,8 +120,14 @@ inline size_t dtype_size(int dt) { return dt == BSRHT_F64 ? 8 : (dt == BSRHT_F32
 
 }  // namespace bsrht
 
-#define BSRHT_CUDA_TRY(expr)                      \
-  do {                                            \
-    cudaError_t e_ = (expr);                      \
-    if (e_ != cudaSuccess) return BSRHT_ECUDA;    \
+namespace bsrht {
+// Reports a failed CUDA call on stderr (file, line, error name) when the
+// environment variable BSRHT_DEBUG is set; returns BSRHT_ECUDA.
+int cuda_failure(cudaError_t e, const char* file, int line);
+}  // namespace bsrht
+
+#define BSRHT_CUDA_TRY(expr)                                                \
+  do {                                                                      \
+    cudaError_t e_ = (expr);                                                \
+    if (e_ != cudaSuccess) return ::bsrht::cuda_failure(e_, __FILE__, __LINE__); \
   } while (0)

@@ -15,9 +15,10 @@ namespace cg = cooperative_groups;
 
 namespace bsrht {
 
-#define DLA_LAUNCH_CHECK()                       \
-  do {                                           \
-    if (cudaGetLastError() != cudaSuccess) return BSRHT_ECUDA; \
+#define DLA_LAUNCH_CHECK()                                                   \
+  do {                                                                       \
+    const cudaError_t e_ = cudaGetLastError();                               \
+    if (e_ != cudaSuccess) return ::bsrht::cuda_failure(e_, __FILE__, __LINE__); \
   } while (0)
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -61,7 +62,7 @@ static int launch_cooperative(const void* func, dim3 grid, dim3 block, void** ar
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, after, 0);
   cudaEventDestroy(before);  // released once the recorded work completes
   cudaEventDestroy(after);
-  return e == cudaSuccess ? BSRHT_OK : BSRHT_ECUDA;
+  return e == cudaSuccess ? BSRHT_OK : cuda_failure(e, __FILE__, __LINE__);
 }
 
 // ------------------------------------------------------------------ GEMM
@@ -1003,7 +1004,12 @@ int launch_jacobi_blk_b(const Dla& d, float* M, float* V, int64_t l, double tol,
   int li = (int)l, nblk = (int)((l + B - 1) / B), msw = max_sweeps;
   nblk += nblk & 1;
   const size_t smem = sizeof(float) * ((size_t)4 * B * l + 2 * B);
-  BSRHT_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_blk<B, JR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // One instance serves every l up to 32 JR, and host threads (the server's
+  // executors) launch it concurrently: the attribute is always set to the
+  // largest of them, so no thread lowers it below another one's launch.
+  const size_t smem_max = sizeof(float) * ((size_t)4 * B * 32 * JR + 2 * B);
+  BSRHT_CUDA_TRY(
+      cudaFuncSetAttribute(k_jacobi_blk<B, JR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
   int occ = 0;
   BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_blk<B, JR>, 32 * B, smem));
   if ((int64_t)(nblk / 2) > (int64_t)occ * num_sms()) return BSRHT_EUNSUP;  // not co-resident: caller falls back
@@ -1044,7 +1050,7 @@ int launch_jacobi_blk(const Dla& d, float* M, float* V, int64_t l, double tol, d
 }  // namespace
 
 int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout,
-               double polish_tol) {
+               double polish_tol, double zero_rel) {
   if (l > 2048) return BSRHT_EUNSUP;
   const int max_sweeps = 40;
   // Rotate only while the cosine of the pair exceeds sqrt(l) eps (the usual
@@ -1129,7 +1135,8 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
     DLA_LAUNCH_CHECK();
   }
   // 4. FP64 one-sided Jacobi (from V0 it converges in a few sweeps).
-  TRY_DLA(launch_jacobi<double>(d, cols, Vc, nrm64, l, tol, 16.0 * tol, fnorm, (double)l * 0x1.0p-53, max_sweeps,
+  TRY_DLA(launch_jacobi<double>(d, cols, Vc, nrm64, l, tol, 16.0 * tol, fnorm,
+                                std::max((double)l * 0x1.0p-53, zero_rel), max_sweeps,
                                 rot, d.status));
   k_col_norms<<<blocks_for(l, 8), 256, 0, d.s>>>(cols, sig, l);
   DLA_LAUNCH_CHECK();

@@ -78,8 +78,13 @@ int chol_inv(const Dla& d, double* g, double* LT, double* Rinv, double* T, doubl
 // polish_tol > 0 replaces the FP64 rotation threshold sqrt(l) 2^-52 on the
 // cosine of a pair: Vout (accumulated rotations) stays orthogonal to FP64
 // rounding whatever the threshold, the columns of U to about polish_tol.
+// Two columns whose norms are both at most zero_rel ||M||_F (at least
+// l 2^-53) count as numerically zero and are not rotated against each other:
+// a caller that drops directions below a rank threshold passes it here, so
+// that columns made of rounding noise at that level do not keep the sweeps
+// going.
 int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout,
-               double polish_tol = 0.0);
+               double polish_tol = 0.0, double zero_rel = 0.0);
 
 // Tensor-core (tcgen05) GEMM in FP32 accuracy (three TF32 products):
 // C (M x N, FP32 or FP64 in tc_out, ldc) = A (M x K, FP32, lda) * B, with B

@@ -67,6 +67,26 @@ int tall_gemm(const Dla& d, Arena& ar, DT ta, DT tc, DT tout, int64_t M, int64_t
               int64_t lda, const double* B64, const void* B32, int64_t ldb, void* C, int64_t ldc, bool tri_b,
               float* Ct = nullptr, bool* ct_done = nullptr) {
   if (ct_done) *ct_done = false;
+  if (ar.measure) {
+    // Which form runs depends on pointers and on column counts that a
+    // rank-revealing basis can lower at run time: size every form the call
+    // could take (tensor cores with N columns and with N rounded down to a
+    // multiple of 4, and the CUDA-core GEMM); the arena keeps the largest.
+    const size_t mk = ar.mark();
+    if (ta == DT::F32 && tc == DT::F32 && M >= 256) {
+      for (int64_t nn : {N, N - N % 4}) {
+        if (nn < 1) continue;
+        const int st = gemm_tc(d, ar, M, nn, K, nullptr, lda, DT::F64, nullptr, ldb, false, tout, nullptr, ldc,
+                               false, tri_b, tout == DT::F32 ? Ct : nullptr);
+        ar.release(mk);
+        if (st != BSRHT_OK && st != BSRHT_EUNSUP) return st;
+      }
+    }
+    const int st = gemm_c(d, ar, ta, tc, tout, M, N, K, A, lda, false, tc == DT::F64 ? (const void*)B64 : B32, ldb,
+                          C, ldc, tri_b, false);
+    ar.release(mk);
+    return st;
+  }
   if (ta == DT::F32 && use_tc(tc, M, N, K, A, lda) && B64 != nullptr) {
     if (tout != DT::F32) Ct = nullptr;
     const size_t mk = ar.mark();
@@ -85,6 +105,24 @@ int tall_gemm(const Dla& d, Arena& ar, DT ta, DT tc, DT tout, int64_t M, int64_t
 // says the product that formed X already left X^T (FP32) there.
 int tall_gram(const Dla& d, Arena& ar, bool dry, DT tc, const void* X, int64_t rows, int64_t l, void* scratch,
               double* G, bool have_t = false) {
+  if (ar.measure) {
+    // As in tall_gemm: size the tensor-core form at l and at l rounded down
+    // to a multiple of 4 (a lower run-time rank may select it) and the
+    // CUDA-core form.
+    const size_t mk = ar.mark();
+    if (tc == DT::F32 && l >= 256 && (rows % 4) == 0) {
+      for (int64_t ll : {l, l - l % 4}) {
+        if (ll < 4 || (ll % 4) != 0) continue;
+        const int st = gemm_tc(d, ar, ll, ll, rows, nullptr, rows, DT::F32, nullptr, rows, true, DT::F64, G, ll,
+                               true);
+        ar.release(mk);
+        if (st != BSRHT_OK && st != BSRHT_EUNSUP) return st;
+      }
+    }
+    const int st = gemm_c(d, ar, tc, tc, DT::F64, l, l, rows, X, l, true, X, l, G, l, false, true);
+    ar.release(mk);
+    return st;
+  }
   if (use_tc(tc, l, l, rows, scratch, rows) && (rows % 4) == 0 && (l % 4) == 0) {
     if (!dry && !have_t) {
       const int st = transpose_to_f32(d, DT::F32, X, rows, l, l, static_cast<float*>(scratch), rows);
@@ -354,8 +392,11 @@ __global__ void k_upper_to_cols(const double* __restrict__ Z, int64_t l, double*
 }
 
 // Rank rule of the basis of range(Y): directions with sigma <= tau sigma_1
-// are numerically absent, tau = l 2^-52.
-double range_tol(int64_t l) { return (double)l * 0x1.0p-52; }
+// are numerically absent, tau = l 2^-44: l times the relative precision of
+// the FP64 sketch (its transform is exact on fixed-point values with at
+// least 45 fraction bits below each column's largest magnitude), so that
+// directions that vanish in exact arithmetic are dropped.
+double range_tol(int64_t l) { return (double)l * 0x1.0p-44; }
 
 // Orthonormal basis Q of the numerical range of the FP64 sketch matrix X
 // (rows x l), Algorithm 1 step 2: range(Q) = range(Y).  Sampling with
@@ -397,7 +438,11 @@ int range_basis(const Dla& d, Arena& ar, bool dry, double* X, double* Y, double*
   }
   {
     const size_t mk = ar.mark();
-    TRY(jacobi_svd(d, ar, b.G, l, b.Ug, b.lam, b.Vg));  // R V = U S: b.Ug = Ur (l x l), b.lam = S
+    // R V = U S: b.Ug = Ur (l x l), b.lam = S.  Columns whose norm is below
+    // the rank rule's tau (against ||R||_F) are numerically zero for the
+    // Jacobi too: they hold the rounding of the sketch (about 2^-45 of its
+    // scale for FP64 data) and would otherwise keep the sweeps going.
+    TRY(jacobi_svd(d, ar, b.G, l, b.Ug, b.lam, b.Vg, 0.0, range_tol(l)));
     ar.release(mk);
   }
   int64_t r = l;
@@ -794,8 +839,12 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
   const int64_t lda = o.lda ? o.lda : n;
   SketchPlan sp_a, sp_y;
   TRY(sketch_make_plan(sp_a, o.dtype, o.variant, n, n, lda, p, l, !dry, dry ? nullptr : A));
-  // The l x l core Omega Y_nu is formed in FP64 whatever the type of A.
-  TRY(sketch_make_plan(sp_y, BSRHT_F64, BSRHT_VARIANT_CUDACORE, n, l, l, p, l, !dry));
+  // The l x l core Omega Y_nu is formed in FP64 whatever the type of A, with
+  // the FP64-add kernel: the shift nu of Remark 3.1 is a few FP64 units of
+  // ||Y||, below the precision of the fixed-point FP64 sketch (an address
+  // the TMA rules reject steers the plan to it, as for grouped sketches).
+  TRY(sketch_make_plan(sp_y, BSRHT_F64, BSRHT_VARIANT_CUDACORE, n, l, l, p, l, !dry,
+                       reinterpret_cast<const void*>(uintptr_t(1))));
   const int64_t rb = sp_a.rb, r = sp_a.r;
   Dla d{static_cast<cudaStream_t>(o.stream), nullptr};
   d.status = static_cast<int*>(ar.take(sizeof(int)));

@@ -260,7 +260,7 @@ int run_graph(cudaStream_t s, GraphCache& cache, const std::string& key, F&& enq
   if (st != BSRHT_OK || ce != cudaSuccess || g == nullptr) {
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
-    return st != BSRHT_OK ? st : BSRHT_ECUDA;
+    return st != BSRHT_OK ? st : cuda_failure(ce, __FILE__, __LINE__);
   }
   auto it = cache.execs.find(key);
   if (it != cache.execs.end()) {
@@ -282,7 +282,7 @@ int run_graph(cudaStream_t s, GraphCache& cache, const std::string& key, F&& enq
   cudaGraphDestroy(g);
   if (ie != cudaSuccess) {
     cudaGetLastError();
-    return BSRHT_ECUDA;
+    return cuda_failure(ie, __FILE__, __LINE__);
   }
   cache.execs[key] = ex;
   return cudaGraphLaunch(ex, s) == cudaSuccess ? BSRHT_OK : BSRHT_ECUDA;
@@ -290,12 +290,13 @@ int run_graph(cudaStream_t s, GraphCache& cache, const std::string& key, F&& enq
 
 // Bounded wait for everything enqueued on s so far.
 int wait_bounded(cudaStream_t s, cudaEvent_t ev, int64_t timeout_ms) {
-  if (cudaEventRecord(ev, s) != cudaSuccess) return BSRHT_ECUDA;
+  const cudaError_t er = cudaEventRecord(ev, s);
+  if (er != cudaSuccess) return cuda_failure(er, __FILE__, __LINE__);
   const double t0 = now_s();
   for (;;) {
     const cudaError_t e = cudaEventQuery(ev);
     if (e == cudaSuccess) return BSRHT_OK;
-    if (e != cudaErrorNotReady) return BSRHT_ECUDA;
+    if (e != cudaErrorNotReady) return cuda_failure(e, __FILE__, __LINE__);
     if ((now_s() - t0) * 1e3 > (double)timeout_ms) return BSRHT_ETIMEDOUT;
     std::this_thread::sleep_for(std::chrono::microseconds(20));
   }

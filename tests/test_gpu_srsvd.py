@@ -43,7 +43,7 @@ def test_srsvd_exact_recovery_fp64(lib, p):
 
 def test_srsvd_matches_oracle_fp64(lib):
     """Rank 10 plus a 1e-9 noise floor: Q and P are rank-revealing bases on
-    both sides (every direction above l 2^-52 sigma_1 kept), so both
+    both sides (every direction above l 2^-44 sigma_1 kept), so both
     determine the same rank-10 factors: 1e-12 relative."""
     rng = np.random.default_rng(30)
     a = synth.exact_rank(4096, 1024, 10, seed=31) + 1e-9 * rng.standard_normal((4096, 1024))

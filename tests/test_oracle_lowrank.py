@@ -198,19 +198,19 @@ def test_rsvd_repeated_rows_is_truncated_svd_of_projection(n, m, p, l, seed, k):
 
 
 def test_range_basis_rule_is_relative_and_scale_free():
-    """Directions with sigma <= l 2^-52 sigma_1 are dropped, larger ones kept,
-    whatever the scale of Y: sigma ratios 1, 1e-3, 1e-11 (kept) and an exact
-    null direction (dropped), scaled by 1e-150 and 1e150."""
+    """Directions with sigma <= l 2^-44 sigma_1 are dropped, larger ones kept,
+    whatever the scale of Y: sigma ratios 1, 1e-3, 1e-11 (kept) and 1e-14
+    and an exact null direction (dropped), scaled by 1e-150 and 1e150."""
     rng = np.random.default_rng(2)
-    u = np.linalg.qr(rng.standard_normal((40, 4)))[0]
-    v = np.linalg.qr(rng.standard_normal((4, 4)))[0]
+    u = np.linalg.qr(rng.standard_normal((40, 5)))[0]
+    v = np.linalg.qr(rng.standard_normal((5, 5)))[0]
     for scale in (1e-150, 1.0, 1e150):
-        y = (u * (scale * np.array([1.0, 1e-3, 1e-11, 0.0]))) @ v.T
+        y = (u * (scale * np.array([1.0, 1e-3, 1e-11, 1e-14, 0.0]))) @ v.T
         q = lowrank.range_basis(y)
         assert q.shape == (40, 3)
         p_ref = u[:, :3] @ u[:, :3].T
         assert np.linalg.norm(q @ q.T - p_ref) <= 1e-4  # the 1e-11 direction is resolved to ~1e-5
-    assert lowrank.range_tol(128) == 128 * 2.0 ** -52
+    assert lowrank.range_tol(128) == 128 * 2.0 ** -44
 
 
 def test_rsvd_rank_below_k_pads_with_zeros():
