@@ -278,18 +278,24 @@ def run_reference(args):
 # describes the kernel and the line reports null (profiles/ holds the
 # capture, its command and the hash).
 TRAFFIC_RECORDS = {
+    # FP32: the reads are A itself; the writes are the per-(CTA, panel)
+    # partial sums, written once (they do not grow with n).
     ("f32", 1 << 20, 4096, 4, 512): {
-        "kernel": "k_sketch_tma", "read_n2e18": None, "write": None,
+        "kernel": "k_sketch_tma", "read_n2e18": 4295588608, "write_n2e18": 11199744, "write_scales": False,
         "sources": ("paper_2210_11295_gb300/csrc/sketch_tma.cu", "paper_2210_11295_gb300/csrc/tma.cuh"),
-        "sha256": None},
+        "sha256": "6d8bc313d6c64fa2da716ee63d46283bfd08cc39c2096305f0cd33a56bd0e97d"},
+    # FP64: besides A, the read-modify-write of the FP64 partial sums at
+    # every flush of the integer sums (one per 32 chunks of a CTA), which
+    # grows with n like the reads.
     ("f64", 1 << 20, 4096, 4, 512): {
-        "kernel": "k_sketch_f64x", "read_n2e18": None, "write": None,
+        "kernel": "k_sketch_f64x", "read_n2e18": 8839051008, "write_n2e18": 266475776, "write_scales": True,
         "sources": ("paper_2210_11295_gb300/csrc/sketch_f64x.cu", "paper_2210_11295_gb300/csrc/tma.cuh"),
-        "sha256": None},
+        "sha256": "355d9498c01dfb623bf0a0c099e6941c4d448c0a76b89af6319342e80145d2b3"},
 }
 
 
 def _sources_sha(paths):
+    """SHA-256 of the files concatenated (what cat a b | sha256sum prints)."""
     import hashlib
     h = hashlib.sha256()
     for p in paths:
@@ -302,11 +308,11 @@ def sketch_traffic(dtype, n, m, p, l, variant="auto"):
     """Recorded DRAM bytes of one launch of the dominant sketch kernel, or
     None (no record for this shape, or the kernel changed since)."""
     rec = TRAFFIC_RECORDS.get((dtype, n, m, p, l))
-    if variant != "auto" or rec is None or rec["read_n2e18"] is None or rec["sha256"] is None:
+    if variant != "auto" or rec is None:
         return None
     if _sources_sha(rec["sources"]) != rec["sha256"]:
         return None
-    return 4 * rec["read_n2e18"] + rec["write"]
+    return 4 * rec["read_n2e18"] + (4 if rec["write_scales"] else 1) * rec["write_n2e18"]
 
 
 def gaussian_comparator(args, lib, a, sketch_ms, step_ms, mode, stream):
@@ -608,7 +614,12 @@ def nystrom_object(lib, peak, stream, n=65536, p=8, l=600, ks=(100, 200, 400), s
     from oracle import lowrank as orl
     x = synth.rbf_points(n, 784, seed=1238)
     h = synth.rbf_bandwidth(x)
-    a = synth.rbf_kernel_device(torch.from_numpy(x).cuda(), h, dtype=torch.float32)
+    xd = torch.from_numpy(x).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a = synth.rbf_kernel_device(xd, h, dtype=torch.float32)
+    torch.cuda.synchronize()
+    gen_ms = (time.perf_counter() - t0) * 1e3
     tr = float(torch.trace(a.double()).item())
     per_k = []
     for k in ks:
@@ -624,6 +635,21 @@ def nystrom_object(lib, peak, stream, n=65536, p=8, l=600, ks=(100, 200, 400), s
     lib.bsrht_sketch(a, p, l, 0, out=out, workspace=sws)
     sk_ms = _events_ms(stream, lambda: lib.bsrht_sketch(a, p, l, 1, out=out, workspace=sws), 3)
     del a, out, sws
+    torch.cuda.empty_cache()
+    # Matrix-free: A formed a column panel at a time from the points and
+    # sketched right away (bsrht_nystrom_rbf), k = ks[0].
+    k0 = ks[0]
+    fws = torch.empty(lib.bsrht_nystrom_rbf_workspace(n, 784, k0, l, p), dtype=torch.uint8, device="cuda")
+    fouts = (torch.empty(n, k0, device="cuda", dtype=torch.float64), torch.empty(k0, device="cuda", dtype=torch.float64))
+    lib.bsrht_nystrom_rbf(xd, h, k0, l, p, 0, workspace=fws, outs=fouts)
+    mf_ms = _events_ms(stream, lambda: lib.bsrht_nystrom_rbf(xd, h, k0, l, p, 1, workspace=fws, outs=fouts), 3)
+    matrix_free = {"k": k0, "ms": round(mf_ms, 3),
+                   "trace_error_rel": float(f"{(tr - float(fouts[1].sum())) / tr:.5e}"),
+                   "scratch_gb": round(fws.numel() / 1e9, 2), "stored_matrix_gb": round(n * n * 4 / 1e9, 2),
+                   "stored_path_ms": per_k[0]["ms"], "generate_stored_matrix_ms": round(gen_ms, 1),
+                   "note": "the stored path needs the n x n matrix formed first (generate_stored_matrix_ms, "
+                           "torch); the matrix-free path forms it panel by panel inside the call"}
+    del fws, fouts, xd
     torch.cuda.empty_cache()
     # The subsample against the oracle (FP32 arithmetic threshold on both sides).
     idx = np.sort(np.random.default_rng(1239).choice(n, size=sub, replace=False))
@@ -641,6 +667,7 @@ def nystrom_object(lib, peak, stream, n=65536, p=8, l=600, ks=(100, 200, 400), s
     gbs = (n * n * 4 + l * n * 4) / (sk_ms * 1e-3) / 1e9
     return {"workload": f"RBF kernel n={n} (x ~ U[0,1]^784, median bandwidth h={h:.4f}) fp32 p={p} l={l}",
             "per_k": per_k, "sketch": {"ms": round(sk_ms, 3), "gbs": round(gbs, 1), "frac_of_measured_peak": round(gbs / peak, 4)},
+            "matrix_free": matrix_free,
             "subsample": {"points": sub, "per_k": sub_rows}}
 
 

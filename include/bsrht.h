@@ -241,6 +241,33 @@ int bsrht_nystrom(const void* A, int64_t n, int32_t k, int64_t l, int32_t p,
 int bsrht_nystrom_workspace(int64_t n, int32_t k, int64_t l, int32_t p,
                             const bsrht_opts* opts, size_t* bytes);
 
+/*
+ * bsrht_nystrom_rbf - bsrht_nystrom on the kernel matrix of a point set,
+ * without storing the matrix (Sec. 4.1 applies Algorithm 2 to such RBF
+ * kernel matrices; step 1 only needs Omega A, which is built from column
+ * panels of A):
+ *   A_ij = exp(-|x_i - x_j|^2 / (2 h^2)),  x_i the rows of X.
+ *   X    : device, n x dim, FP32, row stride opts->lda (0 = dim; a multiple
+ *          of 4, X 16-byte aligned: BSRHT_EUNSUP otherwise); h > 0.
+ *   opts->dtype must be BSRHT_F32 (the matrix is formed in FP32 arithmetic).
+ * Each panel of about 2^28 entries (a multiple of 64 columns) is formed as
+ * the Gram of the points on the tensor cores (FP32 accuracy: three TF32
+ * products), mapped through the exponential in FP32 (the diagonal is
+ * exactly 1), and sketched into Omega A before the next panel is formed;
+ * steps 1b-7 are those of bsrht_nystrom (same shift, thresholds, status
+ * codes; synchronous with opts->stream).  A panel holds n * w FP32 values
+ * of scratch, reported by bsrht_nystrom_rbf_workspace, instead of the n x n
+ * matrix.  Entries differ from a stored FP32 kernel matrix by rounding (A is
+ * symmetric to FP32 accuracy, not bitwise).
+ */
+int bsrht_nystrom_rbf(const float* X, int64_t n, int64_t dim, double h,
+                      int32_t k, int64_t l, int32_t p, uint64_t seed,
+                      double* U, double* Lambda, const bsrht_opts* opts);
+
+int bsrht_nystrom_rbf_workspace(int64_t n, int64_t dim, int32_t k, int64_t l,
+                                int32_t p, const bsrht_opts* opts,
+                                size_t* bytes);
+
 /* Frees the library's scratch pool on the current device (no-op if empty).
  * The caller must make sure no call that uses the pool is still running. */
 int bsrht_release_pool(void);

@@ -120,6 +120,8 @@ def _load() -> ctypes.CDLL:
         "bsrht_srsvd_workspace": (ctypes.c_int, [i64, i64, i32, i64, i64, i32, po, ctypes.POINTER(sz)]),
         "bsrht_nystrom": (ctypes.c_int, [vp, i64, i32, i64, i32, u64, pd, pd, po]),
         "bsrht_nystrom_workspace": (ctypes.c_int, [i64, i32, i64, i32, po, ctypes.POINTER(sz)]),
+        "bsrht_nystrom_rbf": (ctypes.c_int, [vp, i64, i64, ctypes.c_double, i32, i64, i32, u64, pd, pd, po]),
+        "bsrht_nystrom_rbf_workspace": (ctypes.c_int, [i64, i64, i32, i64, i32, po, ctypes.POINTER(sz)]),
         "bsrht_release_pool": (ctypes.c_int, []),
         "bsrht_kernel_launches": (ctypes.c_uint64, []),
         "bsrht_profile_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -298,6 +300,36 @@ def bsrht_nystrom(a: torch.Tensor, k: int, l: int, p: int, seed: int, variant: i
     o = make_opts(a, variant, workspace, stream)
     _check(lib.bsrht_nystrom(_dptr(a), n, k, l, p, seed & (2**64 - 1), _dbl(u), _dbl(lam), ctypes.byref(o)),
            "bsrht_nystrom")
+    return u, lam
+
+
+def bsrht_nystrom_rbf_workspace(n: int, dim: int, k: int, l: int, p: int, ldx: int = 0) -> int:
+    o = Opts()
+    lib.bsrht_opts_init(ctypes.byref(o))
+    o.dtype = F32
+    o.lda = int(ldx)
+    out = ctypes.c_size_t(0)
+    _check(lib.bsrht_nystrom_rbf_workspace(n, dim, k, l, p, ctypes.byref(o), ctypes.byref(out)),
+           "bsrht_nystrom_rbf_workspace")
+    return int(out.value)
+
+
+def bsrht_nystrom_rbf(x: torch.Tensor, h: float, k: int, l: int, p: int, seed: int, variant: int = VARIANT_AUTO,
+                      workspace: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None, outs=None):
+    """Rank-k randomized Nystrom (Algorithm 2) of the RBF kernel matrix
+    A_ij = exp(-|x_i - x_j|^2 / (2 h^2)) of the rows of x (n x dim, float32),
+    without storing A: returns (U n x k, Lambda k) in float64."""
+    if x.dtype != torch.float32:
+        raise ValueError("points must be float32")
+    n, dim = x.shape
+    if outs is None:
+        u = torch.empty(n, k, device=x.device, dtype=torch.float64)
+        lam = torch.empty(k, device=x.device, dtype=torch.float64)
+    else:
+        u, lam = outs
+    o = make_opts(x, variant, workspace, stream)
+    _check(lib.bsrht_nystrom_rbf(_dptr(x), n, dim, float(h), k, l, p, seed & (2**64 - 1), _dbl(u), _dbl(lam),
+                                 ctypes.byref(o)), "bsrht_nystrom_rbf")
     return u, lam
 
 

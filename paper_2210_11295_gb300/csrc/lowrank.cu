@@ -831,14 +831,104 @@ __global__ void k_lambda(const double* __restrict__ sig, const double* __restric
   if (c < k) lam[c] = fmax(sig[c] * sig[c] - *nu, 0.0);
 }
 
+// Matrix-free source of Algorithm 2: the kernel matrix
+// A_ij = exp(-|x_i - x_j|^2 / (2 h^2)) of the points x_i (rows of X, n x dim,
+// FP32, row stride ldx), generated a column panel at a time and sketched
+// right away, so the n x n matrix is never stored.
+struct RbfSource {
+  const float* X = nullptr;  // nullptr: A is a stored matrix
+  int64_t dim = 0, ldx = 0;
+  double h = 0.0;
+};
+
+// sq[i] = |x_i|^2, summed in FP64 and rounded to FP32.
+__global__ void k_row_sqnorm(const float* __restrict__ X, int64_t n, int64_t dim, int64_t ldx,
+                             float* __restrict__ sq) {
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t c = threadIdx.x & 31; c < dim; c += 32) {
+    const double v = X[i * ldx + c];
+    s = fma(v, v, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sq[i] = (float)s;
+}
+
+// Panel of columns [j0, j0 + w) in place: G[i][j] = x_i . x_{j0+j} (FP32
+// accuracy) becomes exp(-max(|x_i|^2 + |x_j|^2 - 2 G, 0) / (2 h^2)) in FP32
+// arithmetic (the entries are FP32 values; the FP64 units of this GPU run
+// at 1/64 of the FP32 rate), with the diagonal exactly 1.
+__global__ void k_rbf_panel(float* __restrict__ P, int64_t n, int64_t w, int64_t j0, const float* __restrict__ sq,
+                            float inv2h2) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * w) return;
+  const int64_t i = idx / w, j = idx - i * w;
+  const float d2 = fmaxf(sq[i] + sq[j0 + j] - 2.0f * P[idx], 0.0f);
+  P[idx] = (i == j0 + j) ? 1.0f : expf(-d2 * inv2h2);
+}
+
+// Column-panel width of the matrix-free sketch: about 1 GiB of FP32 panel,
+// a multiple of 64 columns, at most n.
+int64_t rbf_panel_width(int64_t n) {
+  int64_t w = ((int64_t)1 << 28) / std::max<int64_t>(n, 1);
+  w = std::max<int64_t>(64, std::min<int64_t>(8192, w / 64 * 64));
+  return std::min(w, n);
+}
+
+// B (l x n, row stride n) = Omega A for the kernel matrix of src: per panel,
+// the Gram of the points on the tensor cores (3xTF32), the RBF map, and the
+// sketch of the panel into B's columns.
+int rbf_sketch(const Dla& d, Arena& ar, bool dry, const RbfSource& src, int64_t n, int p, int64_t l, int variant,
+               uint64_t seed, float* B, void* sk_ws, size_t sk_bytes) {
+  const int64_t w = rbf_panel_width(n);
+  float* panel = static_cast<float*>(ar.take(sizeof(float) * (size_t)n * w));
+  float* sq = static_cast<float*>(ar.take(sizeof(float) * (size_t)n));
+  if (!ar.ok()) return BSRHT_ENOMEM;
+  if (!dry) {
+    k_row_sqnorm<<<(unsigned)((n + 7) / 8), 256, 0, d.s>>>(src.X, n, src.dim, src.ldx, sq);
+    BSRHT_CUDA_TRY(cudaGetLastError());
+    note_launches(1);
+  }
+  for (int64_t j0 = 0; j0 < n; j0 += w) {
+    const int64_t wj = std::min(w, n - j0);
+    {
+      const size_t mk = ar.mark();
+      const int st = gemm_tc(d, ar, n, wj, src.dim, src.X, src.ldx, DT::F32, src.X + j0 * src.ldx, src.ldx, true,
+                             DT::F32, panel, wj, false);
+      ar.release(mk);
+      if (st != BSRHT_OK) return st;
+    }
+    if (!dry) trace_mark(d.s, "rbf_gram");
+    SketchPlan sp;
+    TRY(sketch_make_plan(sp, BSRHT_F32, variant, n, wj, wj, p, l, !dry, dry ? nullptr : panel));
+    if (sp.work_bytes > sk_bytes) return BSRHT_ENOMEM;
+    if (dry) break;  // every panel but the last has the same plan; the last one is narrower
+    k_rbf_panel<<<(unsigned)((n * wj + 255) / 256), 256, 0, d.s>>>(panel, n, wj, j0, sq,
+                                                                   (float)(0.5 / (src.h * src.h)));
+    BSRHT_CUDA_TRY(cudaGetLastError());
+    note_launches(1);
+    trace_mark(d.s, "rbf_map");
+    TRY(sketch_run(sp, panel, seed, B + j0, n, sk_ws, d.s));
+  }
+  return BSRHT_OK;
+}
+
 int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l, int p, uint64_t seed, double* U,
-                 double* Lam, Arena& ar, bool dry) {
+                 double* Lam, Arena& ar, bool dry, const RbfSource& src = RbfSource()) {
   const DT ta = dt_of(o.dtype);
   const DT tc = (ta == DT::F64) ? DT::F64 : DT::F32;
   const size_t cs = dt_size(tc);
   const int64_t lda = o.lda ? o.lda : n;
   SketchPlan sp_a, sp_y;
-  TRY(sketch_make_plan(sp_a, o.dtype, o.variant, n, n, lda, p, l, !dry, dry ? nullptr : A));
+  const bool rbf = src.X != nullptr;
+  if (rbf) {
+    // The panels' plan (the widest panel) sizes the sketch scratch.
+    const int64_t w = rbf_panel_width(n);
+    TRY(sketch_make_plan(sp_a, BSRHT_F32, o.variant, n, w, w, p, l, !dry, nullptr));
+  } else {
+    TRY(sketch_make_plan(sp_a, o.dtype, o.variant, n, n, lda, p, l, !dry, dry ? nullptr : A));
+  }
   // The l x l core Omega Y_nu is formed in FP64 whatever the type of A, with
   // the FP64-add kernel: the shift nu of Remark 3.1 is a few FP64 units of
   // ||Y||, below the precision of the fixed-point FP64 sketch (an address
@@ -876,7 +966,14 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
     BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
     // Step 1: Y = A Omega^T = (Omega A)^T for symmetric A.
     trace_begin(d.s);
-    TRY(sketch_run(sp_a, A, seed, B, n, sk_ws, d.s));
+    if (rbf) {
+      const size_t mk = ar.mark();
+      TRY(rbf_sketch(d, ar, false, src, n, p, l, o.variant, seed, static_cast<float*>(B), sk_ws,
+                     std::max(sp_a.work_bytes, sp_y.work_bytes)));
+      ar.release(mk);
+    } else {
+      TRY(sketch_run(sp_a, A, seed, B, n, sk_ws, d.s));
+    }
     trace_mark(d.s, "sketch");
     TRY(transpose_cast(d, tc, B, l, n, n, tc, Y, l));
     {
@@ -889,9 +986,15 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
     BSRHT_CUDA_TRY(cudaGetLastError());
     note_launches(1);
   } else {
-    const size_t mk = ar.mark();
+    size_t mk = ar.mark();
     TRY(frob_norm(d, ar, tc, Y, n * l, ynorm));
     ar.release(mk);
+    if (rbf) {
+      mk = ar.mark();
+      TRY(rbf_sketch(d, ar, true, src, n, p, l, o.variant, seed, nullptr, nullptr,
+                     std::max(sp_a.work_bytes, sp_y.work_bytes)));
+      ar.release(mk);
+    }
   }
   // Steps 1b-2 (Remark 3.1): Y_nu = Y + nu Omega^T, core = sym(Omega Y_nu) in
   // FP64 and its Cholesky factor C (C^T C = core).  When the factorization
@@ -1045,6 +1148,19 @@ int validate_nystrom(const bsrht_opts& o, int64_t n, int k, int64_t l, int p) {
   return BSRHT_OK;
 }
 
+int validate_nystrom_rbf(const bsrht_opts& o, const float* X, int64_t n, int64_t dim, double h, int k, int64_t l,
+                         int p) {
+  if (o.dtype != BSRHT_F32) return o.dtype >= BSRHT_F64 && o.dtype <= BSRHT_F16 ? BSRHT_EUNSUP : BSRHT_EINVAL;
+  if (o.variant == BSRHT_VARIANT_GAUSSIAN || o.variant == BSRHT_VARIANT_TENSOR) return BSRHT_EUNSUP;
+  if (dim < 1 || !(h > 0.0) || !std::isfinite(h)) return BSRHT_EINVAL;
+  const int64_t ldx = o.lda ? o.lda : dim;
+  if (ldx < dim) return BSRHT_EINVAL;
+  if ((ldx % 4) != 0 || (reinterpret_cast<uintptr_t>(X) % 16) != 0) return BSRHT_EUNSUP;
+  bsrht_opts on = o;
+  on.lda = 0;  // opts->lda is the stride of X here, not of an n x n matrix
+  return validate_nystrom(on, n, k, l, p);
+}
+
 }  // namespace
 }  // namespace bsrht
 
@@ -1115,6 +1231,46 @@ int bsrht_nystrom_workspace(int64_t n, int32_t k, int64_t l, int32_t p, const bs
   TRY(nystrom_impl(o, nullptr, n, k, l, p, 0, nullptr, nullptr, ar, true));
   *bytes = ar.high + 256;
   return BSRHT_OK;
+}
+
+
+int bsrht_nystrom_rbf_workspace(int64_t n, int64_t dim, int32_t k, int64_t l, int32_t p, const bsrht_opts* opts,
+                                size_t* bytes) {
+  if (!bytes) return BSRHT_EINVAL;
+  bsrht_opts o = opts_or_default(opts);
+  TRY(validate_nystrom_rbf(o, nullptr, n, dim, 1.0, k, l, p));
+  RbfSource src;
+  src.X = reinterpret_cast<const float*>(uintptr_t(256));  // marks the source; never read in a dry run
+  src.dim = dim;
+  src.ldx = o.lda ? o.lda : dim;
+  src.h = 1.0;
+  o.lda = 0;
+  Arena ar;
+  ar.measure = true;
+  TRY(nystrom_impl(o, nullptr, n, k, l, p, 0, nullptr, nullptr, ar, true, src));
+  *bytes = ar.high + 256;
+  return BSRHT_OK;
+}
+
+int bsrht_nystrom_rbf(const float* X, int64_t n, int64_t dim, double h, int32_t k, int64_t l, int32_t p,
+                      uint64_t seed, double* U, double* Lambda, const bsrht_opts* opts) {
+  bsrht_opts o = opts_or_default(opts);
+  if (!X || !U || !Lambda) return BSRHT_EINVAL;
+  TRY(validate_nystrom_rbf(o, X, n, dim, h, k, l, p));
+  size_t need = 0;
+  TRY(bsrht_nystrom_rbf_workspace(n, dim, k, l, p, &o, &need));
+  void* ws = nullptr;
+  TRY(workspace_for(&o, need, &ws));
+  RbfSource src;
+  src.X = X;
+  src.dim = dim;
+  src.ldx = o.lda ? o.lda : dim;
+  src.h = h;
+  o.lda = 0;
+  Arena ar;
+  ar.base = static_cast<char*>(ws);
+  ar.cap = need;
+  return nystrom_impl(o, nullptr, n, k, l, p, seed, U, Lambda, ar, false, src);
 }
 
 int bsrht_nystrom(const void* A, int64_t n, int32_t k, int64_t l, int32_t p, uint64_t seed, double* U,
