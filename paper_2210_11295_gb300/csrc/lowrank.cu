@@ -231,6 +231,9 @@ OrthBufs take_orth_bufs(Arena& ar, int64_t l, size_t cs) {
 // that happens to exist is meaningless).  Such inputs take the Householder /
 // rank-revealing paths instead.
 constexpr double kCholQrPivotMin64 = 0x1.0p-44;
+// The same for products and Grams at FP32 accuracy (u = 2^-24): condition
+// numbers up to about 10^3.
+constexpr double kCholQrPivotMin32 = 0x1.0p-20;
 
 // Orthonormal basis Q (rows x l, type tc) of the tall X, robust to rank
 // deficiency, and R (l x l FP64) with X = Q R when R != nullptr.
@@ -262,9 +265,11 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
   if (!dry) {
     TRY(chol_inv(d, b.G, b.LT1, b.Rinv, b.Ug, b.Vg, l));
     // FP64 data: the squared pivots of the first factor must stay above
-    // kCholQrPivotMin64 of the largest (see there).
+    // kCholQrPivotMin64 of the largest (see there); FP32 data, when the
+    // caller has a fallback (declined), above kCholQrPivotMin32.
     double ratio = 1.0;
-    if (tc == DT::F64) {
+    const double pivot_min = tc == DT::F64 ? kCholQrPivotMin64 : kCholQrPivotMin32;
+    if (tc == DT::F64 || declined) {
       k_pivot_ratio<<<1, 256, 0, d.s>>>(b.G, l, b.ratio);
       BSRHT_CUDA_TRY(cudaGetLastError());
       note_launches(1);
@@ -273,7 +278,7 @@ int orth_robust(const Dla& d, Arena& ar, bool dry, DT tc, void* X, void* Y, void
     int hs = 0;
     TRY(read_status(d, &hs));
     if (hs & kStatusTcWait) return BSRHT_ETIMEDOUT;
-    if (hs || !(ratio > kCholQrPivotMin64)) {
+    if (hs || !(ratio > pivot_min)) {
       fast = false;
       BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
       if (declined) {
@@ -505,12 +510,34 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
   if (!dry) trace_begin(d.s);
   if (!dry) TRY(sketch_run(sp, A, seed, B, m, sk_ws, d.s));
   if (!dry) trace_mark(d.s, "sketch");
-  // Step 2: Q = orth(B^T) in FP64 (X1 = B^T, m x l), rank revealing:
-  // Q is m x lq with lq = dim range(Y) <= l (range_basis).
-  if (!dry) TRY(transpose_cast(d, tc, B, l, m, m, DT::F64, X1, l));
+  // Step 2: Q = orth(B^T) (m x lq, lq = dim range(Y) <= l).  FP32 data:
+  // the second pass reads Q in FP32, so a well-conditioned sketch takes
+  // CholeskyQR2 at FP32 accuracy on the tensor cores (pivot check
+  // kCholQrPivotMin32) and only V = Q U~_k is made orthonormal in FP64 at
+  // the end (an m x k CholeskyQR2).  Otherwise, and for FP64 data: the
+  // rank-revealing FP64 basis (range_basis).
   double* Q = nullptr;
   int64_t lq = l;
-  TRY(range_basis(d, ar, dry, X1, X2, X3, m, l, seed ^ 0x51ull, ob, &Q, &lq));
+  const void* Qa = nullptr;
+  bool q32 = false;
+  if (tc == DT::F32) {
+    float* Y32 = reinterpret_cast<float*>(X2);
+    if (!dry) TRY(transpose_cast(d, DT::F32, B, l, m, m, DT::F32, Y32, l));
+    void* Qv = nullptr;
+    bool declined = false;
+    TRY(orth_robust(d, ar, dry, DT::F32, Y32, X3, Qc, m, l, seed ^ 0x51ull, ob, nullptr, true, false, &Qv, nullptr,
+                    false, &declined));
+    if (!dry && !declined) {
+      TRY(cast_copy(d, DT::F32, Qv, DT::F64, X1, m * l));
+      Q = X1;
+      Qa = Qv;
+      q32 = true;
+    }
+  }
+  if (!q32) {
+    if (!dry) TRY(transpose_cast(d, tc, B, l, m, m, DT::F64, X1, l));
+    TRY(range_basis(d, ar, dry, X1, X2, X3, m, l, seed ^ 0x51ull, ob, &Q, &lq));
+  }
   if (!dry) trace_mark(d.s, "orth_sketch");
   // Below the numerical rank of Y the factors are zero (lq < k).
   const int64_t kk = std::min<int64_t>(k, lq);
@@ -524,10 +551,12 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
     TRY(read_status(d, &hs));
     return status_to_code(hs);
   }
-  const void* Qa = Q;
-  if (tc == DT::F32) {
-    if (!dry) TRY(cast_copy(d, DT::F64, Q, DT::F32, Qc, m * lq));
-    Qa = Qc;
+  if (!q32) {
+    Qa = Q;
+    if (tc == DT::F32) {
+      if (!dry) TRY(cast_copy(d, DT::F64, Q, DT::F32, Qc, m * lq));
+      Qa = Qc;
+    }
   }
   // Step 3: the paper's Z = Q^T A_paper, i.e. Z^T = A Q (n x lq): second pass over A.
   bool w_t = false;  // W1^T left in W3, the Gram scratch of the QR below
@@ -574,6 +603,15 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
   TRY(tall_gemm(d, ar, tc, tc, DT::F64, n, kk, lq, Pv, lq, Vk64, Vk, ldv, U, k, false));
   TRY(gemm64(d, ar, m, kk, lq, Q, lq, false, Us, lq, V, k));
   if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(S, sig, sizeof(double) * kk, cudaMemcpyDeviceToDevice, d.s));
+  // With the FP32-accuracy Q, V is orthonormal to FP32 accuracy: one FP64
+  // CholeskyQR2 of V (m x k, R close to I) makes it orthonormal to FP64
+  // rounding while moving it by about 1e-6, the accuracy of FP32 data.
+  if ((q32 || dry) && kk == k && tc == DT::F32) {
+    void* Vv = nullptr;
+    TRY(orth_robust(d, ar, dry, DT::F64, V, X2, X3, m, k, seed ^ 0x54ull, ob, nullptr, true, false, &Vv));
+    if (!dry && Vv != static_cast<void*>(V))
+      BSRHT_CUDA_TRY(cudaMemcpyAsync(V, Vv, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, d.s));
+  }
   {
     const size_t mk = ar.mark();
     TRY(sign_normalize(d, ar, U, n, k, V, m));
