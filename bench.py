@@ -470,6 +470,41 @@ def f64_sketch_object(lib, a32, p, l, peak, stream):
             "parity": {"columns": cols, "rel_fro_vs_oracle": float(f"{_rel(got, ref):.3e}"), "tol": 1e-12}}
 
 
+def p_sweep_object(lib, a, l, k, peak, stream):
+    """The tall-skinny FP32 workload at p = 1, 4, 16, 64 blocks (the block
+    count of eq. 2.3; r = n / p rows per Walsh-Hadamard transform): sketch
+    call and kernel time with their HBM fraction, and the rank-k Algorithm 1
+    step time, on the same resident A."""
+    import torch
+    n, m = a.shape
+    rows = []
+    for p in (1, 4, 16, 64):
+        out = torch.empty(l, m, device=a.device, dtype=torch.float32)
+        ws = torch.empty(max(lib.bsrht_sketch_workspace(n, m, p, l, a.dtype), 1), dtype=torch.uint8,
+                         device=a.device)
+        run = lambda s: lib.bsrht_sketch(a, p, l, s, out=out, workspace=ws)  # noqa: E731
+        for w in range(3):
+            run(w)
+        call_ms = _events_ms(stream, lambda: run(7), 5)
+        k_ms = _kernel_ms(lib, lambda: run(8), 5) or call_ms
+        rws = torch.empty(max(lib.bsrht_rsvd_workspace(n, m, k, l, p, a.dtype), 1), dtype=torch.uint8,
+                          device=a.device)
+        outs = (torch.empty(n, k, device=a.device, dtype=torch.float64),
+                torch.empty(k, device=a.device, dtype=torch.float64),
+                torch.empty(m, k, device=a.device, dtype=torch.float64))
+        rs = lambda s: lib.bsrht_rsvd(a, k, l, p, s, workspace=rws, outs=outs)  # noqa: E731
+        rs(0)
+        rsvd_ms = _events_ms(stream, lambda: rs(1), 2)
+        nbytes = n * m * 4 + l * m * 4
+        rows.append({"p": p, "sketch_ms": round(call_ms, 4), "kernel_ms": round(k_ms, 4),
+                     "gbs": round(nbytes / (call_ms * 1e-3) / 1e9, 2),
+                     "kernel_frac_of_measured_peak": round(nbytes / (k_ms * 1e-3) / 1e9 / peak, 4),
+                     "rsvd_ms": round(rsvd_ms, 3)})
+        del out, ws, rws, outs
+        torch.cuda.empty_cache()
+    return {"workload": f"tall-skinny lowrank+noise n={n} m={m} fp32 l={l} k={k}, p in 1, 4, 16, 64", "per_p": rows}
+
+
 def config1_object(lib, stream):
     """The small FP64 workload: A = U diag(e^(-i/10)) V^T, n = 4096, m = 256,
     p = 4, l = 128, rank-20 Algorithm 1, against the oracle."""
@@ -826,6 +861,7 @@ def run_ours(args):
     if mode == "full" and default_shape and rank == 0 and not args.no_extras:
         peak_v = peaks()[0]
         _extra("rsvd_error", lambda: rsvd_error_object(lib, a, u, s, v, args), extras)
+        _extra("p_sweep", lambda: p_sweep_object(lib, a, l, k, peak_v, stream), extras)
         _extra("f64", lambda: f64_sketch_object(lib, a, p, l, peak_v, stream), extras)
         _extra("config1_fp64", lambda: config1_object(lib, stream), extras)
         _extra("nystrom", lambda: nystrom_object(lib, peak_v, stream), extras)
