@@ -281,9 +281,10 @@ TRAFFIC_RECORDS = {
     # FP32: the reads are A itself; the writes are the per-(CTA, panel)
     # partial sums, written once (they do not grow with n).
     ("f32", 1 << 20, 4096, 4, 512): {
-        "kernel": "k_sketch_tma", "read_n2e18": 4295588608, "write_n2e18": 11199744, "write_scales": False,
-        "sources": ("paper_2210_11295_gb300/csrc/sketch_tma.cu", "paper_2210_11295_gb300/csrc/tma.cuh"),
-        "sha256": "6d8bc313d6c64fa2da716ee63d46283bfd08cc39c2096305f0cd33a56bd0e97d"},
+        "kernel": "k_sketch_tma", "read_n2e18": 4295590912, "write_n2e18": 11194624, "write_scales": False,
+        "sources": ("paper_2210_11295_gb300/csrc/sketch_tma.cu", "paper_2210_11295_gb300/csrc/tma.cuh",
+                    "paper_2210_11295_gb300/csrc/f32x2.cuh"),
+        "sha256": "1cd039aecde03d8f4d0c8565b5c31d1b7d4873893bbffec7c79c90b7910bd8f6"},
     # FP64: besides A, the read-modify-write of the FP64 partial sums at
     # every flush of the integer sums (one per 32 chunks of a CTA), which
     # grows with n like the reads.

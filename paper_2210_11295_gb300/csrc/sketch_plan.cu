@@ -247,7 +247,8 @@ static int make_plan_choice(SketchPlan& pl, int dtype, int64_t n, int64_t m, int
   // take the TMA-fed kernel (FP64: the one with the integer transform)
   // unless a chunked instance was chosen; the plain kernel stays the
   // fallback, so a plan made without A reserves scratch for both.
-  const bool tma_ok = pl.r >= 512 && tma_layout_ok(dtype, A, lda);
+  // (The TMA kernels count a panel's chunks in 32 bits.)
+  const bool tma_ok = pl.r >= 512 && tma_layout_ok(dtype, A, lda) && (int64_t)p * ((pl.rb + 511) / 512) < INT32_MAX;
   if (choice == -1 && !(tma_ok || (A == nullptr && pl.r >= 512 && tma_layout_ok(dtype, nullptr, lda))))
     return BSRHT_EINVAL;
   if (tma_ok && choice < 0) {
