@@ -575,8 +575,10 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// One-sided (Hestenes) Jacobi on the columns of M with round-robin pairs;
-// one block of WP warps per column pair, a grid-wide barrier between rounds.
+// One-sided (Hestenes) Jacobi on the l columns (each of `rows` entries,
+// stored contiguously) of M with round-robin pairs, the same rotations
+// applied to the columns of V (also `rows` entries each); one block of WP
+// warps per column pair, a grid-wide barrier between rounds.
 // Warp w of the block holds rows w*32*JR .. (w+1)*32*JR-1 of the two columns
 // of M and of V in registers (JR values per lane), the block sums the
 // partial inner products in shared memory, every warp derives the rotation
@@ -625,7 +627,7 @@ __device__ __forceinline__ double jac_tangent(double alpha, double beta, double 
 
 template <typename T, int JR, int WP>
 __global__ void __launch_bounds__(32 * WP) k_jacobi(T* __restrict__ M, T* __restrict__ V, T* __restrict__ nrm,
-                                                    int l, int lp, double tol, double tol_stop,
+                                                    int l, int lp, int rows, double tol, double tol_stop,
                                                     const double* __restrict__ fnorm, double tiny_rel,
                                                     int max_sweeps, int* __restrict__ rot_counts,
                                                     int* __restrict__ status) {
@@ -641,9 +643,9 @@ __global__ void __launch_bounds__(32 * WP) k_jacobi(T* __restrict__ M, T* __rest
   int sweep = 0, it = 0;
   for (; sweep < max_sweeps; ++sweep) {
     for (int c = gwarp; c < l; c += nwarps) {
-      const T* __restrict__ col = M + (int64_t)c * l;
+      const T* __restrict__ col = M + (int64_t)c * rows;
       T sq = 0;
-      for (int r = lane; r < l; r += 32) sq = fma(col[r], col[r], sq);
+      for (int r = lane; r < rows; r += 32) sq = fma(col[r], col[r], sq);
       sq = warp_sum(sq);
       if (lane == 0) nrm[c] = sq;
     }
@@ -657,15 +659,15 @@ __global__ void __launch_bounds__(32 * WP) k_jacobi(T* __restrict__ M, T* __rest
           q = t;
         }
         if (q >= l) continue;  // padding column (block-uniform)
-        T* __restrict__ a = M + (int64_t)p * l;
-        T* __restrict__ b = M + (int64_t)q * l;
-        T* __restrict__ va = V + (int64_t)p * l;
-        T* __restrict__ vb = V + (int64_t)q * l;
+        T* __restrict__ a = M + (int64_t)p * rows;
+        T* __restrict__ b = M + (int64_t)q * rows;
+        T* __restrict__ va = V + (int64_t)p * rows;
+        T* __restrict__ vb = V + (int64_t)q * rows;
         T x[JR], y[JR], vx[JR], vy[JR];
 #pragma unroll
         for (int e = 0; e < JR; ++e) {
           const int r = row0 + 32 * e;
-          const bool in = r < l;
+          const bool in = r < rows;
           x[e] = in ? a[r] : (T)0;
           y[e] = in ? b[r] : (T)0;
           vx[e] = in ? va[r] : (T)0;
@@ -707,7 +709,7 @@ __global__ void __launch_bounds__(32 * WP) k_jacobi(T* __restrict__ M, T* __rest
 #pragma unroll
         for (int e = 0; e < JR; ++e) {
           const int r = row0 + 32 * e;
-          if (r < l) {
+          if (r < rows) {
             a[r] = c * x[e] - s * y[e];
             b[r] = s * x[e] + c * y[e];
             va[r] = c * vx[e] - s * vy[e];
@@ -780,6 +782,79 @@ __global__ void k_svd_finish(const double* __restrict__ M, const double* __restr
 // The mixed-precision path (FP32 Jacobi, FP64 polish) above this order.
 constexpr int64_t kJacobiMixedMin = 64;
 
+// sigma[c] = ||column c||_2 (FP64 sums) of the ncols columns of `rows`
+// entries stored contiguously in M.
+template <typename T>
+__global__ void k_col_norms_t(const T* __restrict__ M, double* __restrict__ sigma, int64_t ncols, int64_t rows) {
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (c >= ncols) return;
+  double sq = 0.0;
+  for (int64_t i = lane; i < rows; i += 32) {
+    const double v = (double)M[c * rows + i];
+    sq = fma(v, v, sq);
+  }
+  sq = warp_sum(sq);
+  if (lane == 0) sigma[c] = sqrt(sq);
+}
+
+// Vr[i][r] = V32 column perm[r], entry i (row-major l x s, FP64).
+__global__ void k_gather_cols_t(const float* __restrict__ V32, const int* __restrict__ perm, int64_t l, int64_t s,
+                                double* __restrict__ Vr) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= l * s) return;
+  const int64_t i = idx / s, r = idx - i * s;
+  Vr[idx] = (double)V32[(int64_t)perm[r] * l + i];
+}
+
+// Outputs of the partly polished SVD: ranks r < s from the s polished
+// columns (Ysc, Vsc in column storage of l entries, norms sigS, ranks
+// permS), ranks r >= s from the FP32 phase (M32, V32, norms sig, ranks
+// perm, whose first s entries are the columns that were polished).
+__global__ void k_svd_finish_part(const double* __restrict__ Ysc, const double* __restrict__ Vsc,
+                                  const double* __restrict__ sigS, const int* __restrict__ permS, int64_t s,
+                                  const float* __restrict__ M32, const float* __restrict__ V32,
+                                  const double* __restrict__ sig, const int* __restrict__ perm, int64_t l,
+                                  double* __restrict__ U, double* __restrict__ Vout, double* __restrict__ sig_out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= l * l) return;
+  const int64_t i = idx / l, r = idx - i * l;
+  double u, v, sv;
+  if (r < s) {
+    const int64_t c = permS[r];
+    sv = sigS[c];
+    u = sv > 0.0 ? Ysc[c * l + i] / sv : 0.0;
+    v = Vsc[c * l + i];
+  } else {
+    const int64_t c = perm[r];
+    sv = sig[c];
+    u = sv > 0.0 ? (double)M32[c * l + i] / sv : 0.0;
+    v = (double)V32[c * l + i];
+  }
+  U[idx] = u;
+  Vout[idx] = v;
+  if (i == 0) sig_out[r] = sv;
+}
+
+// *flag = 1 when some pair i < j of the columns whose Gram is G (n x n,
+// FP64) has |G_ij| > tol sqrt(G_ii G_jj), pairs whose squared norms are both
+// at most (tiny_rel ||M||_F)^2 left out: the test by which a further Jacobi
+// sweep would rotate a pair (k_jacobi, tol_stop).
+__global__ void k_offdiag_exceeds(const double* __restrict__ G, int64_t n, const double* __restrict__ fnorm,
+                                  double tiny_rel, double tol, int* __restrict__ flag) {
+  const double tiny = tiny_rel * fnorm[0], tiny2 = tiny * tiny, tol2 = tol * tol;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / n, j = idx - i * n;
+    if (i >= j) continue;
+    const double a = G[i * n + i], b = G[j * n + j], g = G[idx];
+    if (a <= tiny2 && b <= tiny2) continue;
+    if (g * g > tol2 * a * b) *flag = 1;
+  }
+}
+
+__global__ void k_or_status(int* __restrict__ status, int v) { atomicOr(status, v); }
+
 __global__ void k_ns_coeff(double* __restrict__ G, int64_t l) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < l * l) G[idx] = (idx / l == idx % l ? 1.5 : 0.0) - 0.5 * G[idx];
@@ -793,12 +868,12 @@ namespace {
 // lane); four for FP32 at l >= 512 and two below, where a round is
 // latency-bound and shorter per-warp chains help.
 template <typename T, int WP>
-int launch_jacobi_wp(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, double tol, double tol_stop,
+int launch_jacobi_wp(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, int64_t rows, double tol, double tol_stop,
                      const double* fnorm, double tiny_rel, int max_sweeps, int* rot, int* status) {
-  int li = (int)l, lp = (int)(l + (l & 1)), msw = max_sweeps;
+  int li = (int)l, lp = (int)(l + (l & 1)), ri = (int)rows, msw = max_sweeps;
   const int threads = 32 * WP;
   const int pairs = lp / 2;
-  void* args[] = {&cols, &Vc, &nrm, &li, &lp, &tol, &tol_stop, &fnorm, &tiny_rel, &msw, &rot, &status};
+  void* args[] = {&cols, &Vc, &nrm, &li, &lp, &ri, &tol, &tol_stop, &fnorm, &tiny_rel, &msw, &rot, &status};
   auto launch = [&](auto kern) -> int {
     int occ = 0;
     BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0));
@@ -809,7 +884,7 @@ int launch_jacobi_wp(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, double tol
     return BSRHT_OK;
   };
   if (l <= 1) return BSRHT_OK;
-  const int64_t per = (l + 32 * WP - 1) / (32 * WP);  // values per lane and column
+  const int64_t per = (rows + 32 * WP - 1) / (32 * WP);  // values per lane and column
   if (per <= 1) return launch(k_jacobi<T, 1, WP>);
   if (per <= 2) return launch(k_jacobi<T, 2, WP>);
   if (per <= 4) return launch(k_jacobi<T, 4, WP>);
@@ -821,17 +896,22 @@ int launch_jacobi_wp(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, double tol
   return BSRHT_EUNSUP;
 }
 
+// l columns of `rows` entries each (rows = l for a square matrix).
 template <typename T>
-int launch_jacobi(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, double tol, double tol_stop, const double* fnorm,
-                  double tiny_rel, int max_sweeps, int* rot, int* status) {
+int launch_jacobi(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, int64_t rows, double tol, double tol_stop,
+                  const double* fnorm, double tiny_rel, int max_sweeps, int* rot, int* status) {
   if constexpr (sizeof(T) == 8) {
-    if (l <= 1024)
-      return launch_jacobi_wp<T, 2>(d, cols, Vc, nrm, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot, status);
-    return launch_jacobi_wp<T, 4>(d, cols, Vc, nrm, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot, status);
-  } else if (l >= 512)
-    return launch_jacobi_wp<T, 4>(d, cols, Vc, nrm, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot, status);
+    if (rows <= 1024)
+      return launch_jacobi_wp<T, 2>(d, cols, Vc, nrm, l, rows, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot,
+                                    status);
+    return launch_jacobi_wp<T, 4>(d, cols, Vc, nrm, l, rows, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot,
+                                  status);
+  } else if (rows >= 512)
+    return launch_jacobi_wp<T, 4>(d, cols, Vc, nrm, l, rows, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot,
+                                  status);
   else
-    return launch_jacobi_wp<T, 2>(d, cols, Vc, nrm, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot, status);
+    return launch_jacobi_wp<T, 2>(d, cols, Vc, nrm, l, rows, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot,
+                                  status);
 }
 
 // Block one-sided Jacobi (FP32 phase of the mixed SVD).  The columns are cut
@@ -1050,13 +1130,21 @@ int launch_jacobi_blk(const Dla& d, float* M, float* V, int64_t l, double tol, d
 }  // namespace
 
 int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout,
-               double polish_tol, double zero_rel) {
+               double polish_tol, double zero_rel, int64_t ktop) {
   if (l > 2048) return BSRHT_EUNSUP;
   const int max_sweeps = 40;
   // Rotate only while the cosine of the pair exceeds sqrt(l) eps (the usual
   // one-sided Jacobi threshold); a tighter one keeps rotating at noise level.
   const double tol = polish_tol > 0.0 ? polish_tol : std::max(1e-15, std::sqrt((double)l) * 0x1.0p-52);
   const bool mixed = l > kJacobiMixedMin;
+  // Callers at FP32-data accuracy that use only the leading ktop triplets
+  // polish the s leading columns of the FP32 phase (a margin of
+  // max(16, ktop / 4) beyond ktop) and keep the FP32 phase's estimates for
+  // the rest.
+  const int64_t s = (mixed && polish_tol > 0.0 && ktop > 0)
+                        ? std::min<int64_t>(l, ktop + std::max<int64_t>(16, ktop / 4))
+                        : l;
+  const bool part = s < l;
   double* Vc = static_cast<double*>(ar.take(sizeof(double) * l * l));
   double* sig = static_cast<double*>(ar.take(sizeof(double) * l));
   int* perm = static_cast<int*>(ar.take(sizeof(int) * l));
@@ -1064,6 +1152,11 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
   double* fnorm = static_cast<double*>(ar.take(sizeof(double)));
   double* nrm64 = static_cast<double*>(ar.take(sizeof(double) * l));
   float* nrm32 = static_cast<float*>(ar.take(sizeof(float) * l));
+  double* Yt = static_cast<double*>(ar.take(sizeof(double) * l * l));  // convergence test: columns, row-major
+  double* Gc = static_cast<double*>(ar.take(sizeof(double) * l * l));  // and their Gram
+  int* cflag = static_cast<int*>(ar.take(sizeof(int)));
+  double* sigS = static_cast<double*>(ar.take(sizeof(double) * l));
+  int* permS = static_cast<int*>(ar.take(sizeof(int) * l));
   float *M32 = nullptr, *V32 = nullptr;
   double *S2 = nullptr, *G = nullptr, *Y = nullptr;
   if (mixed) {
@@ -1074,13 +1167,17 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
     Y = static_cast<double*>(ar.take(sizeof(double) * l * l));
   }
   if (!ar.ok()) return BSRHT_ENOMEM;
-  // The l x l products below release their split-K scratch after use.
-  auto gemm64 = [&](const double* A, bool a_trans, const double* B, double* C, bool gram) -> int {
+  // FP64 products (row-major operands); each releases its split-K scratch.
+  auto gemm_f64 = [&](int64_t Mm, int64_t Nn, int64_t Kk, const double* A, int64_t lda, bool a_trans,
+                      const double* B, int64_t ldb, double* C, int64_t ldc, bool gram) -> int {
     const size_t mk = ar.mark();
-    const int st = gemm(d, ar, DT::F64, DT::F64, DT::F64, true, l, l, l, A, l, a_trans, B, l, C, l, 1.0, 0.0,
-                        false, gram);
+    const int st = gemm(d, ar, DT::F64, DT::F64, DT::F64, true, Mm, Nn, Kk, A, lda, a_trans, B, ldb, C, ldc, 1.0,
+                        0.0, false, gram);
     ar.release(mk);
     return st;
+  };
+  auto gemm64 = [&](const double* A, bool a_trans, const double* B, double* C, bool gram) -> int {
+    return gemm_f64(l, l, l, A, l, a_trans, B, l, C, l, gram);
   };
   {
     const size_t mk = ar.mark();
@@ -1088,14 +1185,63 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
     ar.release(mk);
     if (st != BSRHT_OK) return st;
   }
-  if (ar.measure) {
+  if (ar.measure) {  // every product below
+    TRY_DLA(gemm_f64(s, s, l, nullptr, s, true, nullptr, s, nullptr, s, true));
     if (mixed) {
       TRY_DLA(gemm64(nullptr, true, nullptr, nullptr, true));
       TRY_DLA(gemm64(nullptr, false, nullptr, nullptr, false));
     }
+    if (part) {
+      TRY_DLA(gemm_f64(l, s, s, nullptr, s, false, nullptr, s, nullptr, s, false));
+      TRY_DLA(gemm_f64(l, s, l, nullptr, l, true, nullptr, s, nullptr, s, false));
+    }
     return BSRHT_OK;
   }
   BSRHT_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(int) * 2 * max_sweeps, d.s));
+
+  // FP64 one-sided Jacobi of nc columns of `rows` entries (pc, the same
+  // rotations on pv), one sweep per launch.  A sweep without a significant
+  // rotation ends it.  After a sweep that rotated at most 1/16 of the pairs,
+  // the cosines of all pairs come from the Gram of the columns (one FP64
+  // product) instead of a further sweep, and the sweeps stop once none
+  // exceeds the stopping threshold 16 tol: the test that sweep would make
+  // pair by pair.  (Clustered singular values keep the rotation angles
+  // large while the cosines shrink, so the last rotating sweep is not known
+  // in advance.)
+  auto polish = [&](double* pc, double* pv, int64_t nc, int64_t rows) -> int {
+    const double tiny_rel = std::max((double)l * 0x1.0p-53, zero_rel);
+    const unsigned cblocks = (unsigned)std::min<int64_t>(blocks_for(nc * nc, 256), 4096);
+    bool converged = false;
+    for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
+      TRY_DLA(launch_jacobi<double>(d, pc, pv, nrm64, nc, rows, tol, 16.0 * tol, fnorm, tiny_rel, 1, rot + sw,
+                                    nullptr));
+      int cnt = 0;
+      BSRHT_CUDA_TRY(cudaMemcpyAsync(&cnt, rot + sw, sizeof(int), cudaMemcpyDeviceToHost, d.s));
+      BSRHT_CUDA_TRY(cudaStreamSynchronize(d.s));
+      if (cnt == 0) {
+        converged = true;
+        break;
+      }
+      if ((int64_t)cnt * 16 > nc * (nc - 1) / 2) continue;
+      TRY_DLA(transpose_cast(d, DT::F64, pc, nc, rows, rows, DT::F64, Yt, nc));  // rows x nc
+      TRY_DLA(gemm_f64(nc, nc, rows, Yt, nc, true, Yt, nc, Gc, nc, true));
+      BSRHT_CUDA_TRY(cudaMemsetAsync(cflag, 0, sizeof(int), d.s));
+      k_offdiag_exceeds<<<cblocks, 256, 0, d.s>>>(Gc, nc, fnorm, tiny_rel, 16.0 * tol, cflag);
+      DLA_LAUNCH_CHECK();
+      note_launches(1);
+      int h = 1;
+      BSRHT_CUDA_TRY(cudaMemcpyAsync(&h, cflag, sizeof(int), cudaMemcpyDeviceToHost, d.s));
+      BSRHT_CUDA_TRY(cudaStreamSynchronize(d.s));
+      converged = h == 0;
+    }
+    if (!converged) {
+      k_or_status<<<1, 1, 0, d.s>>>(d.status, kStatusNoConv);
+      DLA_LAUNCH_CHECK();
+      note_launches(1);
+    }
+    return BSRHT_OK;
+  };
+
   double* cols = colsM;
   if (mixed) {
     // 1. FP32 one-sided Jacobi on a copy of M: V32 ~ the right singular
@@ -1107,14 +1253,57 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
     const double tol32 = 16.0 * std::sqrt((double)l) * 0x1.0p-24;
     const int bst = launch_jacobi_blk(d, M32, V32, l, tol32, tol32, fnorm, (double)l * 0x1.0p-24, 20, rot + max_sweeps);
     if (bst == BSRHT_EUNSUP)
-      TRY_DLA(launch_jacobi<float>(d, M32, V32, nrm32, l, tol32, tol32, fnorm, (double)l * 0x1.0p-24, 20,
+      TRY_DLA(launch_jacobi<float>(d, M32, V32, nrm32, l, l, tol32, tol32, fnorm, (double)l * 0x1.0p-24, 20,
                                    rot + max_sweeps, nullptr));
     else if (bst != BSRHT_OK)
       return bst;
     trace_mark(d.s, "svd_jacobi_fp32");
+    if (part) {
+      // 2'. The s leading columns by the FP32 norms: their V32 columns made
+      //     orthonormal in FP64 (Vr, l x s row-major: two Newton-Schulz
+      //     steps Vr <- Vr (1.5 I - 0.5 Vr^T Vr)), Y_S = M Vr, then the FP64
+      //     Jacobi on the s columns of Y_S.  In exact arithmetic this is the
+      //     SVD of M restricted to span(Vr) (Rayleigh-Ritz); it differs from
+      //     the leading triplets of M by terms of second order in the FP32
+      //     phase's residual cosines between the s columns and the rest.
+      k_col_norms_t<float><<<blocks_for(l, 8), 256, 0, d.s>>>(M32, sig, l, l);
+      DLA_LAUNCH_CHECK();
+      k_rank_desc<<<blocks_for(l, 256), 256, 0, d.s>>>(sig, perm, l);
+      DLA_LAUNCH_CHECK();
+      double* Vr = S2;
+      double* Vn = Vc;
+      k_gather_cols_t<<<blocks_for(l * s, 256), 256, 0, d.s>>>(V32, perm, l, s, Vr);
+      DLA_LAUNCH_CHECK();
+      note_launches(3);
+      for (int it = 0; it < 2; ++it) {
+        TRY_DLA(gemm_f64(s, s, l, Vr, s, true, Vr, s, G, s, true));  // G = Vr^T Vr
+        k_ns_coeff<<<blocks_for(s * s, 256), 256, 0, d.s>>>(G, s);   // G <- 1.5 I - 0.5 G
+        DLA_LAUNCH_CHECK();
+        note_launches(1);
+        TRY_DLA(gemm_f64(l, s, s, Vr, s, false, G, s, Vn, s, false));
+        std::swap(Vr, Vn);
+      }
+      TRY_DLA(gemm_f64(l, s, l, colsM, l, true, Vr, s, Y, s, false));  // Y_S = M Vr (colsM row-major is M^T)
+      double* Ysc = colsM;                                               // column storage: s x l
+      double* Vsc = G;
+      TRY_DLA(transpose_cast(d, DT::F64, Y, l, s, s, DT::F64, Ysc, l));
+      TRY_DLA(transpose_cast(d, DT::F64, Vr, l, s, s, DT::F64, Vsc, l));
+      trace_mark(d.s, "svd_orthogonalize");
+      TRY_DLA(polish(Ysc, Vsc, s, l));
+      k_col_norms_t<double><<<blocks_for(s, 8), 256, 0, d.s>>>(Ysc, sigS, s, l);
+      DLA_LAUNCH_CHECK();
+      k_rank_desc<<<blocks_for(s, 256), 256, 0, d.s>>>(sigS, permS, s);
+      DLA_LAUNCH_CHECK();
+      k_svd_finish_part<<<blocks_for(l * l, 256), 256, 0, d.s>>>(Ysc, Vsc, sigS, permS, s, M32, V32, sig, perm, l,
+                                                                  U, Vout, sigma);
+      DLA_LAUNCH_CHECK();
+      note_launches(3);
+      return BSRHT_OK;
+    }
     // 2. Make it orthogonal in FP64: with S = V0^T (the column storage),
     //    two Newton-Schulz steps S <- 1.5 S - 0.5 S (S^T S) take the
-    //    orthogonality error from ~1e-6 to rounding level.
+    //    orthogonality error from that of the accumulated FP32 rotations
+    //    to rounding level.
     TRY_DLA(cast_copy(d, DT::F32, V32, DT::F64, Vc, l * l));
     for (int it = 0; it < 2; ++it) {
       TRY_DLA(gemm64(Vc, true, Vc, G, true));  // G = S^T S
@@ -1135,9 +1324,7 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
     DLA_LAUNCH_CHECK();
   }
   // 4. FP64 one-sided Jacobi (from V0 it converges in a few sweeps).
-  TRY_DLA(launch_jacobi<double>(d, cols, Vc, nrm64, l, tol, 16.0 * tol, fnorm,
-                                std::max((double)l * 0x1.0p-53, zero_rel), max_sweeps,
-                                rot, d.status));
+  TRY_DLA(polish(cols, Vc, l, l));
   k_col_norms<<<blocks_for(l, 8), 256, 0, d.s>>>(cols, sig, l);
   DLA_LAUNCH_CHECK();
   k_rank_desc<<<blocks_for(l, 256), 256, 0, d.s>>>(sig, perm, l);

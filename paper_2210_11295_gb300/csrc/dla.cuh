@@ -72,9 +72,8 @@ int tri_inverse(const Dla& d, const double* L, double* LT, double* Rinv, int64_t
 int chol_inv(const Dla& d, double* g, double* LT, double* Rinv, double* T, double* X, int64_t l);
 
 // One-sided Jacobi SVD of the l x l FP64 matrix given by its COLUMNS:
-// colsM[c*l + i] = M[i][c].  On return colsM holds U Sigma (columns),
-// colsV[c*l + i] = V[i][c]; sigma[c] = ||U Sigma e_c||.  Columns are sorted
-// by descending sigma into U (l x l row-major, U[i][c]) and Vout (row-major).
+// colsM[c*l + i] = M[i][c].  The singular triplets, sorted by descending
+// sigma, go to U (l x l row-major, U[i][c]), sigma and Vout (row-major).
 // polish_tol > 0 replaces the FP64 rotation threshold sqrt(l) 2^-52 on the
 // cosine of a pair: Vout (accumulated rotations) stays orthogonal to FP64
 // rounding whatever the threshold, the columns of U to about polish_tol.
@@ -83,8 +82,15 @@ int chol_inv(const Dla& d, double* g, double* LT, double* Rinv, double* T, doubl
 // a caller that drops directions below a rank threshold passes it here, so
 // that columns made of rounding noise at that level do not keep the sweeps
 // going.
+// ktop > 0 with polish_tol > 0 (a caller at FP32-data accuracy that uses
+// only the leading ktop triplets, l > 64): only the s = min(l, ktop +
+// max(16, ktop / 4)) leading columns of the FP32 phase are polished in FP64
+// (the SVD of M restricted to their span, which differs from the leading
+// triplets of M in second order of the FP32 phase's residual cosines);
+// ranks s and beyond hold the FP32 phase's estimates.  colsM is overwritten
+// in every case.
 int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout,
-               double polish_tol = 0.0, double zero_rel = 0.0);
+               double polish_tol = 0.0, double zero_rel = 0.0, int64_t ktop = 0);
 
 // Tensor-core (tcgen05) GEMM in FP32 accuracy (three TF32 products):
 // C (M x N, FP32 or FP64 in tc_out, ldc) = A (M x K, FP32, lda) * B, with B

@@ -579,7 +579,7 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
     const size_t mk = ar.mark();
     if (tc == DT::F32) {
       if (!dry) TRY(transpose_lower_to_upper(d, R, RT, lq));
-      TRY(jacobi_svd(d, ar, RT, lq, Vs, sig, Us, polish_tol_fp32(lq)));
+      TRY(jacobi_svd(d, ar, RT, lq, Vs, sig, Us, polish_tol_fp32(lq), 0.0, k));
     } else {
       TRY(jacobi_svd(d, ar, R, lq, Us, sig, Vs));
     }
@@ -779,12 +779,20 @@ int srsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, 
   if (!dry && L != rp) BSRHT_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * L * L, d.s));
   TRY(gemm64(d, ar, rq, rp, rp, T2, rp, false, Gi2, rp, C, L));
   if (!dry) trace_mark(d.s, "core");
-  // Step 5: SVD of C (Jacobi on its columns, the rows of C^T); the zero
-  // frame leaves the nonzero singular triplets unchanged.
-  if (!dry) TRY(transpose_lower_to_upper(d, C, CT, L));
+  // Step 5: SVD of C = U~ Sigma~ V~^T; the zero frame leaves the nonzero
+  // singular triplets unchanged.  FP64 data: Jacobi on the columns of C (the
+  // rows of C^T).  FP32 data: Jacobi on the columns of C^T (C's row-major
+  // storage), polished to FP32-data accuracy on the k leading triplets, so
+  // that the accumulated rotations, orthogonal to FP64 rounding, give U~,
+  // which multiplies the FP64 basis Q below; the other factor meets P.
   {
     const size_t mk = ar.mark();
-    TRY(jacobi_svd(d, ar, CT, L, Uc, sig, Vc));
+    if (tc == DT::F32) {
+      TRY(jacobi_svd(d, ar, C, L, Vc, sig, Uc, polish_tol_fp32(L), 0.0, k));
+    } else {
+      if (!dry) TRY(transpose_lower_to_upper(d, C, CT, L));
+      TRY(jacobi_svd(d, ar, CT, L, Uc, sig, Vc));
+    }
     ar.release(mk);
   }
   if (!dry) trace_mark(d.s, "small_svd");
@@ -1130,7 +1138,8 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
   }
   {
     const size_t mk = ar.mark();
-    TRY(jacobi_svd(d, ar, RT, lr, Us, sig, Vs, tc == DT::F32 ? polish_tol_fp32(lr) : 0.0));
+    TRY(jacobi_svd(d, ar, RT, lr, Us, sig, Vs, tc == DT::F32 ? polish_tol_fp32(lr) : 0.0, 0.0,
+                   tc == DT::F32 ? k : 0));
     ar.release(mk);
   }
   if (!dry) trace_mark(d.s, "small_svd");
