@@ -60,6 +60,11 @@ def parse_args():
     ap.add_argument("--serve-compare", type=int, default=120,
                     help="requests of the reduced stream timed on both the served path and the plain "
                          "FP64 one-at-a-time path (serve mode)")
+    ap.add_argument("--serve-points", default="0.5,0.8,1.0",
+                    help="serve mode: loads (fractions of the saturation throughput) of the Poisson runs")
+    ap.add_argument("--serve-sat-requests", type=int, default=0,
+                    help="serve mode: measure the saturation throughput on this many leading requests "
+                         "(0: the whole stream)")
     ap.add_argument("--serve-window", type=int, default=96,
                     help="most requests in flight at once (client side, serve mode)")
     ap.add_argument("--variant", choices=["auto", "cudacore", "tensor", "gaussian"], default="auto",
@@ -1135,13 +1140,15 @@ def run_serve(args):
     dtypes = [torch.bfloat16 if rng.random() < 0.5 and r["kind"] != "nystrom" else torch.float32 for r in reqs]
     inputs = _ServeInputs()
     kw = dict(hbm_budget=24 << 30, executors=4, max_group=16)
-    bytes_a = sum(r["n"] * r["m"] * (2 if dt == torch.bfloat16 else 4) for r, dt in zip(reqs, dtypes))
-    # Warm-up pass (graphs, tuning, allocator) on the first requests, then saturation.
+    # Warm-up pass (graphs, tuning, allocator) on the first requests, then
+    # saturation (on the whole stream, or on its leading requests).
     _serve_run(lib, inputs, reqs[: min(60, len(reqs))], dtypes, math.inf, args.serve_window, **kw)
-    sat_s, lat_sat, st_sat, _ = _serve_run(lib, inputs, reqs, dtypes, math.inf, args.serve_window, **kw)
-    x_sat = len(reqs) / sat_s
+    n_sat = len(reqs) if args.serve_sat_requests <= 0 else min(len(reqs), args.serve_sat_requests)
+    sat_s, lat_sat, st_sat, _ = _serve_run(lib, inputs, reqs[:n_sat], dtypes[:n_sat], math.inf, args.serve_window,
+                                           **kw)
+    x_sat = n_sat / sat_s
     points = []
-    for frac in (0.5, 0.8, 1.0):
+    for frac in (float(f) for f in args.serve_points.split(",") if f.strip()):
         ms, lat, st, _ = _serve_run(lib, inputs, reqs, dtypes, frac * x_sat, args.serve_window, **kw)
         points.append({"load": frac, "rate_req_s": round(frac * x_sat, 2), "makespan_s": round(ms, 3),
                        "throughput_req_s": round(len(reqs) / ms, 2), "p50_ms": round(_pct(lat, 50), 3),
@@ -1167,8 +1174,9 @@ def run_serve(args):
                                "k=l//4, FP32 or BF16 (Nystrom: n<=2^15, FP32 PSD)",
                    "executors": kw["executors"], "max_group": kw["max_group"], "hbm_budget": kw["hbm_budget"],
                    "window": args.serve_window, "input_gb": round(inputs.bytes() / 1e9, 2)},
-        "saturation": {"makespan_s": round(sat_s, 3), "throughput_req_s": round(x_sat, 2),
-                       "a_gb_per_s": round(bytes_a / sat_s / 1e9, 2), "p50_ms": round(_pct(lat_sat, 50), 3),
+        "saturation": {"requests": n_sat, "makespan_s": round(sat_s, 3), "throughput_req_s": round(x_sat, 2),
+                       "a_gb_per_s": round(sum(r["n"] * r["m"] * (2 if dt == torch.bfloat16 else 4)
+                                               for r, dt in zip(reqs[:n_sat], dtypes[:n_sat])) / sat_s / 1e9, 2), "p50_ms": round(_pct(lat_sat, 50), 3),
                        "p99_ms": round(_pct(lat_sat, 99), 3), "grouped_launches": st_sat["grouped_launches"],
                        "grouped_requests": st_sat["grouped_requests"], "graph_launches": st_sat["graph_launches"],
                        "tuned_classes": st_sat["tuned_classes"]},

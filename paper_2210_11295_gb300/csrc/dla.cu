@@ -10,6 +10,7 @@
 #include "trace.cuh"
 #include "gemm.cuh"
 #include "sketch.cuh"
+#include "f32x2.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -925,7 +926,7 @@ int launch_jacobi(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, int64_t rows,
 // rotated exactly once, as in the scalar kernel, with the same rotation and
 // stopping rules.  Column norms are formed exactly when a block pair is
 // loaded and carried through the rotations in between.
-template <int B, int JR>
+template <int B, int JR, bool VEC>
 __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, float* __restrict__ V, int l, int nblk,
                                                        double tol, double tol_stop, const double* __restrict__ fnorm,
                                                        double tiny_rel, int max_sweeps,
@@ -1008,7 +1009,64 @@ __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, fl
         float* vb = Vs + (size_t)q * l;
         const float alpha = nrm[p], beta = nrm[q];
         bool skip = gp >= l || gq >= l || (alpha <= tiny2 && beta <= tiny2);
-        if (!skip) {
+        if (!skip && VEC) {
+          // l % 4 == 0: the lane holds rows 128 e + 4 lane + j (j < 4) of the
+          // two columns of M and V, moved with 16-byte shared-memory accesses,
+          // and rotates them as packed pairs (rows j = 0, 1 and 2, 3).
+          constexpr int JQ = JR / 4;
+          const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(a);
+          const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(b);
+          const ulonglong2* va2 = reinterpret_cast<const ulonglong2*>(va);
+          const ulonglong2* vb2 = reinterpret_cast<const ulonglong2*>(vb);
+          ulonglong2 x[JQ], y[JQ], vx[JQ], vy[JQ];
+          const ulonglong2 z2 = make_ulonglong2(0ull, 0ull);
+#pragma unroll
+          for (int e = 0; e < JQ; ++e) {
+            const bool in = 128 * e + 4 * lane < l;
+            x[e] = in ? a2[32 * e + lane] : z2;
+            y[e] = in ? b2[32 * e + lane] : z2;
+            vx[e] = in ? va2[32 * e + lane] : z2;
+            vy[e] = in ? vb2[32 * e + lane] : z2;
+          }
+          f2 g2[2] = {0ull, 0ull};
+#pragma unroll
+          for (int e = 0; e < JQ; ++e) {
+            g2[e & 1] = f2_fma(x[e].x, y[e].x, g2[e & 1]);
+            g2[e & 1] = f2_fma(x[e].y, y[e].y, g2[e & 1]);
+          }
+          const float2 gp = f2_to_float2(f2_add(g2[0], g2[1]));
+          const float gamma = warp_sum(gp.x + gp.y);
+          const float gnorm = sqrtf(alpha) * sqrtf(beta);
+          if (gamma != 0.f && fabsf(gamma) > ttol * gnorm) {
+            const float t = jac_tangent(alpha, beta, gamma);
+            const float c = rsqrtf(1.f + t * t), sn = c * t;
+            const f2 C2 = f2_splat(c), S2 = f2_splat(sn), NS2 = f2_splat(-sn);
+            // new p = c x - s y = (-s) y + c x, new q = s x + c y = c y + s x
+#pragma unroll
+            for (int e = 0; e < JQ; ++e) {
+              if (128 * e + 4 * lane < l) {
+                ulonglong2 na, nb, nva, nvb;
+                na.x = f2_fma(y[e].x, NS2, f2_mul(x[e].x, C2));
+                na.y = f2_fma(y[e].y, NS2, f2_mul(x[e].y, C2));
+                nb.x = f2_fma(y[e].x, C2, f2_mul(x[e].x, S2));
+                nb.y = f2_fma(y[e].y, C2, f2_mul(x[e].y, S2));
+                nva.x = f2_fma(vy[e].x, NS2, f2_mul(vx[e].x, C2));
+                nva.y = f2_fma(vy[e].y, NS2, f2_mul(vx[e].y, C2));
+                nvb.x = f2_fma(vy[e].x, C2, f2_mul(vx[e].x, S2));
+                nvb.y = f2_fma(vy[e].y, C2, f2_mul(vx[e].y, S2));
+                reinterpret_cast<ulonglong2*>(a)[32 * e + lane] = na;
+                reinterpret_cast<ulonglong2*>(b)[32 * e + lane] = nb;
+                reinterpret_cast<ulonglong2*>(va)[32 * e + lane] = nva;
+                reinterpret_cast<ulonglong2*>(vb)[32 * e + lane] = nvb;
+              }
+            }
+            if (lane == 0) {
+              nrm[p] = alpha - t * gamma;
+              nrm[q] = beta + t * gamma;
+              if (fabsf(gamma) > tstop * gnorm) atomicAdd(&rot_counts[sweep], 1);
+            }
+          }
+        } else if (!skip) {
           // The warp's two columns of M and of V in registers (JR values per
           // lane; rows lane + 32 e), loaded back to back.
           float x[JR], y[JR], vx[JR], vy[JR];
@@ -1078,8 +1136,8 @@ __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, fl
   }
 }
 
-template <int B, int JR>
-int launch_jacobi_blk_b(const Dla& d, float* M, float* V, int64_t l, double tol, double tol_stop,
+template <int B, int JR, bool VEC>
+int launch_jacobi_blk_v(const Dla& d, float* M, float* V, int64_t l, double tol, double tol_stop,
                         const double* fnorm, double tiny_rel, int max_sweeps, int* rot) {
   int li = (int)l, nblk = (int)((l + B - 1) / B), msw = max_sweeps;
   nblk += nblk & 1;
@@ -1089,15 +1147,25 @@ int launch_jacobi_blk_b(const Dla& d, float* M, float* V, int64_t l, double tol,
   // largest of them, so no thread lowers it below another one's launch.
   const size_t smem_max = sizeof(float) * ((size_t)4 * B * 32 * JR + 2 * B);
   BSRHT_CUDA_TRY(
-      cudaFuncSetAttribute(k_jacobi_blk<B, JR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+      cudaFuncSetAttribute(k_jacobi_blk<B, JR, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
   int occ = 0;
-  BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_blk<B, JR>, 32 * B, smem));
+  BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_blk<B, JR, VEC>, 32 * B, smem));
   if ((int64_t)(nblk / 2) > (int64_t)occ * num_sms()) return BSRHT_EUNSUP;  // not co-resident: caller falls back
   void* args[] = {&M, &V, &li, &nblk, &tol, &tol_stop, &fnorm, &tiny_rel, &msw, &rot};
-  const int st = launch_cooperative((const void*)k_jacobi_blk<B, JR>, dim3(nblk / 2), dim3(32 * B), args, smem, d.s);
+  const int st =
+      launch_cooperative((const void*)k_jacobi_blk<B, JR, VEC>, dim3(nblk / 2), dim3(32 * B), args, smem, d.s);
   if (st != BSRHT_OK) return st;
   note_launches(1);
   return BSRHT_OK;
+}
+
+// The 16-byte form when the columns (and so the blocks) start on 16 bytes.
+template <int B, int JR>
+int launch_jacobi_blk_b(const Dla& d, float* M, float* V, int64_t l, double tol, double tol_stop,
+                        const double* fnorm, double tiny_rel, int max_sweeps, int* rot) {
+  if (l % 4 == 0)
+    return launch_jacobi_blk_v<B, JR, true>(d, M, V, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot);
+  return launch_jacobi_blk_v<B, JR, false>(d, M, V, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot);
 }
 
 template <int B>
@@ -1112,18 +1180,18 @@ int launch_jacobi_blk_jr(const Dla& d, float* M, float* V, int64_t l, double tol
   return BSRHT_EUNSUP;
 }
 
-// Blocks of 8 columns, for l <= 512 only.  Only l / 16 CTAs work, and a
-// block round is bound by their instruction issue (ncu at l = 512, B = 16:
-// 43 % issue-active, about 460 warp instructions per warp and inner round),
-// so the block form wins only while the grid barriers it saves outweigh the
-// SMs it leaves idle: measured on GB300, FP32 phase at l = 512 10.9 ms
-// (B = 8) against 13.3 (B = 16) and 15.2 (scalar kernel), at l = 128 1.2
-// against 2.7 ms; at l = 600 and 1024 the scalar kernel is as fast or
-// faster.  BSRHT_EUNSUP sends the caller to the scalar kernel (also when the
-// block pairs cannot all be resident at once).
+// Blocks of 8 columns, for l <= 1024.  Only l / 16 CTAs work, and a block
+// round is bound by their instruction issue and latency (ncu at l = 512,
+// B = 16: 43 % issue-active), so the block form wins only while the grid
+// barriers it saves outweigh the SMs it leaves idle.  Measured on GB300,
+// FP32 phase of the benchmark's rSVD (16-byte accesses and packed
+// rotations when l % 4 == 0): l = 512 7.9 ms (B = 8; scalar kernel 11.6 ms,
+// B = 4 10.4 ms, B = 16 13.3 ms), l = 600 12.3 ms (scalar 14.1),
+// l = 1024 28.4 ms (scalar 34.9).  BSRHT_EUNSUP sends the caller to the
+// scalar kernel (also when the block pairs cannot all be resident at once).
 int launch_jacobi_blk(const Dla& d, float* M, float* V, int64_t l, double tol, double tol_stop, const double* fnorm,
                       double tiny_rel, int max_sweeps, int* rot) {
-  if (l <= 1 || l > 512) return BSRHT_EUNSUP;
+  if (l <= 1 || l > 1024) return BSRHT_EUNSUP;
   return launch_jacobi_blk_jr<8>(d, M, V, l, tol, tol_stop, fnorm, tiny_rel, max_sweeps, rot);
 }
 

@@ -601,16 +601,41 @@ int rsvd_impl(const bsrht_opts& o, const void* A, int64_t n, int64_t m, int k, i
     Vk = Vs_c;
   }
   TRY(tall_gemm(d, ar, tc, tc, DT::F64, n, kk, lq, Pv, lq, Vk64, Vk, ldv, U, k, false));
-  TRY(gemm64(d, ar, m, kk, lq, Q, lq, false, Us, lq, V, k));
+  if (q32 || (dry && tc == DT::F32)) {
+    // FP32-accuracy Q: V = Q U~_k on the tensor cores (FP32 accuracy, that
+    // of Q itself; U~_k also in FP32 for the CUDA-core form).
+    if (!dry) TRY(cast_copy(d, DT::F64, Us, DT::F32, Vs_c, lq * lq));
+    TRY(tall_gemm(d, ar, DT::F32, DT::F32, DT::F64, m, kk, lq, Qa, lq, Us, Vs_c, lq, V, k, false));
+  }
+  if (!q32) TRY(gemm64(d, ar, m, kk, lq, Q, lq, false, Us, lq, V, k));
   if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(S, sig, sizeof(double) * kk, cudaMemcpyDeviceToDevice, d.s));
   // With the FP32-accuracy Q, V is orthonormal to FP32 accuracy: one FP64
-  // CholeskyQR2 of V (m x k, R close to I) makes it orthonormal to FP64
-  // rounding while moving it by about 1e-6, the accuracy of FP32 data.
+  // CholeskyQR pass (V^T V = I + O(1e-6), so one pass reaches FP64 rounding)
+  // makes it orthonormal while moving it by about 1e-6, the accuracy of
+  // FP32 data; CholeskyQR2 with its fallbacks if that Cholesky fails.
   if ((q32 || dry) && kk == k && tc == DT::F32) {
-    void* Vv = nullptr;
-    TRY(orth_robust(d, ar, dry, DT::F64, V, X2, X3, m, k, seed ^ 0x54ull, ob, nullptr, true, false, &Vv));
-    if (!dry && Vv != static_cast<void*>(V))
-      BSRHT_CUDA_TRY(cudaMemcpyAsync(V, Vv, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, d.s));
+    bool done = false;
+    TRY(tall_gram(d, ar, dry, DT::F64, V, m, k, X3, ob.G));
+    if (!dry) {
+      TRY(chol_inv(d, ob.G, ob.LT1, ob.Rinv, ob.Ug, ob.Vg, k));
+      int hs = 0;
+      TRY(read_status(d, &hs));
+      if (hs & kStatusTcWait) return BSRHT_ETIMEDOUT;
+      if (hs)
+        BSRHT_CUDA_TRY(cudaMemsetAsync(d.status, 0, sizeof(int), d.s));
+      else
+        done = true;
+    }
+    if (done || dry) {
+      TRY(gemm64(d, ar, m, k, k, V, k, false, ob.Rinv, k, X2, k, true, false));
+      if (!dry) BSRHT_CUDA_TRY(cudaMemcpyAsync(V, X2, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, d.s));
+    }
+    if (!done) {
+      void* Vv = nullptr;
+      TRY(orth_robust(d, ar, dry, DT::F64, V, X2, X3, m, k, seed ^ 0x54ull, ob, nullptr, true, false, &Vv));
+      if (!dry && Vv != static_cast<void*>(V))
+        BSRHT_CUDA_TRY(cudaMemcpyAsync(V, Vv, sizeof(double) * m * k, cudaMemcpyDeviceToDevice, d.s));
+    }
   }
   {
     const size_t mk = ar.mark();
