@@ -294,9 +294,9 @@ TRAFFIC_RECORDS = {
     # every flush of the integer sums (one per 32 chunks of a CTA), which
     # grows with n like the reads.
     ("f64", 1 << 20, 4096, 4, 512): {
-        "kernel": "k_sketch_f64x", "read_n2e18": 8839051008, "write_n2e18": 266475776, "write_scales": True,
+        "kernel": "k_sketch_f64x", "read_n2e18": 8838070016, "write_n2e18": 266583552, "write_scales": True,
         "sources": ("paper_2210_11295_gb300/csrc/sketch_f64x.cu", "paper_2210_11295_gb300/csrc/tma.cuh"),
-        "sha256": "355d9498c01dfb623bf0a0c099e6941c4d448c0a76b89af6319342e80145d2b3"},
+        "sha256": "13dd167a62728e7de4f5dafe612557852b4d179c5eab3a41148373abf2378615"},
 }
 
 
@@ -716,7 +716,9 @@ def serve_object(lib, requests=120, compare=40):
     """A short config-5 stream through the serving loop (the serve mode runs
     the long one): saturation throughput, Poisson arrivals at 0.5x of it
     with p50 / p99 latency, and a reduced stream (n <= 2^17, m <= 1024)
-    served in FP32 against the plain FP64 one-request-at-a-time path."""
+    served from FP32 storage against the plain FP64 one-request-at-a-time
+    path: with Nystrom in FP64 arithmetic (equal accuracy) and, for
+    comparison, in FP32 arithmetic."""
     import numpy as np
     import torch
     import synth
@@ -735,7 +737,11 @@ def serve_object(lib, requests=120, compare=40):
     p_s, _, p_outs = _plain_run(lib, inputs, small, math.inf, keep_outputs=True)
     s_s, _, _, s_outs = _serve_run(lib, inputs, small, sdt, math.inf, len(small), keep_outputs=True, **kw)
     acc = _accuracy(lib, inputs, small, s_outs, p_outs, sdt)
-    del inputs
+    del s_outs
+    s32_s, _, _, s32_outs = _serve_run(lib, inputs, small, sdt, math.inf, len(small), keep_outputs=True,
+                                       nystrom_f64=False, **kw)
+    acc32 = _accuracy(lib, inputs, small, s32_outs, p_outs, sdt)
+    del inputs, s32_outs, p_outs
     torch.cuda.empty_cache()
     return {"stream": f"{len(reqs)} config-5 requests (sketch / rSVD / Nystrom, half BF16)",
             "saturation_req_s": round(x_sat, 2), "saturation_p50_ms": round(_pct(lat_sat, 50), 2),
@@ -744,7 +750,12 @@ def serve_object(lib, requests=120, compare=40):
                              "p99_ms": round(_pct(lat, 99), 2), "makespan_s": round(ms, 2)},
             "grouped_requests": st_sat["grouped_requests"], "graph_launches": st_sat["graph_launches"],
             "vs_plain_fp64": {"requests": len(small), "closed_batch_speedup": round(p_s / s_s, 2),
-                              "accuracy_worst": {kk: float(f"{vv:.3e}") for kk, vv in acc.items()}}}
+                              "accuracy_worst": {kk: float(f"{vv:.3e}") for kk, vv in acc.items()},
+                              "policy": "FP32 storage; sketch and rSVD in FP32 arithmetic, Nystrom in FP64 "
+                                        "arithmetic (BSRHT_PREC_F64)",
+                              "nystrom_in_fp32": {"closed_batch_speedup": round(p_s / s32_s, 2),
+                                                  "accuracy_worst": {kk: float(f"{vv:.3e}")
+                                                                     for kk, vv in acc32.items()}}}}
 
 
 def _extra(name, fn, out):
@@ -1010,7 +1021,7 @@ def _serve_outputs(req, dtype, lib):
     return (torch.empty(n, k, device="cuda", dtype=torch.float64), torch.empty(k, device="cuda", dtype=torch.float64))
 
 
-def _serve_run(lib, inputs, reqs, dtypes, rate, window, keep_outputs=False, **server_kw):
+def _serve_run(lib, inputs, reqs, dtypes, rate, window, keep_outputs=False, nystrom_f64=True, **server_kw):
     """Feeds reqs (arrival times scaled to `rate` req/s; inf = all at once)
     to a fresh server, at most `window` in flight.  Returns (makespan s,
     latencies arrival->done ms, stats, outputs)."""
@@ -1043,7 +1054,12 @@ def _serve_run(lib, inputs, reqs, dtypes, rate, window, keep_outputs=False, **se
             elif r["kind"] == "rsvd":
                 t = srv.submit_rsvd(a, r["k"], r["l"], r["p"], r["seed"], o)
             else:
-                t = srv.submit_nystrom(a, r["k"], r["l"], r["p"], r["seed"], o)
+                # Nystrom on FP32 storage in FP64 arithmetic: an FP32 sketch
+                # cannot resolve core directions below l 2^-23 of the
+                # largest, which the FP64 path keeps (Remark 3.1's threshold).
+                t = srv.submit_nystrom(a, r["k"], r["l"], r["p"], r["seed"], o,
+                                       precision=lib.PREC_F64 if nystrom_f64 and a.dtype == torch.float32
+                                       else lib.PREC_AUTO)
             tickets[i], outs[i] = t, o
             inflight.append(i)
         for j in inflight:

@@ -95,6 +95,22 @@ typedef enum bsrht_variant {
  * low-rank calls see it in their status word and return BSRHT_ETIMEDOUT).
  */
 
+/* ---- arithmetic precision ---------------------------------------------- */
+typedef enum bsrht_precision {
+  BSRHT_PREC_AUTO = 0, /* the arithmetic the dtype names (bsrht_dtype)        */
+  BSRHT_PREC_F64 = 1   /* FP64 arithmetic on FP32 storage (bsrht_sketch and
+                          bsrht_nystrom only; a no-op for BSRHT_F64 data):
+                          the sketch is the exact integer Walsh-Hadamard
+                          transform of the FP32 values widened to FP64 (the
+                          FP64 kernel), written in FP64, and everything after
+                          it runs as for FP64 data.  A is still read as FP32
+                          (half the bytes of FP64 storage).  Needs blocks of
+                          at least 512 rows (r >= 512) and 16-byte aligned
+                          rows; otherwise, and for 16-bit data, any variant
+                          but AUTO / CUDACORE and the other calls:
+                          BSRHT_EUNSUP.                                        */
+} bsrht_precision;
+
 typedef struct bsrht_opts {
   int32_t dtype;          /* bsrht_dtype of A                                */
   int32_t variant;        /* bsrht_variant                                   */
@@ -103,9 +119,11 @@ typedef struct bsrht_opts {
   void* stream;           /* cudaStream_t, NULL = legacy default stream      */
   void* workspace;        /* device scratch or NULL (library pool)           */
   size_t workspace_bytes; /* size of opts->workspace in bytes                */
+  int32_t precision;      /* bsrht_precision                                 */
 } bsrht_opts;
 
-/* Fills *opts with dtype F64, variant AUTO, lda 0, NULL stream/workspace. */
+/* Fills *opts with dtype F64, variant AUTO, lda 0, NULL stream/workspace,
+ * precision AUTO. */
 void bsrht_opts_init(bsrht_opts* opts);
 
 /* Short English description of a status code (static storage). */
@@ -117,7 +135,8 @@ const char* bsrht_strerror(int status);
  *   n, m : n >= 1, m >= 0.  p: number of blocks, 1 <= p <= n.
  *   l    : sketch rows, 1 <= l <= n (Thm 2.1 assumes n >= l); l > r is
  *          allowed because R samples with replacement.
- *   out  : l x m, row stride m; double for BSRHT_F64 input, float otherwise.
+ *   out  : l x m, row stride m; double for BSRHT_F64 input or precision
+ *          BSRHT_PREC_F64, float otherwise.
  * One pass over A: Philox signs, the Walsh-Hadamard butterflies, the row
  * sample and the sum over the p blocks all run inside the kernels; the block
  * sum is reduced in a fixed order, so repeated calls give identical bits.
@@ -232,6 +251,9 @@ int bsrht_srsvd_workspace(int64_t n, int64_t m, int32_t k, int64_t l, int64_t s,
  *   replaced by the SVD square root's pseudo-inverse (Remark 3.1);
  *   Z = Y_nu C^-1; R factor of Z (CholeskyQR2, rank-robust); SVD
  *   R = U~ Sigma~ V~^T; U = Z V~_k Sigma~_k^-1; Lambda = max(Sigma~_k^2 - nu, 0).
+ *   With BSRHT_F32 data and opts->precision = BSRHT_PREC_F64, Y is the FP64
+ *   sketch of the FP32 values and every step after it runs in FP64 (eps
+ *   2^-52): the result of the same matrix stored in FP64.
  *   Synchronises opts->stream; status codes as for bsrht_rsvd.
  */
 int bsrht_nystrom(const void* A, int64_t n, int32_t k, int64_t l, int32_t p,
@@ -349,6 +371,7 @@ typedef struct bsrht_request {
   double* U;
   double* S;        /* singular values (RSVD) or Lambda (Nystrom)          */
   double* V;        /* RSVD only                                           */
+  int32_t precision;/* bsrht_precision (sketch, Nystrom)                    */
 } bsrht_request;
 
 typedef struct bsrht_server_opts {

@@ -7,7 +7,8 @@ sm_103a CUDA kernels; torch only supplies device memory and streams.
 """
 
 from ._binding import (  # noqa: F401
-    BF16, F16, F32, F64, VARIANT_AUTO, VARIANT_CUDACORE, VARIANT_TENSOR, VARIANT_GAUSSIAN, BsrhtError, LIB_PATH, Server,
+    BF16, F16, F32, F64, VARIANT_AUTO, VARIANT_CUDACORE, VARIANT_TENSOR, VARIANT_GAUSSIAN, PREC_AUTO, PREC_F64,
+    BsrhtError, LIB_PATH, Server,
     bsrht_kernel_launches, bsrht_selftest_pool_allocator, bsrht_sketch_autotune, bsrht_sketch_autotune_reset, bsrht_nystrom, bsrht_nystrom_rbf, bsrht_nystrom_rbf_workspace, bsrht_profile_enable, bsrht_profile_stages, bsrht_nystrom_workspace, bsrht_release_pool, bsrht_rsvd, bsrht_rsvd_workspace, bsrht_srsvd, bsrht_srsvd_workspace,
     bsrht_sketch, bsrht_sketch_workspace, lib, sketch_out_dtype, strerror, version,
 )

@@ -27,6 +27,7 @@ BSRHT_ECUDA = -1003
 
 F64, F32, BF16, F16 = 0, 1, 2, 3
 VARIANT_AUTO, VARIANT_CUDACORE, VARIANT_TENSOR, VARIANT_GAUSSIAN = 0, 1, 2, 3
+PREC_AUTO, PREC_F64 = 0, 1  # bsrht_precision
 
 _DTYPES = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
@@ -45,6 +46,7 @@ class Opts(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
+        ("precision", ctypes.c_int32),
     ]
 
 
@@ -64,6 +66,7 @@ class Request(ctypes.Structure):
         ("U", ctypes.c_void_p),
         ("S", ctypes.c_void_p),
         ("V", ctypes.c_void_p),
+        ("precision", ctypes.c_int32),
     ]
 
 
@@ -174,7 +177,7 @@ def _dbl(t: torch.Tensor):
 
 
 def make_opts(a: torch.Tensor, variant: int = VARIANT_AUTO, workspace: torch.Tensor | None = None,
-              stream: torch.cuda.Stream | None = None) -> Opts:
+              stream: torch.cuda.Stream | None = None, precision: int = 0) -> Opts:
     if a.dim() != 2 or a.stride(1) != 1:
         raise ValueError("A must be a 2-D tensor with unit column stride (row-major)")
     if a.dtype not in _DTYPES:
@@ -183,6 +186,7 @@ def make_opts(a: torch.Tensor, variant: int = VARIANT_AUTO, workspace: torch.Ten
     lib.bsrht_opts_init(ctypes.byref(o))
     o.dtype = _DTYPES[a.dtype]
     o.variant = int(variant)
+    o.precision = int(precision)
     o.lda = int(a.stride(0)) if a.shape[0] > 1 else int(a.shape[1])
     s = stream if stream is not None else torch.cuda.current_stream(a.device)
     o.stream = ctypes.c_void_p(s.cuda_stream)
@@ -192,16 +196,17 @@ def make_opts(a: torch.Tensor, variant: int = VARIANT_AUTO, workspace: torch.Ten
     return o
 
 
-def sketch_out_dtype(dtype: torch.dtype) -> torch.dtype:
-    return torch.float64 if dtype == torch.float64 else torch.float32
+def sketch_out_dtype(dtype: torch.dtype, precision: int = 0) -> torch.dtype:
+    return torch.float64 if dtype == torch.float64 or precision == PREC_F64 else torch.float32
 
 
 def bsrht_sketch_workspace(n: int, m: int, p: int, l: int, dtype=torch.float32,
-                           variant: int = VARIANT_AUTO) -> int:
+                           variant: int = VARIANT_AUTO, precision: int = 0) -> int:
     o = Opts()
     lib.bsrht_opts_init(ctypes.byref(o))
     o.dtype = _DTYPES[dtype]
     o.variant = int(variant)
+    o.precision = int(precision)
     out = ctypes.c_size_t(0)
     _check(lib.bsrht_sketch_workspace(n, m, p, l, ctypes.byref(o), ctypes.byref(out)), "bsrht_sketch_workspace")
     return int(out.value)
@@ -209,14 +214,16 @@ def bsrht_sketch_workspace(n: int, m: int, p: int, l: int, dtype=torch.float32,
 
 def bsrht_sketch(a: torch.Tensor, p: int, l: int, seed: int, out: torch.Tensor | None = None,
                  variant: int = VARIANT_AUTO, workspace: torch.Tensor | None = None,
-                 stream: torch.cuda.Stream | None = None) -> torch.Tensor:
-    """B = Omega A (l x m) for the n x m device matrix ``a``."""
+                 stream: torch.cuda.Stream | None = None, precision: int = 0) -> torch.Tensor:
+    """B = Omega A (l x m) for the n x m device matrix ``a`` (FP64 output
+    for FP64 data or precision=PREC_F64)."""
     n, m = a.shape
+    odt = sketch_out_dtype(a.dtype, precision)
     if out is None:
-        out = torch.empty(l, m, device=a.device, dtype=sketch_out_dtype(a.dtype))
-    if out.shape != (l, m) or not out.is_contiguous() or out.dtype != sketch_out_dtype(a.dtype):
+        out = torch.empty(l, m, device=a.device, dtype=odt)
+    if out.shape != (l, m) or not out.is_contiguous() or out.dtype != odt:
         raise ValueError("out must be a contiguous l x m tensor of the sketch dtype")
-    o = make_opts(a, variant, workspace, stream)
+    o = make_opts(a, variant, workspace, stream, precision)
     _check(lib.bsrht_sketch(_dptr(a), n, m, p, l, seed & (2**64 - 1), _dptr(out), ctypes.byref(o)),
            "bsrht_sketch")
     return out
@@ -275,10 +282,11 @@ def bsrht_srsvd(a: torch.Tensor, k: int, l: int, s: int, p: int, seed: int,
     return u, sv, v
 
 
-def bsrht_nystrom_workspace(n: int, k: int, l: int, p: int, dtype=torch.float32) -> int:
+def bsrht_nystrom_workspace(n: int, k: int, l: int, p: int, dtype=torch.float32, precision: int = 0) -> int:
     o = Opts()
     lib.bsrht_opts_init(ctypes.byref(o))
     o.dtype = _DTYPES[dtype]
+    o.precision = int(precision)
     out = ctypes.c_size_t(0)
     _check(lib.bsrht_nystrom_workspace(n, k, l, p, ctypes.byref(o), ctypes.byref(out)),
            "bsrht_nystrom_workspace")
@@ -287,7 +295,7 @@ def bsrht_nystrom_workspace(n: int, k: int, l: int, p: int, dtype=torch.float32)
 
 def bsrht_nystrom(a: torch.Tensor, k: int, l: int, p: int, seed: int, variant: int = VARIANT_AUTO,
                   workspace: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None,
-                  outs=None):
+                  outs=None, precision: int = 0):
     """Rank-k randomized Nystrom (Algorithm 2): returns (U n x k, Lambda k) in float64."""
     n = a.shape[0]
     if a.shape[1] != n:
@@ -297,7 +305,7 @@ def bsrht_nystrom(a: torch.Tensor, k: int, l: int, p: int, seed: int, variant: i
         lam = torch.empty(k, device=a.device, dtype=torch.float64)
     else:
         u, lam = outs
-    o = make_opts(a, variant, workspace, stream)
+    o = make_opts(a, variant, workspace, stream, precision)
     _check(lib.bsrht_nystrom(_dptr(a), n, k, l, p, seed & (2**64 - 1), _dbl(u), _dbl(lam), ctypes.byref(o)),
            "bsrht_nystrom")
     return u, lam
@@ -419,11 +427,14 @@ class Server:
         r.p, r.k, r.l, r.seed = int(p), int(k), int(l), int(seed)
         return r
 
-    def submit_sketch(self, a: torch.Tensor, p: int, l: int, seed: int, out: torch.Tensor) -> int:
-        if out.shape != (l, a.shape[1]) or not out.is_contiguous() or out.dtype != sketch_out_dtype(a.dtype):
+    def submit_sketch(self, a: torch.Tensor, p: int, l: int, seed: int, out: torch.Tensor,
+                      precision: int = 0) -> int:
+        if (out.shape != (l, a.shape[1]) or not out.is_contiguous()
+                or out.dtype != sketch_out_dtype(a.dtype, precision)):
             raise ValueError("out must be a contiguous l x m tensor of the sketch dtype")
         r = self._base(a, REQ_SKETCH, p, l, seed)
         r.out = out.data_ptr()
+        r.precision = int(precision)
         return self._submit(r, (a, out))
 
     def submit_rsvd(self, a: torch.Tensor, k: int, l: int, p: int, seed: int,
@@ -434,10 +445,11 @@ class Server:
         return self._submit(r, (a, u, sv, v))
 
     def submit_nystrom(self, a: torch.Tensor, k: int, l: int, p: int, seed: int,
-                       outs: tuple[torch.Tensor, torch.Tensor]) -> int:
+                       outs: tuple[torch.Tensor, torch.Tensor], precision: int = 0) -> int:
         u, lam = outs
         r = self._base(a, REQ_NYSTROM, p, l, seed, k)
         r.U, r.S = u.data_ptr(), lam.data_ptr()
+        r.precision = int(precision)
         return self._submit(r, (a, u, lam))
 
     def poll(self, ticket: int) -> tuple[bool, int]:

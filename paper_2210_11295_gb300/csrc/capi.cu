@@ -73,6 +73,22 @@ bsrht_opts opts_or_default(const bsrht_opts* o) {
   return o ? *o : d;
 }
 
+int plan_dtype(const bsrht_opts& o, int* dt) {
+  if (o.precision != BSRHT_PREC_AUTO && o.precision != BSRHT_PREC_F64) return BSRHT_EINVAL;
+  if (o.precision == BSRHT_PREC_AUTO || o.dtype == BSRHT_F64) {
+    *dt = o.dtype;
+    return BSRHT_OK;
+  }
+  if (o.dtype != BSRHT_F32) return o.dtype >= BSRHT_F64 && o.dtype <= BSRHT_F16 ? BSRHT_EUNSUP : BSRHT_EINVAL;
+  *dt = kDtypeF32AsF64;
+  return BSRHT_OK;
+}
+
+int precision_auto_only(const bsrht_opts& o) {
+  if (o.precision == BSRHT_PREC_AUTO || (o.precision == BSRHT_PREC_F64 && o.dtype == BSRHT_F64)) return BSRHT_OK;
+  return o.precision == BSRHT_PREC_F64 ? BSRHT_EUNSUP : BSRHT_EINVAL;
+}
+
 }  // namespace bsrht
 
 using namespace bsrht;
@@ -87,6 +103,7 @@ void bsrht_opts_init(bsrht_opts* o) {
   o->stream = nullptr;
   o->workspace = nullptr;
   o->workspace_bytes = 0;
+  o->precision = BSRHT_PREC_AUTO;
 }
 
 const char* bsrht_strerror(int s) {
@@ -111,8 +128,11 @@ int bsrht_sketch_workspace(int64_t n, int64_t m, int32_t p, int64_t l, const bsr
                            size_t* bytes) {
   if (!bytes) return BSRHT_EINVAL;
   const bsrht_opts o = opts_or_default(opts);
+  int dt = 0;
+  int st = plan_dtype(o, &dt);
+  if (st != BSRHT_OK) return st;
   SketchPlan pl;
-  const int st = sketch_make_plan(pl, o.dtype, o.variant, n, m, o.lda, p, l, false);
+  st = sketch_make_plan(pl, dt, o.variant, n, m, o.lda, p, l, false);
   if (st != BSRHT_OK) return st;
   *bytes = pl.work_bytes;
   return BSRHT_OK;
@@ -122,8 +142,11 @@ int bsrht_sketch(const void* A, int64_t n, int64_t m, int32_t p, int64_t l, uint
                  const bsrht_opts* opts) {
   const bsrht_opts o = opts_or_default(opts);
   if ((!A && m > 0) || (!out && m > 0)) return BSRHT_EINVAL;
+  int dt = 0;
+  int st = plan_dtype(o, &dt);
+  if (st != BSRHT_OK) return st;
   SketchPlan pl;
-  int st = sketch_make_plan(pl, o.dtype, o.variant, n, m, o.lda, p, l, true, A);
+  st = sketch_make_plan(pl, dt, o.variant, n, m, o.lda, p, l, true, A);
   if (st != BSRHT_OK) return st;
   if (m == 0) return BSRHT_OK;
   void* work = nullptr;
@@ -139,6 +162,10 @@ int bsrht_sketch_autotune(const void* A, int64_t n, int64_t m, int32_t p, int64_
                           int32_t* choice, double* best_ms) {
   const bsrht_opts o = opts_or_default(opts);
   if (!A || m < 1 || n < 1 || p < 1 || l < 1) return BSRHT_EINVAL;
+  {
+    const int ps = precision_auto_only(o);
+    if (ps != BSRHT_OK) return ps;
+  }
   const size_t wb = sketch_autotune_work_bytes(o.dtype, n, m, o.lda, p, l);
   const size_t ob = (size_t)l * (size_t)m * (o.dtype == BSRHT_F64 ? 8 : 4);
   const size_t wpad = (wb + 255) / 256 * 256;

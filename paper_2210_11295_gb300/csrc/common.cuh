@@ -116,7 +116,14 @@ __host__ __device__ constexpr int ilog2c(long long x) { return x <= 1 ? 0 : 1 + 
 // Adds k to the library's kernel-launch counter (bsrht_kernel_launches).
 void note_launches(int k);
 
-inline size_t dtype_size(int dt) { return dt == BSRHT_F64 ? 8 : (dt == BSRHT_F32 ? 4 : 2); }
+// Internal element-type code for FP32 storage with FP64 arithmetic
+// (bsrht_opts.precision = BSRHT_PREC_F64 on BSRHT_F32 data): the sketch runs
+// the FP64 integer-transform kernel on FP32 input and writes FP64.
+constexpr int kDtypeF32AsF64 = 16;
+
+inline size_t dtype_size(int dt) {
+  return dt == BSRHT_F64 ? 8 : (dt == BSRHT_F32 || dt == kDtypeF32AsF64 ? 4 : 2);
+}
 
 }  // namespace bsrht
 

@@ -987,18 +987,22 @@ int rbf_sketch(const Dla& d, Arena& ar, bool dry, const RbfSource& src, int64_t 
 
 int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l, int p, uint64_t seed, double* U,
                  double* Lam, Arena& ar, bool dry, const RbfSource& src = RbfSource()) {
-  const DT ta = dt_of(o.dtype);
-  const DT tc = (ta == DT::F64) ? DT::F64 : DT::F32;
+  // FP64 arithmetic for FP64 data and for FP32 data with precision
+  // BSRHT_PREC_F64 (then Y is the FP64 sketch of the FP32 values).
+  const bool f64 = o.dtype == BSRHT_F64 || o.precision == BSRHT_PREC_F64;
+  const DT tc = f64 ? DT::F64 : DT::F32;
   const size_t cs = dt_size(tc);
   const int64_t lda = o.lda ? o.lda : n;
   SketchPlan sp_a, sp_y;
   const bool rbf = src.X != nullptr;
+  int a_dt = o.dtype;
+  if (!rbf) TRY(plan_dtype(o, &a_dt));
   if (rbf) {
     // The panels' plan (the widest panel) sizes the sketch scratch.
     const int64_t w = rbf_panel_width(n);
     TRY(sketch_make_plan(sp_a, BSRHT_F32, o.variant, n, w, w, p, l, !dry, nullptr));
   } else {
-    TRY(sketch_make_plan(sp_a, o.dtype, o.variant, n, n, lda, p, l, !dry, dry ? nullptr : A));
+    TRY(sketch_make_plan(sp_a, a_dt, o.variant, n, n, lda, p, l, !dry, dry ? nullptr : A));
   }
   // The l x l core Omega Y_nu is formed in FP64 whatever the type of A, with
   // the FP64-add kernel: the shift nu of Remark 3.1 is a few FP64 units of
@@ -1196,6 +1200,7 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
 
 int validate_rsvd(const bsrht_opts& o, int64_t n, int64_t m, int k, int64_t l, int p) {
   if (o.dtype < BSRHT_F64 || o.dtype > BSRHT_F16) return BSRHT_EINVAL;
+  TRY(precision_auto_only(o));
   if (n < 1 || m < 1 || k < 1 || l < k || l > m || l > n || p < 1 || p > n) return BSRHT_EINVAL;
   if (o.lda != 0 && o.lda < m) return BSRHT_EINVAL;
   return BSRHT_OK;
@@ -1204,6 +1209,7 @@ int validate_rsvd(const bsrht_opts& o, int64_t n, int64_t m, int k, int64_t l, i
 int validate_srsvd(const bsrht_opts& o, int64_t n, int64_t m, int k, int64_t l, int64_t s, int p) {
   if (o.dtype != BSRHT_F64 && o.dtype != BSRHT_F32) return o.dtype >= BSRHT_F64 && o.dtype <= BSRHT_F16
                                                                ? BSRHT_EUNSUP : BSRHT_EINVAL;
+  TRY(precision_auto_only(o));
   if (o.variant != BSRHT_VARIANT_AUTO && o.variant != BSRHT_VARIANT_CUDACORE) return BSRHT_EUNSUP;
   if (n < 1 || m < 1 || k < 1 || l < k || s < l || s > m || s > n || p < 1 || p > n) return BSRHT_EINVAL;
   if (o.lda != 0 && o.lda < m) return BSRHT_EINVAL;
@@ -1212,6 +1218,10 @@ int validate_srsvd(const bsrht_opts& o, int64_t n, int64_t m, int k, int64_t l, 
 
 int validate_nystrom(const bsrht_opts& o, int64_t n, int k, int64_t l, int p) {
   if (o.dtype < BSRHT_F64 || o.dtype > BSRHT_F16) return BSRHT_EINVAL;
+  {
+    int dt = 0;
+    TRY(plan_dtype(o, &dt));  // FP64 arithmetic on FP32 storage, or the dtype's
+  }
   // The shift of Remark 3.1 adds nu Omega^T entry by entry from the block
   // SRHT definition; the Gaussian comparator is a sketch / rSVD option only.
   if (o.variant == BSRHT_VARIANT_GAUSSIAN) return BSRHT_EUNSUP;
@@ -1223,6 +1233,7 @@ int validate_nystrom(const bsrht_opts& o, int64_t n, int k, int64_t l, int p) {
 int validate_nystrom_rbf(const bsrht_opts& o, const float* X, int64_t n, int64_t dim, double h, int k, int64_t l,
                          int p) {
   if (o.dtype != BSRHT_F32) return o.dtype >= BSRHT_F64 && o.dtype <= BSRHT_F16 ? BSRHT_EUNSUP : BSRHT_EINVAL;
+  TRY(precision_auto_only(o));
   if (o.variant == BSRHT_VARIANT_GAUSSIAN || o.variant == BSRHT_VARIANT_TENSOR) return BSRHT_EUNSUP;
   if (dim < 1 || !(h > 0.0) || !std::isfinite(h)) return BSRHT_EINVAL;
   const int64_t ldx = o.lda ? o.lda : dim;

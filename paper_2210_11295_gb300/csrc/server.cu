@@ -360,6 +360,9 @@ void executor(bsrht_server* sv) {
       o.stream = s;
       o.workspace = sv->pool + q->off;
       o.workspace_bytes = q->bytes;
+      o.precision = r.precision;
+      int pdt = r.dtype;  // the sketch plan's element-type code (validated at submit)
+      plan_dtype(o, &pdt);
       if (r.kind == BSRHT_REQ_SKETCH) {
         if (q->tune) {
           const size_t wb = sketch_autotune_work_bytes(r.dtype, r.n, r.m, r.lda, r.p, r.l);
@@ -371,7 +374,7 @@ void executor(bsrht_server* sv) {
         }
         SketchPlan pl;
         if (common == BSRHT_OK)
-          common = sketch_make_plan(pl, r.dtype, BSRHT_VARIANT_AUTO, r.n, r.m, r.lda, r.p, r.l, true, r.A);
+          common = sketch_make_plan(pl, pdt, BSRHT_VARIANT_AUTO, r.n, r.m, r.lda, r.p, r.l, true, r.A);
         if (common == BSRHT_OK && pl.work_bytes > q->bytes) common = BSRHT_ENOMEM;
         if (common == BSRHT_OK) {
           auto enq = [&](cudaStream_t st_) {
@@ -422,13 +425,23 @@ int validate_and_size(bsrht_server* sv, const bsrht_request& r, Req& q) {
   bsrht_opts_init(&o);
   o.dtype = r.dtype;
   o.lda = r.lda;
+  o.precision = r.precision;
   size_t bytes = 0;
   if (r.kind == BSRHT_REQ_SKETCH) {
     if (!r.out || r.m < 1) return BSRHT_EINVAL;
+    int pdt = r.dtype;
+    int st = plan_dtype(o, &pdt);
+    if (st != BSRHT_OK) return st;
     SketchPlan pl;
-    int st = sketch_make_plan(pl, r.dtype, BSRHT_VARIANT_AUTO, r.n, r.m, r.lda, r.p, r.l, true, r.A);
+    st = sketch_make_plan(pl, pdt, BSRHT_VARIANT_AUTO, r.n, r.m, r.lda, r.p, r.l, true, r.A);
     if (st != BSRHT_OK) return st;
     const int64_t lda = r.lda == 0 ? r.m : r.lda;
+    if (pdt != r.dtype) {
+      // FP64 arithmetic on FP32 storage: the TMA-fed integer-transform
+      // kernel alone (no grouped launch, no tuning).
+      q.bytes = FirstFit::round(pl.work_bytes);
+      return q.bytes > sv->alloc.cap() ? BSRHT_ENOMEM : BSRHT_OK;
+    }
     SketchPlan gp;
     const int gst = sketch_make_plan_grouped(gp, r.dtype, r.n, r.m, lda, r.p, r.l);
     const int occ_tiles = num_sms() * 2;

@@ -132,15 +132,22 @@ __device__ __forceinline__ uint64_t to_fixed_fast(uint64_t raw, int c0, uint32_t
   return (q ^ sm) - sm;
 }
 
-template <int JU>
+// The FP64 bits of an input value: FP64 as stored, FP32 widened (exactly).
+__device__ __forceinline__ uint64_t raw64(double x) { return (uint64_t)__double_as_longlong(x); }
+__device__ __forceinline__ uint64_t raw64(float x) { return (uint64_t)__double_as_longlong((double)x); }
+
+// Tin: FP64 A, or FP32 A with FP64 arithmetic (each value widened to FP64
+// at the load; a 64 KB stage slot then receives a 32 KB chunk and, after
+// the register phase, its 64-bit fixed-point transform).
+template <int JU, typename Tin>
 __global__ void __launch_bounds__(kNT, 1)
     k_sketch_f64x(const __grid_constant__ CUtensorMap tmap, SketchArgs g, const uint32_t* __restrict__ dmtab,
                   const uint64_t* __restrict__ dttab, int64_t tw, int* __restrict__ err) {
   using S = F64xShape<JU>;
   constexpr int JG = S::JG, NH = JU / 16 > 0 ? JU / 16 : 1;
+  constexpr uint32_t kChunkBytes = (uint32_t)(sizeof(Tin) * kR2 * kW);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128 - (reinterpret_cast<uintptr_t>(smem_raw) & 127)) & 127);
-  uint64_t* stage = reinterpret_cast<uint64_t*>(base);                         // [kStages][kR2][kW]
   uint32_t* s_off = reinterpret_cast<uint32_t*>(base + kStages * kStageBytes);  // [rg][u]: (s_j & 511) * kW
   uint32_t* s_hi = s_off + JG;                                                  // s_j >> 9
   int* s_scale = reinterpret_cast<int*>(s_hi + JG);                            // column scales S
@@ -178,8 +185,8 @@ __global__ void __launch_bounds__(kNT, 1)
   int64_t issued = 0;
   auto issue_next = [&]() {
     const int s = (int)(issued % kStages);
-    uint64_t* dst = stage + (size_t)s * kR2 * kW;
-    mbar_arrive_expect_tx(&bar[s], (uint32_t)kStageBytes);
+    Tin* dst = reinterpret_cast<Tin*>(base + (size_t)s * kStageBytes);
+    mbar_arrive_expect_tx(&bar[s], kChunkBytes);
     const int32_t x = (int32_t)(iss.pc * kW);
     const int64_t y0 = iss.i * g.rb + iss.a * kR2;
 #pragma unroll
@@ -295,7 +302,10 @@ __global__ void __launch_bounds__(kNT, 1)
       gmask[h] = (__ballot_sync(0xffffffffu, (u < JU && jl < jn) ? sg : 0u) >> (16 * (lane >> 4))) & 0xFFFFu;
     }
     const bool ok = mbar_wait_bounded(&bar[s], parity, kWaitLimit64);
-    uint64_t* st = stage + (size_t)s * kR2 * kW;
+    // The chunk as loaded (Tin) and, from the register phase's store on,
+    // its 64-bit fixed-point transform in the same slot.
+    const Tin* st_in = reinterpret_cast<const Tin*>(base + (size_t)s * kStageBytes);
+    uint64_t* st = reinterpret_cast<uint64_t*>(base + (size_t)s * kStageBytes);
 
     // Register phase: raw bits of rows rl + 32 e, their largest exponent
     // (kept in place in bits 20-30 of the high word).
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(kNT, 1)
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int rr = rl + 32 * e;
-      const uint64_t raw = rr < nvalid ? st[rr * kW + cg] : 0ull;
+      const uint64_t raw = rr < nvalid ? raw64(st_in[rr * kW + cg]) : 0ull;
       v[e] = raw;
       mex = max(mex, (uint32_t)(raw >> 32) & 0x7FF00000u);
     }
@@ -405,10 +415,10 @@ __global__ void k_sketch_reduce_checked64(SketchArgs g, double* __restrict__ out
   *o = sum * scale;
 }
 
-template <int JU>
+template <int JU, typename Tin>
 int launch_f64x(const SketchPlan& plan, const SketchArgs& a, const CUtensorMap& map, int* err, uint32_t* dmtab,
                 uint64_t* dttab, void* out, int64_t ldo, cudaStream_t stream) {
-  auto kern = k_sketch_f64x<JU>;
+  auto kern = k_sketch_f64x<JU, Tin>;
   const size_t smem = F64xShape<JU>::smem_bytes();
   BSRHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t tw = (a.jn + 63) / 64;
@@ -432,7 +442,7 @@ int launch_f64x(const SketchPlan& plan, const SketchArgs& a, const CUtensorMap& 
 
 template <int JU>
 int occ_f64x() {
-  auto kern = k_sketch_f64x<JU>;
+  auto kern = k_sketch_f64x<JU, double>;
   const size_t smem = F64xShape<JU>::smem_bytes();
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
@@ -453,12 +463,16 @@ int sketch_occupancy_f64x(const SketchPlan& plan) { return plan.JM == 8 ? occ_f6
 int sketch_launch_f64x(const SketchPlan& plan, const SketchArgs& a, void* out, int64_t ldo, int* err,
                        uint64_t* dtab, uint64_t* dttab, cudaStream_t stream) {
   CUtensorMap map;
-  if (!make_tensor_map_2d(&map, a.A, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, (uint64_t)plan.n, (uint64_t)plan.m,
-                          (uint64_t)plan.lda, kW, kBoxR))
+  const bool in32 = plan.dtype == kDtypeF32AsF64;
+  if (!make_tensor_map_2d(&map, a.A, in32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                          in32 ? 4 : 8, (uint64_t)plan.n, (uint64_t)plan.m, (uint64_t)plan.lda, kW, kBoxR))
     return BSRHT_EUNSUP;
   uint32_t* dmtab = reinterpret_cast<uint32_t*>(dtab);
-  if (plan.JM == 8) return launch_f64x<8>(plan, a, map, err, dmtab, dttab, out, ldo, stream);
-  return launch_f64x<16>(plan, a, map, err, dmtab, dttab, out, ldo, stream);
+  if (in32)
+    return plan.JM == 8 ? launch_f64x<8, float>(plan, a, map, err, dmtab, dttab, out, ldo, stream)
+                        : launch_f64x<16, float>(plan, a, map, err, dmtab, dttab, out, ldo, stream);
+  if (plan.JM == 8) return launch_f64x<8, double>(plan, a, map, err, dmtab, dttab, out, ldo, stream);
+  return launch_f64x<16, double>(plan, a, map, err, dmtab, dttab, out, ldo, stream);
 }
 
 }  // namespace bsrht

@@ -19,6 +19,7 @@
 // results: serialise them on one stream.
 #include <mutex>
 
+#include "capi_internal.cuh"
 #include "common.cuh"
 #include "sketch.cuh"
 #include "trace.cuh"
@@ -63,8 +64,11 @@ extern "C" int bsrht_sketch_noalloc(const void* A, int64_t n, int64_t m, int32_t
   bsrht_opts_init(&o);
   if (opts) o = *opts;
   if ((!A && m > 0) || (!out && m > 0)) return BSRHT_EINVAL;
+  int dt = 0;
+  int st = plan_dtype(o, &dt);
+  if (st != BSRHT_OK) return st;
   SketchPlan pl;
-  int st = sketch_make_plan(pl, o.dtype, o.variant, n, m, o.lda, p, l, true, A);
+  st = sketch_make_plan(pl, dt, o.variant, n, m, o.lda, p, l, true, A);
   if (st != BSRHT_OK) return st;
   if (m == 0) return BSRHT_OK;
   if (pl.work_bytes > kNoAllocScratchBytes) return BSRHT_ENOMEM;

@@ -266,10 +266,21 @@ static int make_plan_choice(SketchPlan& pl, int dtype, int64_t n, int64_t m, int
 
 int sketch_make_plan(SketchPlan& pl, int dtype, int variant, int64_t n, int64_t m, int64_t lda,
                      int p, int64_t l, bool query_device, const void* A) {
-  if (dtype < BSRHT_F64 || dtype > BSRHT_F16) return BSRHT_EINVAL;
+  if ((dtype < BSRHT_F64 || dtype > BSRHT_F16) && dtype != kDtypeF32AsF64) return BSRHT_EINVAL;
   if (n < 1 || m < 0 || p < 1 || (int64_t)p > n || l < 1 || l > n) return BSRHT_EINVAL;
   if (lda == 0) lda = m;
   if (lda < m) return BSRHT_EINVAL;
+  if (dtype == kDtypeF32AsF64) {
+    // FP32 A, FP64 arithmetic: only the TMA-fed integer-transform kernel
+    // (blocks of at least one 512-row chunk, 16-byte aligned rows).
+    if (variant != BSRHT_VARIANT_AUTO && variant != BSRHT_VARIANT_CUDACORE) return BSRHT_EUNSUP;
+    const int st = make_plan_choice(pl, BSRHT_F64, n, m, lda, p, l, query_device, nullptr, -2);
+    if (st != BSRHT_OK) return st;
+    const bool tma_ok = pl.r >= 512 && tma_layout_ok(dtype, A, lda) && (int64_t)p * ((pl.rb + 511) / 512) < INT32_MAX;
+    if (!tma_ok) return BSRHT_EUNSUP;
+    pl.dtype = dtype;
+    return make_plan_f64x(pl, query_device);
+  }
   int64_t rb = (n + p - 1) / p, r = 1;
   while (r < rb) r <<= 1;
   if (variant == BSRHT_VARIANT_GAUSSIAN) return gaussian_plan(pl, dtype, n, m, lda, p, l);

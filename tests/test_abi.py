@@ -171,3 +171,46 @@ def test_lowrank_workspace_queries_scale():
     assert ws > w20  # Algorithm 3 also holds the on-device transpose of A
     wn = b.bsrht_nystrom_workspace(65536, 100, 600, 8, torch.float32)
     assert wn >= 65536 * 600 * 4
+
+
+def test_precision_option_defaults_and_queries():
+    """bsrht_opts.precision (appended last): AUTO by default; FP64
+    arithmetic on FP32 storage is accepted by the sketch and Nystrom
+    queries only (BSRHT_EUNSUP elsewhere, for 16-bit data and for blocks
+    below one 512-row chunk), unknown values are BSRHT_EINVAL; the query
+    with it sizes the FP64 integer-transform kernel's scratch."""
+    import torch
+    import paper_2210_11295_gb300 as b
+    from paper_2210_11295_gb300 import _binding as bb
+    o = bb.Opts()
+    o.precision = 5  # bsrht_opts_init must overwrite the appended field too
+    b.lib.bsrht_opts_init(ctypes.byref(o))
+    assert o.precision == b.PREC_AUTO and o.dtype == bb.F64
+    w32 = b.bsrht_sketch_workspace(1 << 16, 256, 4, 512, torch.float32)
+    w64 = b.bsrht_sketch_workspace(1 << 16, 256, 4, 512, torch.float64)
+    wx = b.bsrht_sketch_workspace(1 << 16, 256, 4, 512, torch.float32, precision=b.PREC_F64)
+    assert wx > 0 and w32 > 0 and w64 > 0
+    with pytest.raises(b.BsrhtError) as e:
+        b.bsrht_sketch_workspace(1 << 16, 256, 4, 512, torch.bfloat16, precision=b.PREC_F64)
+    assert e.value.status == bb.BSRHT_EUNSUP
+    with pytest.raises(b.BsrhtError) as e:  # r = 256 < 512
+        b.bsrht_sketch_workspace(1024, 256, 4, 64, torch.float32, precision=b.PREC_F64)
+    assert e.value.status == bb.BSRHT_EUNSUP
+    with pytest.raises(b.BsrhtError) as e:
+        b.bsrht_sketch_workspace(1 << 16, 256, 4, 512, torch.float32, precision=7)
+    assert e.value.status == bb.BSRHT_EINVAL
+    assert b.bsrht_nystrom_workspace(1 << 14, 40, 200, 4, torch.float32, precision=b.PREC_F64) > 0
+    o = _opts(bb.F32)
+    o.precision = b.PREC_F64
+    out = ctypes.c_size_t(0)
+    assert b.lib.bsrht_rsvd_workspace(1 << 14, 256, 10, 40, 4, ctypes.byref(o), ctypes.byref(out)) == bb.BSRHT_EUNSUP
+    o.dtype = bb.F64  # a no-op for FP64 data
+    assert b.lib.bsrht_rsvd_workspace(1 << 14, 256, 10, 40, 4, ctypes.byref(o), ctypes.byref(out)) == bb.BSRHT_OK
+
+
+def test_request_struct_precision_is_last():
+    from paper_2210_11295_gb300 import _binding as bb
+    names = [n for n, _ in bb.Request._fields_]
+    assert names[-1] == "precision" and names[-2] == "V"
+    names = [n for n, _ in bb.Opts._fields_]
+    assert names[-1] == "precision" and names[-2] == "workspace_bytes"
