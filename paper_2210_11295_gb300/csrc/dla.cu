@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "dla.cuh"
@@ -1198,7 +1199,7 @@ int launch_jacobi_blk(const Dla& d, float* M, float* V, int64_t l, double tol, d
 }  // namespace
 
 int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout,
-               double polish_tol, double zero_rel, int64_t ktop) {
+               double polish_tol, double zero_rel, int64_t ktop, double keep_rel) {
   if (l > 2048) return BSRHT_EUNSUP;
   const int max_sweeps = 40;
   // Rotate only while the cosine of the pair exceeds sqrt(l) eps (the usual
@@ -1209,10 +1210,13 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
   // polish the s leading columns of the FP32 phase (a margin of
   // max(16, ktop / 4) beyond ktop) and keep the FP32 phase's estimates for
   // the rest.
-  const int64_t s = (mixed && polish_tol > 0.0 && ktop > 0)
-                        ? std::min<int64_t>(l, ktop + std::max<int64_t>(16, ktop / 4))
-                        : l;
-  const bool part = s < l;
+  // With keep_rel > 0 instead, the leading columns are those whose FP32
+  // norm exceeds keep_rel times the largest (counted after the FP32 phase),
+  // with the same margin; the workspace is sized for all l.
+  auto with_margin = [&](int64_t c) { return std::min<int64_t>(l, c + std::max<int64_t>(16, c / 4)); };
+  const bool part_mode = mixed && polish_tol > 0.0 && (ktop > 0 || keep_rel > 0.0);
+  int64_t s = part_mode ? (ktop > 0 ? with_margin(ktop) : l) : l;
+  const bool part = part_mode && (s < l || keep_rel > 0.0);
   double* Vc = static_cast<double*>(ar.take(sizeof(double) * l * l));
   double* sig = static_cast<double*>(ar.take(sizeof(double) * l));
   int* perm = static_cast<int*>(ar.take(sizeof(int) * l));
@@ -1338,6 +1342,15 @@ int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, dou
       DLA_LAUNCH_CHECK();
       k_rank_desc<<<blocks_for(l, 256), 256, 0, d.s>>>(sig, perm, l);
       DLA_LAUNCH_CHECK();
+      if (ktop <= 0) {
+        std::vector<double> sh((size_t)l);
+        BSRHT_CUDA_TRY(cudaMemcpyAsync(sh.data(), sig, sizeof(double) * l, cudaMemcpyDeviceToHost, d.s));
+        BSRHT_CUDA_TRY(cudaStreamSynchronize(d.s));
+        const double smax = *std::max_element(sh.begin(), sh.end());
+        int64_t c = 0;
+        for (double v : sh) c += v > keep_rel * smax;
+        s = with_margin(std::max<int64_t>(c, 1));
+      }
       double* Vr = S2;
       double* Vn = Vc;
       k_gather_cols_t<<<blocks_for(l * s, 256), 256, 0, d.s>>>(V32, perm, l, s, Vr);

@@ -87,10 +87,12 @@ int chol_inv(const Dla& d, double* g, double* LT, double* Rinv, double* T, doubl
 // max(16, ktop / 4)) leading columns of the FP32 phase are polished in FP64
 // (the SVD of M restricted to their span, which differs from the leading
 // triplets of M in second order of the FP32 phase's residual cosines);
-// ranks s and beyond hold the FP32 phase's estimates.  colsM is overwritten
-// in every case.
+// ranks s and beyond hold the FP32 phase's estimates.  keep_rel > 0 with
+// polish_tol > 0 and ktop = 0 (a caller that keeps the triplets with
+// sigma > keep_rel sigma_1): s = c + max(16, c / 4) with c the FP32 phase's
+// count above that threshold.  colsM is overwritten in every case.
 int jacobi_svd(const Dla& d, Arena& ar, double* colsM, int64_t l, double* U, double* sigma, double* Vout,
-               double polish_tol = 0.0, double zero_rel = 0.0, int64_t ktop = 0);
+               double polish_tol = 0.0, double zero_rel = 0.0, int64_t ktop = 0, double keep_rel = 0.0);
 
 // Tensor-core (tcgen05) GEMM in FP32 accuracy (three TF32 products):
 // C (M x N, FP32 or FP64 in tc_out, ldc) = A (M x K, FP32, lda) * B, with B

@@ -1129,8 +1129,13 @@ int nystrom_impl(const bsrht_opts& o, const void* A, int64_t n, int k, int64_t l
       note_launches(1);
     }
     {
+      // FP32 data: only eigenvalues above tau_core lambda_max are kept, so
+      // only those columns (with a margin) are polished in FP64.
       const size_t mk = ar.mark();
-      TRY(jacobi_svd(d, ar, G, l, ob.Ug, ob.lam, Cinv));
+      if (tc == DT::F32)
+        TRY(jacobi_svd(d, ar, G, l, ob.Ug, ob.lam, Cinv, polish_tol_fp32(l), 0.0, 0, 0.5 * tau_core));
+      else
+        TRY(jacobi_svd(d, ar, G, l, ob.Ug, ob.lam, Cinv));
       ar.release(mk);
     }
     if (!dry) {
