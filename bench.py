@@ -286,10 +286,10 @@ TRAFFIC_RECORDS = {
     # FP32: the reads are A itself; the writes are the per-(CTA, panel)
     # partial sums, written once (they do not grow with n).
     ("f32", 1 << 20, 4096, 4, 512): {
-        "kernel": "k_sketch_tma", "read_n2e18": 4295590912, "write_n2e18": 11194624, "write_scales": False,
+        "kernel": "k_sketch_tma", "read_n2e18": 4295974144, "write_n2e18": 10893056, "write_scales": False,
         "sources": ("paper_2210_11295_gb300/csrc/sketch_tma.cu", "paper_2210_11295_gb300/csrc/tma.cuh",
                     "paper_2210_11295_gb300/csrc/f32x2.cuh"),
-        "sha256": "1cd039aecde03d8f4d0c8565b5c31d1b7d4873893bbffec7c79c90b7910bd8f6"},
+        "sha256": "ccf7d93578422680a1a8c72cc11d4a815afe82894387239a164cfbf28f722790"},
     # FP64: besides A, the read-modify-write of the FP64 partial sums at
     # every flush of the integer sums (one per 32 chunks of a CTA), which
     # grows with n like the reads.
@@ -466,14 +466,33 @@ def f64_sketch_object(lib, a32, p, l, peak, stream):
     ref = orc.sketch_fast(a[:, cols].cpu().numpy(), p, l, 9)
     nbytes = n * m * 8 + l * m * 8
     ach = nbytes / (k_ms * 1e-3) / 1e9
-    del a, out, ws
+    del out, ws
+    torch.cuda.empty_cache()
+    # The whole rank-100 Algorithm 1 in FP64 on the same matrix: one warm-up
+    # call, one timed call with its stages (the tall products run on the
+    # FP64 units, 1.25 TFLOP/s nominal on this GPU).
+    k = 100
+    rws = torch.empty(max(lib.bsrht_rsvd_workspace(n, m, k, l, p, torch.float64), 1), dtype=torch.uint8,
+                      device=a.device)
+    outs = (torch.empty(n, k, device=a.device, dtype=torch.float64),
+            torch.empty(k, device=a.device, dtype=torch.float64),
+            torch.empty(m, k, device=a.device, dtype=torch.float64))
+    lib.bsrht_rsvd(a, k, l, p, 0, workspace=rws, outs=outs)
+    lib.bsrht_profile_enable(True)
+    rs_ms = _events_ms(stream, lambda: lib.bsrht_rsvd(a, k, l, p, 1, workspace=rws, outs=outs), 1)
+    rs_st = {name: round(v, 2) for name, v in lib.bsrht_profile_stages()}
+    lib.bsrht_profile_enable(False)
+    rs_s1 = float(outs[1][0].item())
+    del a, rws, outs
     torch.cuda.empty_cache()
     return {"workload": f"tall-skinny lowrank+noise n={n} m={m} f64 p={p} l={l} (sketch)", "dtype": "f64",
             "kernel": "k_sketch_f64x (exact 64-bit integer Walsh-Hadamard transform, TMA-fed)",
             "ms": round(call_ms, 4), "kernel_ms": round(k_ms, 4), "gbs": round(nbytes / (call_ms * 1e-3) / 1e9, 2),
             "roofline": {"bound": "hbm", "achieved": round(ach, 2), "peak": peak, "unit": "GB/s",
                          "frac": round(ach / peak, 4), "traffic": sketch_traffic("f64", n, m, p, l)},
-            "parity": {"columns": cols, "rel_fro_vs_oracle": float(f"{_rel(got, ref):.3e}"), "tol": 1e-12}}
+            "parity": {"columns": cols, "rel_fro_vs_oracle": float(f"{_rel(got, ref):.3e}"), "tol": 1e-12},
+            "rsvd_fp64": {"k": k, "ms": round(rs_ms, 1), "sigma_1": rs_s1, "stages_ms": rs_st,
+                          "note": "tall products A Q and the tall QR on the FP64 units"}}
 
 
 def p_sweep_object(lib, a, l, k, peak, stream):
