@@ -927,8 +927,8 @@ int launch_jacobi(const Dla& d, T* cols, T* Vc, T* nrm, int64_t l, int64_t rows,
 // rotated exactly once, as in the scalar kernel, with the same rotation and
 // stopping rules.  Column norms are formed exactly when a block pair is
 // loaded and carried through the rotations in between.
-template <int B, int JR, bool VEC>
-__global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, float* __restrict__ V, int l, int nblk,
+template <int B, int JR, bool VEC, int WP>
+__global__ void __launch_bounds__(32 * B * WP) k_jacobi_blk(float* __restrict__ M, float* __restrict__ V, int l, int nblk,
                                                        double tol, double tol_stop, const double* __restrict__ fnorm,
                                                        double tiny_rel, int max_sweeps,
                                                        int* __restrict__ rot_counts) {
@@ -937,7 +937,9 @@ __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, fl
   float* Ms = jsm;
   float* Vs = jsm + (size_t)2 * B * l;
   float* nrm = Vs + (size_t)2 * B * l;
+  float* part = nrm + 2 * B;  // [B][2]: the two warps' partial inner products (WP = 2)
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pw = w / WP, hw = w % WP;  // pair slot and half of the warp
   const float ttol = (float)tol, tstop = (float)tol_stop;
   const double tiny = tiny_rel * fnorm[0];
   const float tiny2 = (float)(tiny * tiny);
@@ -976,7 +978,7 @@ __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, fl
         }
       }
       __syncthreads();
-      for (int j = w; j < 2 * B; j += B) {
+      for (int j = w; j < 2 * B; j += B * WP) {
         const float* col = Ms + (size_t)j * l;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
         int r = lane;
@@ -994,14 +996,14 @@ __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, fl
       const int nr = (R == 0 ? B - 1 : 0) + B;
       for (int ir = 0; ir < nr; ++ir) {
         int p, q;
-        if (R == 0 && ir < B - 1) {  // inside block 0 (warps 0..B/2-1) or block 1
-          const int half = w / (B / 2), k = w % (B / 2);
+        if (R == 0 && ir < B - 1) {  // inside block 0 (pair slots 0..B/2-1) or block 1
+          const int half = pw / (B / 2), k = pw % (B / 2);
           p = half * B + rr_player(k, ir, B);
           q = half * B + rr_player(B - 1 - k, ir, B);
         } else {
           const int cr = ir - (R == 0 ? B - 1 : 0);
-          p = w;
-          q = B + (w + cr) % B;
+          p = pw;
+          q = B + (pw + cr) % B;
         }
         const int gp = gcol(P, Q, p), gq = gcol(P, Q, q);
         float* a = Ms + (size_t)p * l;
@@ -1010,11 +1012,16 @@ __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, fl
         float* vb = Vs + (size_t)q * l;
         const float alpha = nrm[p], beta = nrm[q];
         bool skip = gp >= l || gq >= l || (alpha <= tiny2 && beta <= tiny2);
-        if (!skip && VEC) {
+        if constexpr (VEC) {
+          if (!skip) {
           // l % 4 == 0: the lane holds rows 128 e + 4 lane + j (j < 4) of the
           // two columns of M and V, moved with 16-byte shared-memory accesses,
-          // and rotates them as packed pairs (rows j = 0, 1 and 2, 3).
-          constexpr int JQ = JR / 4;
+          // and rotates them as packed pairs (rows j = 0, 1 and 2, 3).  With
+          // WP = 2 the pair's two warps take the chunks e = 2 e' + hw and add
+          // their partial inner products through shared memory (a 64-thread
+          // named barrier per pair), in the same order in both warps, so both
+          // derive the same rotation.
+          constexpr int JQ = JR / 4 / WP;
           const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(a);
           const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(b);
           const ulonglong2* va2 = reinterpret_cast<const ulonglong2*>(va);
@@ -1023,11 +1030,12 @@ __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, fl
           const ulonglong2 z2 = make_ulonglong2(0ull, 0ull);
 #pragma unroll
           for (int e = 0; e < JQ; ++e) {
-            const bool in = 128 * e + 4 * lane < l;
-            x[e] = in ? a2[32 * e + lane] : z2;
-            y[e] = in ? b2[32 * e + lane] : z2;
-            vx[e] = in ? va2[32 * e + lane] : z2;
-            vy[e] = in ? vb2[32 * e + lane] : z2;
+            const int c4 = 32 * (WP * e + hw) + lane;  // 16-byte chunk: rows 4 c4 .. 4 c4 + 3
+            const bool in = 4 * c4 < l;
+            x[e] = in ? a2[c4] : z2;
+            y[e] = in ? b2[c4] : z2;
+            vx[e] = in ? va2[c4] : z2;
+            vy[e] = in ? vb2[c4] : z2;
           }
           f2 g2[2] = {0ull, 0ull};
 #pragma unroll
@@ -1036,7 +1044,12 @@ __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, fl
             g2[e & 1] = f2_fma(x[e].y, y[e].y, g2[e & 1]);
           }
           const float2 gp = f2_to_float2(f2_add(g2[0], g2[1]));
-          const float gamma = warp_sum(gp.x + gp.y);
+          float gamma = warp_sum(gp.x + gp.y);
+          if constexpr (WP == 2) {
+            if (lane == 0) part[2 * pw + hw] = gamma;
+            asm volatile("bar.sync %0, 64;" ::"r"(1 + pw) : "memory");
+            gamma = part[2 * pw] + part[2 * pw + 1];
+          }
           const float gnorm = sqrtf(alpha) * sqrtf(beta);
           if (gamma != 0.f && fabsf(gamma) > ttol * gnorm) {
             const float t = jac_tangent(alpha, beta, gamma);
@@ -1045,7 +1058,8 @@ __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, fl
             // new p = c x - s y = (-s) y + c x, new q = s x + c y = c y + s x
 #pragma unroll
             for (int e = 0; e < JQ; ++e) {
-              if (128 * e + 4 * lane < l) {
+              const int c4 = 32 * (WP * e + hw) + lane;
+              if (4 * c4 < l) {
                 ulonglong2 na, nb, nva, nvb;
                 na.x = f2_fma(y[e].x, NS2, f2_mul(x[e].x, C2));
                 na.y = f2_fma(y[e].y, NS2, f2_mul(x[e].y, C2));
@@ -1055,17 +1069,18 @@ __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, fl
                 nva.y = f2_fma(vy[e].y, NS2, f2_mul(vx[e].y, C2));
                 nvb.x = f2_fma(vy[e].x, C2, f2_mul(vx[e].x, S2));
                 nvb.y = f2_fma(vy[e].y, C2, f2_mul(vx[e].y, S2));
-                reinterpret_cast<ulonglong2*>(a)[32 * e + lane] = na;
-                reinterpret_cast<ulonglong2*>(b)[32 * e + lane] = nb;
-                reinterpret_cast<ulonglong2*>(va)[32 * e + lane] = nva;
-                reinterpret_cast<ulonglong2*>(vb)[32 * e + lane] = nvb;
+                reinterpret_cast<ulonglong2*>(a)[c4] = na;
+                reinterpret_cast<ulonglong2*>(b)[c4] = nb;
+                reinterpret_cast<ulonglong2*>(va)[c4] = nva;
+                reinterpret_cast<ulonglong2*>(vb)[c4] = nvb;
               }
             }
-            if (lane == 0) {
+            if (hw == 0 && lane == 0) {
               nrm[p] = alpha - t * gamma;
               nrm[q] = beta + t * gamma;
               if (fabsf(gamma) > tstop * gnorm) atomicAdd(&rot_counts[sweep], 1);
             }
+          }
           }
         } else if (!skip) {
           // The warp's two columns of M and of V in registers (JR values per
@@ -1137,24 +1152,28 @@ __global__ void __launch_bounds__(32 * B) k_jacobi_blk(float* __restrict__ M, fl
   }
 }
 
+// Two warps per column pair (each on half the rows) in the 16-byte form
+// when a lane holds at least two 16-byte chunks: four warps per scheduler
+// instead of two hide the shared-memory and FMA latencies of a round.
 template <int B, int JR, bool VEC>
 int launch_jacobi_blk_v(const Dla& d, float* M, float* V, int64_t l, double tol, double tol_stop,
                         const double* fnorm, double tiny_rel, int max_sweeps, int* rot) {
+  constexpr int WP = (VEC && JR >= 8) ? 2 : 1;
+  constexpr int NT = 32 * B * WP;
+  auto kern = k_jacobi_blk<B, JR, VEC, WP>;
   int li = (int)l, nblk = (int)((l + B - 1) / B), msw = max_sweeps;
   nblk += nblk & 1;
-  const size_t smem = sizeof(float) * ((size_t)4 * B * l + 2 * B);
+  const size_t smem = sizeof(float) * ((size_t)4 * B * l + 4 * B);
   // One instance serves every l up to 32 JR, and host threads (the server's
   // executors) launch it concurrently: the attribute is always set to the
   // largest of them, so no thread lowers it below another one's launch.
-  const size_t smem_max = sizeof(float) * ((size_t)4 * B * 32 * JR + 2 * B);
-  BSRHT_CUDA_TRY(
-      cudaFuncSetAttribute(k_jacobi_blk<B, JR, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+  const size_t smem_max = sizeof(float) * ((size_t)4 * B * 32 * JR + 4 * B);
+  BSRHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
   int occ = 0;
-  BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_blk<B, JR, VEC>, 32 * B, smem));
+  BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
   if ((int64_t)(nblk / 2) > (int64_t)occ * num_sms()) return BSRHT_EUNSUP;  // not co-resident: caller falls back
   void* args[] = {&M, &V, &li, &nblk, &tol, &tol_stop, &fnorm, &tiny_rel, &msw, &rot};
-  const int st =
-      launch_cooperative((const void*)k_jacobi_blk<B, JR, VEC>, dim3(nblk / 2), dim3(32 * B), args, smem, d.s);
+  const int st = launch_cooperative((const void*)kern, dim3(nblk / 2), dim3(NT), args, smem, d.s);
   if (st != BSRHT_OK) return st;
   note_launches(1);
   return BSRHT_OK;
