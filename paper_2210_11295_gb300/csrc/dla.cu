@@ -1204,10 +1204,11 @@ int launch_jacobi_blk_jr(const Dla& d, float* M, float* V, int64_t l, double tol
 // round is bound by their instruction issue and latency (ncu at l = 512,
 // B = 16: 43 % issue-active), so the block form wins only while the grid
 // barriers it saves outweigh the SMs it leaves idle.  Measured on GB300,
-// FP32 phase of the benchmark's rSVD (16-byte accesses and packed
-// rotations when l % 4 == 0): l = 512 7.9 ms (B = 8; scalar kernel 11.6 ms,
-// B = 4 10.4 ms, B = 16 13.3 ms), l = 600 12.3 ms (scalar 14.1),
-// l = 1024 28.4 ms (scalar 34.9).  BSRHT_EUNSUP sends the caller to the
+// FP32 phase of the benchmark's rSVD (16-byte accesses, packed rotations
+// and two warps per pair when l % 4 == 0): l = 512 7.3 ms (B = 8, one warp
+// per pair 7.9; scalar kernel 11.6 ms, B = 4 10.4 ms, B = 16 13.3 ms),
+// l = 600 11.1 ms (one warp 12.3, scalar 14.1), l = 1024 22.9 ms (one warp
+// 28.4, scalar 34.9).  BSRHT_EUNSUP sends the caller to the
 // scalar kernel (also when the block pairs cannot all be resident at once).
 int launch_jacobi_blk(const Dla& d, float* M, float* V, int64_t l, double tol, double tol_stop, const double* fnorm,
                       double tiny_rel, int max_sweeps, int* rot) {
