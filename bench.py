@@ -286,10 +286,10 @@ TRAFFIC_RECORDS = {
     # FP32: the reads are A itself; the writes are the per-(CTA, panel)
     # partial sums, written once (they do not grow with n).
     ("f32", 1 << 20, 4096, 4, 512): {
-        "kernel": "k_sketch_tma", "read_n2e18": 4295974144, "write_n2e18": 10893056, "write_scales": False,
+        "kernel": "k_sketch_tma", "read_n2e18": 4295577600, "write_n2e18": 10937344, "write_scales": False,
         "sources": ("paper_2210_11295_gb300/csrc/sketch_tma.cu", "paper_2210_11295_gb300/csrc/tma.cuh",
-                    "paper_2210_11295_gb300/csrc/f32x2.cuh"),
-        "sha256": "ccf7d93578422680a1a8c72cc11d4a815afe82894387239a164cfbf28f722790"},
+                    "paper_2210_11295_gb300/csrc/f32x2.cuh", "paper_2210_11295_gb300/csrc/tmem.cuh"),
+        "sha256": "ca6860d416ec01d8c929f0487f7bd6c01e8f56c165772ffdb2198846db92a4b4"},
     # FP64: besides A, the read-modify-write of the FP64 partial sums at
     # every flush of the integer sums (one per 32 chunks of a CTA), which
     # grows with n like the reads.

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -91,10 +92,17 @@ int gemm_launch(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const 
   g.upper_c = gram ? 1 : 0;
   const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
   const int64_t tiles = gram ? tm * (tm + 1) / 2 : tm * tn;
+  // Split K when the tiles alone leave SMs idle.  FP64 FMAs run at 1/64 of
+  // the FP32 rate on this GPU (about two per SM and clock): one 64 x 64 tile
+  // over K = 256 keeps an SM busy for a quarter of a millisecond, so FP64
+  // products split K down to 32-deep ranges; FP32 ones keep ranges of at
+  // least 256.
+  constexpr bool kF64 = std::is_same<Tacc, double>::value;
+  constexpr int64_t kMinRange = kF64 ? 4 * BK : 32 * BK, kMinK = kF64 ? 8 * BK : 64 * BK;
   int splits = 1;
   const int64_t target = 2 * (int64_t)num_sms();
-  if (tiles < target && K > 64 * BK) {
-    splits = (int)std::min<int64_t>((target + tiles - 1) / tiles, K / (32 * BK));
+  if (tiles < target && K > kMinK) {
+    splits = (int)std::min<int64_t>((target + tiles - 1) / tiles, K / kMinRange);
     splits = std::max(1, std::min(splits, 64));
   }
   dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)splits);

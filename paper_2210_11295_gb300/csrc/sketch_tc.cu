@@ -71,9 +71,6 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
       : "memory");
 }
 
-// Waits for this thread's outstanding tcgen05.ld.
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
 // Byte offset of element (row n, k) in a K-major operand of 128-byte rows
 // (64 16-bit values) with the 128-byte swizzle; K-blocks of 64 are
 // rows_per_kblock * 128 bytes apart.
@@ -235,7 +232,7 @@ __global__ void __launch_bounds__(kNT, 1)
                        : "memory");
         }
       }
-      tmem_wait_ld();
+      tc::tmem_wait_ld();
 #pragma unroll
       for (int c = 0; c < EC; ++c) {
         const float x0 = __uint_as_float(r[0][c]), x1 = __uint_as_float(r[1][c]);

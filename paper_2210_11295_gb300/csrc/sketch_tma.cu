@@ -9,9 +9,10 @@
 // phase (high five row bits) gives each thread one column of 32 rows; the
 // exchange phase (low four bits) and the gather give it two adjacent columns
 // and use 64-bit shared-memory accesses, the exchange phase as packed FP32
-// pairs.  For l > 512 a 256-thread form (k_sketch_tma256, and
-// k_sketch_tma256w above l = 768) holds 2 x 32 rows in the register phase
-// and 4 columns in the exchange phase and gather.  Here one thread
+// pairs.  For 512 < l <= 768 a 256-thread form (k_sketch_tma256) holds
+// 2 x 32 rows in the register phase and 4 columns in the exchange phase and
+// gather; above that the 512-thread kernel keeps half of its 1024-row
+// group's accumulators in tensor memory.  Here one thread
 // streams the chunks with cp.async.bulk.tensor into a STAGES-deep ring
 // guarded by mbarriers, so HBM reads of later chunks overlap the butterflies
 // and the gather of the current one.  FP32 inputs are transformed in place
@@ -25,6 +26,7 @@
 #include "sketch_kernels.cuh"
 #include "tma.cuh"
 #include "f32x2.cuh"
+#include "tmem.cuh"
 
 namespace bsrht {
 
@@ -49,7 +51,7 @@ struct TmaShape {
   static constexpr int BOXR = R2 < 256 ? R2 : 256;
   static constexpr size_t stage_bytes = sizeof(Tin) * (size_t)R2 * W;
   static constexpr size_t tile_bytes = kInPlace ? 0 : sizeof(float) * (size_t)R2 * W;
-  static constexpr size_t meta_bytes = 2 * sizeof(uint32_t) * JG + sizeof(uint64_t) * STAGES;
+  static constexpr size_t meta_bytes = 2 * sizeof(uint32_t) * JG + sizeof(uint64_t) * STAGES + 16;
   static constexpr size_t smem_bytes() { return STAGES * stage_bytes + tile_bytes + meta_bytes + 128; }
   static_assert(NT % W == 0 && E >= NRL && E % NRL == 0, "thread layout");
   static_assert(R2 >= 64 && R2 % BOXR == 0, "chunk rows");
@@ -123,6 +125,7 @@ __global__ void __launch_bounds__(NT, 1)
   uint32_t* s_off = reinterpret_cast<uint32_t*>(base + STAGES * S::stage_bytes + S::tile_bytes);  // s_lo * W
   uint32_t* s_hi = s_off + JG;
   uint64_t* bar = reinterpret_cast<uint64_t*>(s_hi + JG);
+  uint32_t* tm_slot = reinterpret_cast<uint32_t*>(bar + STAGES);  // TMEM base address (JM = 64)
 
   const int tid = threadIdx.x;
   const int cg = tid % W;  // == lane
@@ -187,7 +190,27 @@ __global__ void __launch_bounds__(NT, 1)
     s_off[(jl % 32) * (JM / 2) + jl / 32] = off;  // [row lane rg][u]: jl = rg + 32 u
     s_hi[jl] = hi;
   }
+  // Sketch-row groups of 1024 (JU = 32 rows per thread, 64 accumulators):
+  // the 128-register budget of 512 threads holds half of them, and the
+  // other half waits in TMEM (unused by this kernel otherwise).  Each warp
+  // owns two 32-column slots of its lane quarter; per chunk the gather
+  // works through the half in registers, swaps it with the half in TMEM
+  // (one tcgen05.st and one tcgen05.ld of 32 values per thread) and works
+  // through that one; the next chunk starts with the half now in registers.
+  constexpr int JU = JM / 2, NH = JU / 16;
+  constexpr bool kTm = JU > 16;
+  constexpr int JR = kTm ? 16 : JU;  // sketch rows whose accumulators are in registers
+  constexpr uint32_t kTmCols = 256;
+  if constexpr (kTm) {
+    if (tid < 32) tc::tmem_alloc(tm_slot, kTmCols);
+    tc::tc_fence_before();
+  }
   __syncthreads();
+  uint32_t tm_addr = 0;  // this thread's slot 0; slot 1 is 32 columns on
+  if constexpr (kTm) {
+    tc::tc_fence_after();
+    tm_addr = *tm_slot + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + 64u * (uint32_t)(tid >> 7);
+  }
   if (tid == 0)
     for (int64_t k = 0; k < STAGES && k < ntiles; ++k) issue_next();
 
@@ -197,23 +220,33 @@ __global__ void __launch_bounds__(NT, 1)
   // evaluates the outer-factor x Dt^(i) sign of u = 16 h + cp and a warp
   // ballot hands each lane its row lane's 16 bits.  s_hi never changes; the
   // Dt word only with the block.
-  constexpr int JU = JM / 2, NH = JU / 16;
   const int cp = tid & 15, rg = tid >> 4;
   uint32_t my_hi[NH];
 #pragma unroll
   for (int h = 0; h < NH; ++h) my_hi[h] = s_hi[rg + 32 * (16 * h + cp)];  // 0 for jl >= jn
 
-  float acc[JU][2];
+  float acc[JR][2];
+  float(&accv)[2 * JR] = reinterpret_cast<float(&)[2 * JR]>(acc);
 #pragma unroll
-  for (int u = 0; u < JU; ++u) acc[u][0] = acc[u][1] = 0.f;
+  for (int u = 0; u < JR; ++u) acc[u][0] = acc[u][1] = 0.f;
+  int hcur = 0;  // (JM = 64) the half of the sketch rows whose accumulators are in registers
   int64_t cur_pc = -1;
   float* part = static_cast<float*>(g.part);
-  auto flush = [&](int64_t pc) {
+  auto flush_rows = [&](int64_t pc, int ubase) {  // sketch rows rg + 32 (ubase + u)
     float* dst = part + sched.slot(pc) * (int64_t)jn * W + 2 * cp;
 #pragma unroll
-    for (int u = 0; u < JU; ++u) {
-      const int jl = rg + 32 * u;
+    for (int u = 0; u < JR; ++u) {
+      const int jl = rg + 32 * (ubase + u);
       if (jl < jn) *reinterpret_cast<float2*>(dst + (int64_t)jl * W) = make_float2(acc[u][0], acc[u][1]);
+    }
+  };
+  auto flush = [&](int64_t pc) {
+    if constexpr (kTm) {
+      flush_rows(pc, JR * hcur);
+      tc::tmem_ld32(tm_addr + 32u * (uint32_t)(1 - hcur), accv);
+      flush_rows(pc, JR * (1 - hcur));
+    } else {
+      flush_rows(pc, 0);
     }
   };
 
@@ -242,7 +275,8 @@ __global__ void __launch_bounds__(NT, 1)
     if (new_panel) {
       if (cur_pc >= 0) flush(cur_pc);
 #pragma unroll
-      for (int u = 0; u < JU; ++u) acc[u][0] = acc[u][1] = 0.f;
+      for (int u = 0; u < JR; ++u) acc[u][0] = acc[u][1] = 0.f;
+      if constexpr (kTm) tc::tmem_st32(tm_addr + 32u * (uint32_t)(1 - hcur), accv);
       cur_pc = pc;
     }
     int nvalid = R2;
@@ -312,7 +346,14 @@ __global__ void __launch_bounds__(NT, 1)
         for (int64_t kk = (issued - STAGES < k ? k : issued - STAGES); kk < issued; ++kk)
           mbar_wait_bounded(&bar[kk % STAGES], (uint32_t)((kk / STAGES) & 1), kWaitLimit);
       }
+      if constexpr (kTm) tc::tc_fence_before();
       __syncthreads();
+      if constexpr (kTm) {
+        if (tid < 32) {
+          tc::tc_fence_after();
+          tc::tmem_dealloc(*tm_slot, kTmCols);
+        }
+      }
       return;
     }
     // In place (FP32): every thread has finished the previous chunk, so its
@@ -337,22 +378,39 @@ __global__ void __launch_bounds__(NT, 1)
     }
     __syncthreads();
     // Sampled rows (offsets s_lo * W) with the signs of gmask, two columns per load.
-    const uint4* offv = reinterpret_cast<const uint4*>(s_off + rg * JU);
     const float* tq = tile + 2 * cp;
+    auto gather = [&](int hs) {  // sketch rows rg + 32 (JR hs + u), u < JR
+      const uint4* offv = reinterpret_cast<const uint4*>(s_off + rg * JU + JR * hs);
+      const uint32_t gm = (NH > 1 && hs) ? gmask[NH - 1] : gmask[0];
 #pragma unroll
-    for (int u4 = 0; u4 < JU / 4; ++u4) {
-      const uint4 o = offv[u4];
-      const uint32_t oo[4] = {o.x, o.y, o.z, o.w};
+      for (int u4 = 0; u4 < JR / 4; ++u4) {
+        // Groups of four sketch rows all at or past jn hold nothing (uniform).
+        if constexpr (kTm) {
+          if (32 * (JR * hs + 4 * u4) >= jn) break;
+        }
+        const uint4 o = offv[u4];
+        const uint32_t oo[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int u = 4 * u4 + q;
-        const float2 tv = *reinterpret_cast<const float2*>(tq + oo[q]);
-        // +-1.0f from the sign bit: the product is exact, so the FMA adds
-        // exactly +-tv, one instruction per column.
-        const float sg = __uint_as_float(((gmask[u >> 4] << (31 - (u & 15))) & 0x80000000u) | 0x3f800000u);
-        acc[u][0] = fmaf(tv.x, sg, acc[u][0]);
-        acc[u][1] = fmaf(tv.y, sg, acc[u][1]);
+        for (int q = 0; q < 4; ++q) {
+          const int u = 4 * u4 + q;
+          const float2 tv = *reinterpret_cast<const float2*>(tq + oo[q]);
+          // +-1.0f from the sign bit: the product is exact, so the FMA adds
+          // exactly +-tv, one instruction per column.
+          const float sg = __uint_as_float((((NH > 1 ? gm : gmask[u >> 4]) << (31 - (u & 15))) & 0x80000000u) |
+                                           0x3f800000u);
+          acc[u][0] = fmaf(tv.x, sg, acc[u][0]);
+          acc[u][1] = fmaf(tv.y, sg, acc[u][1]);
+        }
       }
+    };
+    if constexpr (kTm) {
+      gather(hcur);
+      tc::tmem_st32(tm_addr + 32u * (uint32_t)hcur, accv);
+      tc::tmem_ld32(tm_addr + 32u * (uint32_t)(1 - hcur), accv);
+      hcur ^= 1;
+      gather(hcur);
+    } else {
+      gather(0);
     }
     if constexpr (!S::kInPlace) {
       __syncthreads();  // stage s and the separate tile are free again
@@ -373,6 +431,14 @@ __global__ void __launch_bounds__(NT, 1)
     if (wrap) pc += sched.step;
   }
   if (cur_pc >= 0) flush(cur_pc);
+  if constexpr (kTm) {
+    tc::tc_fence_before();
+    __syncthreads();
+    if (tid < 32) {
+      tc::tc_fence_after();
+      tc::tmem_dealloc(*tm_slot, kTmCols);
+    }
+  }
 }
 
 template <typename Tin, int JU, int STAGES>
@@ -381,7 +447,7 @@ __global__ void __launch_bounds__(256, 1)
                  const uint64_t* __restrict__ dttab, int64_t tw, int* __restrict__ err) {
   using S = TmaShape256<Tin, JU, STAGES>;
   constexpr int W = S::W, NT = S::NT, R2 = S::R2, JG = S::JG, BOXR = S::BOXR;
-  static_assert(JU <= 24, "32 sketch rows per thread: k_sketch_tma256w");
+  static_assert(JU <= 24, "32 sketch rows per thread: k_sketch_tma with JM = 64");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128 - (reinterpret_cast<uintptr_t>(smem_raw) & 127)) & 127);
   Tin* stage = reinterpret_cast<Tin*>(base);                                   // [STAGES][R2][W]
@@ -641,261 +707,6 @@ __global__ void __launch_bounds__(256, 1)
   if (cur_pc >= 0) flush(cur_pc);
 }
 
-// The 256-thread form with 32 sketch rows per thread (l > 768): scalar
-// butterflies and 64-bit tile indices, the arrangement in which the
-// register allocator places the spills of its 128 accumulators best
-// (measured on GB300: 5.6 ms at n = 2^20, m = 4096, l = 1024 against 6.7 to
-// 7.0 ms for the packed and 32-bit-index forms).
-template <typename Tin, int JU, int STAGES>
-__global__ void __launch_bounds__(256, 1)
-    k_sketch_tma256w(const __grid_constant__ CUtensorMap tmap, SketchArgs g, const uint32_t* __restrict__ dmtab,
-                 const uint64_t* __restrict__ dttab, int64_t tw, int* __restrict__ err) {
-  using S = TmaShape256<Tin, JU, STAGES>;
-  constexpr int W = S::W, NT = S::NT, R2 = S::R2, JG = S::JG, BOXR = S::BOXR;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned char* base = smem_raw + ((128 - (reinterpret_cast<uintptr_t>(smem_raw) & 127)) & 127);
-  Tin* stage = reinterpret_cast<Tin*>(base);                                   // [STAGES][R2][W]
-  float* tile_sep = reinterpret_cast<float*>(base + STAGES * S::stage_bytes);  // [R2][W] (16-bit inputs)
-  uint32_t* s_off = reinterpret_cast<uint32_t*>(base + STAGES * S::stage_bytes + S::tile_bytes);  // s_lo * W
-  uint32_t* s_hi = s_off + JG;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(s_hi + JG);
-
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int rl = tid >> 4, cp = tid & 15;  // register phase: row lane, column pair
-  const int rg = tid >> 3, c4 = tid & 7;   // exchange phase and gather: row group, column quad
-  const int jn = (int)g.jn;
-  TileSched sched;
-  sched.init(g, (int)blockIdx.x);
-  const int64_t t_begin = sched.begin;
-  const int64_t ntiles = sched.end - sched.begin;
-
-  // Tile t = (panel pc, block i, chunk a) in panel-major order; iterators
-  // advance without divisions.
-  struct TileIt {
-    int64_t pc, i, a;
-    int step;
-    __device__ void next(int64_t nch, int p) {
-      if (++a == nch) {
-        a = 0;
-        if (++i == p) {
-          i = 0;
-          pc += step;
-        }
-      }
-    }
-  };
-  auto tile_at = [&](int64_t t) {  // unit t of the schedule
-    TileIt it;
-    const int64_t u = t / g.C;
-    const int64_t c = t - u * g.C;
-    it.pc = u * sched.step + sched.half;
-    it.i = c / g.nch;
-    it.a = c - it.i * g.nch;
-    it.step = sched.step;
-    return it;
-  };
-  TileIt iss = tile_at(t_begin);  // next tile to issue (thread 0 only)
-  int64_t issued = 0;
-  auto issue_next = [&]() {  // TMA for the CTA's next tile into stage issued % STAGES
-    const int s = (int)(issued % STAGES);
-    Tin* dst = stage + (size_t)s * R2 * W;
-    mbar_arrive_expect_tx(&bar[s], (uint32_t)S::stage_bytes);
-    const int32_t x = (int32_t)(iss.pc * W);
-    const int64_t y0 = iss.i * g.rb + iss.a * R2;
-#pragma unroll
-    for (int h = 0; h < R2 / BOXR; ++h)
-      tma_load_2d(dst + (size_t)h * BOXR * W, &tmap, &bar[s], x, (int32_t)(y0 + h * BOXR));
-    iss.next(g.nch, g.p);
-    ++issued;
-  };
-
-  if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
-    fence_mbar_init();
-  }
-  for (int jl = tid; jl < JG; jl += NT) {
-    uint32_t off = 0, hi = 0;
-    if (jl < jn) {
-      const uint64_t sv = sample_word(g.seed, (uint64_t)(g.j0 + jl)) & (uint64_t)(g.r - 1);
-      off = (uint32_t)(sv & (R2 - 1)) * W;
-      hi = (uint32_t)(sv >> 9);  // R2 = 512
-    }
-    s_off[(jl % 32) * JU + jl / 32] = off;  // [row group rg][u]: jl = rg + 32 u
-    s_hi[jl] = hi;
-  }
-  __syncthreads();
-  if (tid == 0)
-    for (int64_t k = 0; k < STAGES && k < ntiles; ++k) issue_next();
-
-  // Gather: sketch rows jl = rg + 32 u, u < JU, four columns each.  The 8
-  // lanes of a row group share its sketch rows: lane c4 evaluates the
-  // outer-factor x Dt^(i) sign of u = 8 h + c4 and a warp ballot hands each
-  // lane its row group's byte.  s_hi never changes; the Dt word only with
-  // the block.
-  constexpr int NH = JU / 8;
-  uint32_t my_hi[NH];
-  uint64_t my_dt[NH];
-  int64_t dt_block = -1;
-#pragma unroll
-  for (int h = 0; h < NH; ++h) {
-    my_hi[h] = s_hi[rg + 32 * (8 * h + c4)];
-    my_dt[h] = 0;
-  }
-
-  float acc[JU][4];
-#pragma unroll
-  for (int u = 0; u < JU; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
-  int64_t cur_pc = -1;
-  float* part = static_cast<float*>(g.part);
-  auto flush = [&](int64_t pc) {
-    float* dst = part + sched.slot(pc) * (int64_t)jn * W + 4 * c4;
-#pragma unroll
-    for (int u = 0; u < JU; ++u) {
-      const int jl = rg + 32 * u;
-      if (jl < jn)
-        *reinterpret_cast<float4*>(dst + (int64_t)jl * W) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
-    }
-  };
-
-  TileIt cur = tile_at(t_begin);
-  uint32_t dmask_next = ntiles > 0 ? __ldg(dmtab + (cur.i * g.nch + cur.a) * 16 + rl) : 0u;  // rows rl + 16 e
-  int s = 0;
-  uint32_t parity = 0;
-  for (int64_t k = 0; k < ntiles; ++k, cur.next(g.nch, g.p)) {
-    const int64_t pc = cur.pc, i = cur.i, a = cur.a;
-    if (pc != cur_pc) {
-      if (cur_pc >= 0) flush(cur_pc);
-#pragma unroll
-      for (int u = 0; u < JU; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
-      cur_pc = pc;
-    }
-    const int64_t rows_i = min(g.rb, g.n - i * g.rb);
-    const int64_t row0 = a * R2;
-    const int nvalid = (int)min((int64_t)R2, rows_i - row0);
-    // This thread's 32 D^(i) signs (rows rl + 16e) and, by a warp ballot, the
-    // outer-factor x Dt^(i) signs of its row lane's sketch rows jl = rl + 16u.
-    const uint32_t dmask = dmask_next;
-    {  // prefetch the next chunk's D mask
-      TileIt nx = cur;
-      nx.next(g.nch, g.p);
-      if (k + 1 < ntiles) dmask_next = __ldg(dmtab + (nx.i * g.nch + nx.a) * 16 + rl);
-    }
-    if (i != dt_block) {
-#pragma unroll
-      for (int h = 0; h < NH; ++h) {
-        const int jl = rg + 32 * (8 * h + c4);
-        my_dt[h] = jl < jn ? __ldg(dttab + i * tw + (jl >> 6)) : 0ull;
-      }
-      dt_block = i;
-    }
-    uint32_t gmask[NH];
-#pragma unroll
-    for (int h = 0; h < NH; ++h) {
-      const int jl = rg + 32 * (8 * h + c4);
-      const uint32_t sg = (uint32_t)((__popc(my_hi[h] & (uint32_t)a) + (int)((my_dt[h] >> (jl & 63)) & 1ull)) & 1);
-      gmask[h] = (__ballot_sync(0xffffffffu, jl < jn ? sg : 0u) >> (8 * (lane >> 3))) & 0xFFu;
-    }
-    const bool ok = mbar_wait_bounded(&bar[s], parity, kWaitLimit);
-
-    Tin* st = stage + (size_t)s * R2 * W;
-    float* tile = S::kInPlace ? reinterpret_cast<float*>(st) : tile_sep;
-    // Register phase: rows rl + 16 e (high five row bits), columns 2 cp,
-    // 2 cp + 1, D^(i) signs (one per row for both columns).
-    {
-      float v0[32], v1[32];
-#pragma unroll
-      for (int e = 0; e < 32; ++e) {
-        const int rr = rl + 16 * e;
-        float x0 = 0.f, x1 = 0.f;
-        if (nvalid == R2 || rr < nvalid) {
-          if constexpr (sizeof(Tin) == 4) {
-            const float2 t2 = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st) + rr * W + 2 * cp);
-            x0 = t2.x;
-            x1 = t2.y;
-          } else {
-            const uint32_t raw = *reinterpret_cast<const uint32_t*>(st + rr * W + 2 * cp);
-            const Tin* h2 = reinterpret_cast<const Tin*>(&raw);
-            x0 = widen<Tin>(h2[0]);
-            x1 = widen<Tin>(h2[1]);
-          }
-        }
-        const uint32_t sb = (dmask << (31 - e)) & 0x80000000u;
-        v0[e] = __uint_as_float(__float_as_uint(x0) ^ sb);
-        v1[e] = __uint_as_float(__float_as_uint(x1) ^ sb);
-      }
-      fwht_regs<float, 32>(v0);
-      fwht_regs<float, 32>(v1);
-      if constexpr (!S::kInPlace) __syncthreads();  // the previous chunk's gather is done with the tile
-#pragma unroll
-      for (int e = 0; e < 32; ++e)
-        *reinterpret_cast<float2*>(tile + (rl + 16 * e) * W + 2 * cp) = make_float2(v0[e], v1[e]);
-    }
-    // One barrier both publishes the register phase and makes a failed
-    // (bounded) wait CTA-uniform: data read after a failed wait is garbage
-    // but nothing reaches global memory before this check.
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicOr(err, 1);
-        for (int64_t kk = (issued - STAGES < k ? k : issued - STAGES); kk < issued; ++kk)
-          mbar_wait_bounded(&bar[kk % STAGES], (uint32_t)((kk / STAGES) & 1), kWaitLimit);
-      }
-      __syncthreads();
-      return;
-    }
-    // Every thread has finished the previous chunk's gather (FP32: its stage,
-    // which is its tile, is free) or this chunk's widening (16-bit: this
-    // stage is free): refill it.
-    if (tid == 0 && issued < ntiles && (!S::kInPlace || k >= 1)) {
-      fence_proxy_async_smem();
-      issue_next();
-    }
-    // Exchange phase: rows 16 rg + b (low four bits), columns 4 c4 .. 4 c4 + 3.
-    {
-      float w[4][16];
-      float* tp = tile + (16 * rg) * W + 4 * c4;
-#pragma unroll
-      for (int b = 0; b < 16; ++b) {
-        const float4 t4 = *reinterpret_cast<const float4*>(tp + b * W);
-        w[0][b] = t4.x;
-        w[1][b] = t4.y;
-        w[2][b] = t4.z;
-        w[3][b] = t4.w;
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) fwht_regs<float, 16>(w[c]);
-#pragma unroll
-      for (int b = 0; b < 16; ++b)
-        *reinterpret_cast<float4*>(tp + b * W) = make_float4(w[0][b], w[1][b], w[2][b], w[3][b]);
-    }
-    __syncthreads();
-    // Sampled rows (offsets s_lo * W) with the signs of gmask, four columns
-    // per load; +-1.0f from the sign bit makes the FMA add exactly +-t.
-    const uint4* offv = reinterpret_cast<const uint4*>(s_off + rg * JU);
-    const float* tq = tile + 4 * c4;
-#pragma unroll
-    for (int u4 = 0; u4 < JU / 4; ++u4) {
-      const uint4 o = offv[u4];
-      const uint32_t oo[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int u = 4 * u4 + q;
-        const float4 tv = *reinterpret_cast<const float4*>(tq + oo[q]);
-        const float sg = __uint_as_float(((gmask[u >> 3] << (31 - (u & 7))) & 0x80000000u) | 0x3f800000u);
-        acc[u][0] = fmaf(tv.x, sg, acc[u][0]);
-        acc[u][1] = fmaf(tv.y, sg, acc[u][1]);
-        acc[u][2] = fmaf(tv.z, sg, acc[u][2]);
-        acc[u][3] = fmaf(tv.w, sg, acc[u][3]);
-      }
-    }
-    if (++s == STAGES) {
-      s = 0;
-      parity ^= 1u;
-    }
-  }
-  if (cur_pc >= 0) flush(cur_pc);
-}
-
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -915,15 +726,15 @@ EncodeFn encode_fn() {
   return fn;
 }
 
-// l <= 512 (JM = 32): 512 threads of 32 values (more warps hide the
-// shared-memory latency); l > 512: 256 threads of 64 values, whose
-// 255-register budget holds the accumulators -- 96 for l <= 768 (JM = 48,
-// sketch-row groups of 768, packed butterflies), 128 for larger l (JM = 64,
-// groups of 1024, k_sketch_tma256w).
+// l <= 512 (JM = 32) and l > 768 (JM = 64, sketch-row groups of 1024, half
+// the accumulators in TMEM): 512 threads of 32 values (more warps hide the
+// shared-memory latency); 512 < l <= 768 (JM = 48): 256 threads of 64
+// values, whose 255-register budget holds 96 accumulators (packed
+// butterflies).
 template <typename Tin, int JM>
 struct TmaKernel {
   static constexpr int STAGES = stages_for<Tin>();
-  static constexpr bool k256 = JM > 32;
+  static constexpr bool k256 = JM == 48;
   static constexpr int NT = k256 ? 256 : 512;
   static size_t smem() {
     if constexpr (k256)
@@ -932,9 +743,7 @@ struct TmaKernel {
       return TmaShape<Tin, 32, 512, 512, JM, STAGES>::smem_bytes();
   }
   static auto fn() {
-    if constexpr (JM > 48)
-      return k_sketch_tma256w<Tin, JM / 2, STAGES>;
-    else if constexpr (k256)
+    if constexpr (k256)
       return k_sketch_tma256<Tin, JM / 2, STAGES>;
     else
       return k_sketch_tma<Tin, 32, 512, 512, JM, STAGES>;
