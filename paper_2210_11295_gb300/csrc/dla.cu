@@ -945,7 +945,7 @@ __global__ void __launch_bounds__(32 * B * WP) k_jacobi_blk(float* __restrict__ 
   float* Ms = jsm;
   float* Vs = jsm + (size_t)2 * B * l;
   float* nrm = Vs + (size_t)2 * B * l;
-  float* part = nrm + 2 * B;  // [B][2]: the two warps' partial inner products (WP = 2)
+  float* part = nrm + 2 * B;  // [B][WP]: the pair's warps' partial inner products (WP > 1)
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pw = w / WP, hw = w % WP;  // pair slot and half of the warp
   const float ttol = (float)tol, tstop = (float)tol_stop;
@@ -1025,10 +1025,10 @@ __global__ void __launch_bounds__(32 * B * WP) k_jacobi_blk(float* __restrict__ 
           // l % 4 == 0: the lane holds rows 128 e + 4 lane + j (j < 4) of the
           // two columns of M and V, moved with 16-byte shared-memory accesses,
           // and rotates them as packed pairs (rows j = 0, 1 and 2, 3).  With
-          // WP = 2 the pair's two warps take the chunks e = 2 e' + hw and add
-          // their partial inner products through shared memory (a 64-thread
-          // named barrier per pair), in the same order in both warps, so both
-          // derive the same rotation.
+          // WP > 1 the pair's WP warps take the chunks e = WP e' + hw and add
+          // their partial inner products through shared memory (a named
+          // barrier of 32 WP threads per pair), in the same order in every
+          // warp, so all derive the same rotation.
           constexpr int JQ = JR / 4 / WP;
           const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(a);
           const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(b);
@@ -1053,10 +1053,12 @@ __global__ void __launch_bounds__(32 * B * WP) k_jacobi_blk(float* __restrict__ 
           }
           const float2 gp = f2_to_float2(f2_add(g2[0], g2[1]));
           float gamma = warp_sum(gp.x + gp.y);
-          if constexpr (WP == 2) {
-            if (lane == 0) part[2 * pw + hw] = gamma;
-            asm volatile("bar.sync %0, 64;" ::"r"(1 + pw) : "memory");
-            gamma = part[2 * pw] + part[2 * pw + 1];
+          if constexpr (WP > 1) {
+            if (lane == 0) part[WP * pw + hw] = gamma;
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + pw), "r"(32 * WP) : "memory");
+            gamma = part[WP * pw];
+#pragma unroll
+            for (int h = 1; h < WP; ++h) gamma += part[WP * pw + h];
           }
           const float gnorm = sqrtf(alpha) * sqrtf(beta);
           if (gamma != 0.f && fabsf(gamma) > ttol * gnorm) {
@@ -1171,11 +1173,11 @@ int launch_jacobi_blk_v(const Dla& d, float* M, float* V, int64_t l, double tol,
   auto kern = k_jacobi_blk<B, JR, VEC, WP>;
   int li = (int)l, nblk = (int)((l + B - 1) / B), msw = max_sweeps;
   nblk += nblk & 1;
-  const size_t smem = sizeof(float) * ((size_t)4 * B * l + 4 * B);
+  const size_t smem = sizeof(float) * ((size_t)4 * B * l + (2 + WP) * B);
   // One instance serves every l up to 32 JR, and host threads (the server's
   // executors) launch it concurrently: the attribute is always set to the
   // largest of them, so no thread lowers it below another one's launch.
-  const size_t smem_max = sizeof(float) * ((size_t)4 * B * 32 * JR + 4 * B);
+  const size_t smem_max = sizeof(float) * ((size_t)4 * B * 32 * JR + (2 + WP) * B);
   BSRHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
   int occ = 0;
   BSRHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
