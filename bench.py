@@ -71,9 +71,6 @@ def parse_args():
                     help="sketch kernel: library choice, CUDA-core butterflies (K1), tensor cores (K2, 16-bit A), "
                          "or the Gaussian-embedding comparator of Sec. 4 (FP32)")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--h2d-streams", type=int, default=4,
-                    help="end-to-end run: the host-to-device copy of A as this many row ranges on as many "
-                         "streams (several copy engines at once)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the metric's other parts (FP64 sketch, small FP64 workload, 16-bit workload, "
                          "stated rSVD error, Nystrom, serving summary)")
@@ -921,31 +918,11 @@ def run_ours(args):
         else:
             hb = torch.empty(l, m, dtype=out.dtype).pin_memory()
         del a
-        nh = max(1, args.h2d_streams)
-        h2d_streams = [torch.cuda.Stream() for _ in range(nh)] if nh > 1 else []
-        rows_per = (n + nh - 1) // nh
-
-        def copy_in():
-            # Row ranges of A on side streams that start after the current
-            # stream's earlier work and that the current stream waits for.
-            if not h2d_streams:
-                a_dev2.copy_(a_host, non_blocking=True)
-                return
-            cur = torch.cuda.current_stream()
-            ev = cur.record_event()
-            for c, st in enumerate(h2d_streams):
-                st.wait_event(ev)
-                with torch.cuda.stream(st):
-                    a_dev2[c * rows_per:(c + 1) * rows_per].copy_(a_host[c * rows_per:(c + 1) * rows_per],
-                                                                  non_blocking=True)
-            for st in h2d_streams:
-                cur.wait_stream(st)
-
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
         for i in range(args.e2e_steps):
-            copy_in()
+            a_dev2.copy_(a_host, non_blocking=True)
             if mode == "full":
                 lib.bsrht_rsvd(a_dev2, k, l, p, i, variant=variant, workspace=rws, outs=(u, s, v))
                 hu.copy_(u, non_blocking=True)
@@ -996,7 +973,7 @@ def run_ours(args):
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
         "e2e": {"value": round(total_bytes_all / (e2e_ms * 1e-3) / 1e9, 3) if e2e_ms else None, "unit": "GB/s",
                 "ms_per_step": round(e2e_ms, 3) if e2e_ms else None,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "h2d_streams": max(1, args.h2d_streams)},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
     }
     if stages:

@@ -105,7 +105,11 @@ int gemm_launch(const Dla& d, Arena& ar, int64_t M, int64_t N, int64_t K, const 
     splits = (int)std::min<int64_t>((target + tiles - 1) / tiles, K / kMinRange);
     splits = std::max(1, std::min(splits, 64));
   }
-  dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)splits);
+  // Row and column tiles on one grid dimension (the y dimension's 65535
+  // would cap M at about 4 million rows).
+  g.tiles_n = tn;
+  if (tm * tn > (int64_t)INT32_MAX) return BSRHT_EUNSUP;
+  dim3 grid((unsigned)(tm * tn), 1u, (unsigned)splits);
   if (splits > 1 || gram) {
     Tacc* P = static_cast<Tacc*>(ar.take(sizeof(Tacc) * (size_t)splits * M * N));
     if (!ar.ok()) return BSRHT_ENOMEM;

@@ -21,6 +21,7 @@ struct GemmArgs {
   void* C;         // TC output (splits == 1) or Tacc partials (splits > 1)
   int64_t M, N, K;
   int64_t lda, ldb, ldc;
+  int64_t tiles_n;  // column tiles: tile t of the 1-D grid is (t / tiles_n, t % tiles_n)
   double alpha, beta;
   int splits;      // split-K factor (gridDim.z)
   int a_trans;     // 1: op(A) = A^T
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs g) {
   __shared__ Tacc Bs[2][BK][BN + 4];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  const int64_t bm = blockIdx.y, bn = blockIdx.x;
+  const int64_t bm = (int64_t)blockIdx.x / g.tiles_n, bn = (int64_t)blockIdx.x % g.tiles_n;
   if (g.upper_c && bm > bn) return;
   const int64_t m0 = bm * BM, n0 = bn * BN;
   int64_t kend = g.K;

@@ -84,6 +84,21 @@ def test_rsvd_exact_recovery_fp64(lib, p):
     assert np.linalg.norm(v.T @ v - np.eye(20)) <= 1e-12
 
 
+def test_rsvd_fp64_beyond_65535_row_tiles(lib):
+    """n = 2^22 + 4096 rows: the FP64 tall products (W = A Q and the tall QR)
+    have more than 65535 row tiles of 64, which one grid dimension of the
+    SIMT GEMM now carries; exact recovery of a rank-6 matrix as at small n."""
+    n, m, r = (1 << 22) + 4096, 16, 6
+    a = synth.exact_rank(n, m, r, seed=21)
+    u, s, v = lib.bsrht_rsvd(torch.from_numpy(a).cuda(), r, 12, 4, 2)
+    torch.cuda.synchronize()
+    u, s, v = u.cpu().numpy(), s.cpu().numpy(), v.cpu().numpy()
+    sv = np.linalg.svd(a, compute_uv=False)
+    np.testing.assert_allclose(s, sv[:r], rtol=1e-12, atol=1e-13 * sv[0])
+    assert np.linalg.norm(a - (u * s) @ v.T) <= 1e-12 * np.linalg.norm(a)
+    assert np.linalg.norm(u.T @ u - np.eye(r)) <= 1e-12
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
 def test_rsvd_reduced_precision_matches_oracle(lib, dtype):
     a32 = synth.lowrank_noise(1 << 15, 384, rank=200, seed=12, dtype=np.float32)
